@@ -1,0 +1,341 @@
+"""Plain, slow FP64 CPU oracle for the adjoint-based variational tau-descent of KS loops.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this module.  The
+product path never calls it and shares no code with it: every transform here is a naive
+dense DFT (matrix products over the paper's signed mode ranges), with no FFT library, no
+half-spectrum tricks and no blocking or fusion.
+
+Paper: Azimi, Ashtari & Schneider, "Adjoint-based variational method for constructing
+periodic orbits of high-dimensional chaotic systems" (arXiv:2007.06427).
+
+What is computed, in the paper's order and notation (KS with nu = 1):
+
+* a loop is l = [u(x, s); T] on [0, L) x [0, 1), both directions periodic (Sec. 2,
+  Eq. loop_def);
+* residual r = -(1/T) u_s - u u_x - u_xx - u_xxxx (Sec. 4.1, Eq. KS_R);
+* cost J = int_0^1 int_0^L r^2 dx ds (Sec. 2, Eq. cost_function);
+* adjoint L^dag_1 r = (1/T) r_s + u r_x - r_xx - r_xxxx and
+  L^dag_2 = int int (1/T^2) u_s r dx ds (Sec. 4.1, Eq. KS_L_dagger; App. B);
+* loop flow du/dtau = -L^dag_1, dT/dtau = -L^dag_2 (Eq. KS_G);
+* discretisation: M x N Fourier modes on the uniform grid (m L / M, n / N), synthesis
+  without a 1/N factor (Sec. 4.2, Eq. 2D_Fourier); derivatives in spectral space, products
+  on the grid, 2/3-rule dealiasing in x and s (Sec. 4.2);
+* tau-integration: IMEX Euler for u (the diagonal linear symbol Lambda_jk implicit, the
+  remaining nonlinear part explicit) and explicit Euler for T, with the T integral taken as
+  L x the (0,0) mode of the grid product (Sec. 4.2).  An EXPLICIT Euler variant is provided
+  for small-step tests.
+
+Readings where the paper is silent (each also listed in the design notes):
+
+* Dealiasing placement: the state u is kept in the 2/3 band; each grid product (u u_x and
+  u r_x) is transformed forward and truncated to the band, so r and L^dag_1 r are band
+  limited.  The cut-off keeps |j| <= floor(M/3), |k| <= floor(N/3) and zeroes the Nyquist
+  modes.
+* The two-stage form r -> L^dag_1 r is the flow that is integrated (it is the exact
+  gradient of the discrete J).  The expanded form G_1,L + G_1,NL of Eq. KS_G_1 is provided
+  separately as an independent check (``flow_expanded``).
+* IMEX: Lambda_jk uses T at the start of the step; u and T are both advanced from the same
+  state l^n.
+* Names: ``G`` is +L^dag_1 r (the ascent direction); ``dJdT`` is dJ/dT = 2 L^dag_2.
+
+The grid layout is u[n, m] (n: s-sample, m: x-sample).  Spectral arrays are indexed by
+signed modes in the paper's ranges, k = -N/2 .. N/2-1 on axis 0 and j = -M/2 .. M/2-1 on
+axis 1.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+EXPLICIT = 0
+IMEX = 1
+
+
+# ---------------------------------------------------------------------------------------
+# Discretisation (Sec. 4.2, Eq. 2D_Fourier)
+# ---------------------------------------------------------------------------------------
+
+def signed_modes(M: int) -> np.ndarray:
+    """Mode indices -M/2 .. M/2-1, the range of the paper's double sum (Eq. 2D_Fourier)."""
+    return np.arange(-(M // 2), M - M // 2, dtype=np.int64)
+
+
+def dft_matrix(M: int) -> np.ndarray:
+    """E[m, j] = exp(2 pi i m j / M) for grid index m and signed mode j.
+
+    The integer product m*j is reduced mod M before forming the angle so every entry is
+    cos/sin of 2 pi t / M with 0 <= t < M, accurate to about one ulp.
+    """
+    m = np.arange(M, dtype=np.int64)[:, None]
+    j = signed_modes(M)[None, :]
+    t = np.mod(m * j, M).astype(np.float64)
+    ang = 2.0 * math.pi * t / M
+    return np.cos(ang) + 1j * np.sin(ang)
+
+
+class Grid:
+    """Dense DFT operators and wavenumbers for one (M, N, L) discretisation."""
+
+    def __init__(self, Nx: int, Ns: int, L: float):
+        self.Nx, self.Ns, self.L = int(Nx), int(Ns), float(L)
+        self.Ex = dft_matrix(self.Nx)          # [m, j]
+        self.Es = dft_matrix(self.Ns)          # [n, k]
+        self.j = signed_modes(self.Nx)         # spatial modes (axis 1)
+        self.k = signed_modes(self.Ns)         # temporal modes (axis 0)
+        self.q = 2.0 * math.pi * self.j / self.L        # q_j = 2 pi j / L
+        self.omega = 2.0 * math.pi * self.k             # omega_k = 2 pi k (s has period 1)
+        self.Kx = self.Nx // 3
+        self.Ks = self.Ns // 3
+        # 2/3 rule in both directions (Sec. 4.2)
+        self.mask = (np.abs(self.k)[:, None] <= self.Ks) & (np.abs(self.j)[None, :] <= self.Kx)
+        self.Q = np.broadcast_to(self.q[None, :], (self.Ns, self.Nx))
+        self.W = np.broadcast_to(self.omega[:, None], (self.Ns, self.Nx))
+
+    # synthesis of Eq. 2D_Fourier: u(x_m, s_n) = sum_jk uh_jk exp(2 pi i (m j / M + n k / N))
+    def to_grid(self, uh: np.ndarray) -> np.ndarray:
+        return self.Es @ uh @ self.Ex.T
+
+    # analysis, the inverse of to_grid: uh_jk = (1/(M N)) sum_mn u_mn exp(-2 pi i (...))
+    def to_spectral(self, u: np.ndarray) -> np.ndarray:
+        return (self.Es.conj().T @ u @ self.Ex.conj()) / (self.Nx * self.Ns)
+
+    def project(self, uh: np.ndarray) -> np.ndarray:
+        """P: zero every mode outside |j| <= floor(M/3), |k| <= floor(N/3)."""
+        return np.where(self.mask, uh, 0.0)
+
+    def real_grid(self, uh: np.ndarray) -> np.ndarray:
+        return self.to_grid(uh).real
+
+    def dx(self, uh):
+        return 1j * self.Q * uh
+
+    def ds(self, uh):
+        return 1j * self.W * uh
+
+
+_GRIDS: dict = {}
+
+
+def grid(Nx: int, Ns: int, L: float) -> Grid:
+    key = (int(Nx), int(Ns), float(L))
+    g = _GRIDS.get(key)
+    if g is None:
+        g = _GRIDS[key] = Grid(*key)
+    return g
+
+
+# ---------------------------------------------------------------------------------------
+# Residual, cost and adjoint (Sec. 2, Sec. 4.1, App. B)
+# ---------------------------------------------------------------------------------------
+
+def band_state(u: np.ndarray, L: float) -> np.ndarray:
+    """Project grid values onto the 2/3 band: uh = P F[u]."""
+    g = grid(u.shape[1], u.shape[0], L)
+    return g.project(g.to_spectral(np.asarray(u, dtype=np.float64)))
+
+
+def residual_hat(uh: np.ndarray, T: float, g: Grid):
+    """Spectral residual of Eq. KS_R with the u u_x product dealiased (Sec. 4.2).
+
+    r_hat = -(1/T) (i omega) uh - P F[u u_x] - (i q)^2 uh - (i q)^4 uh.
+    Returns (r_hat, u, u_x) with u, u_x on the grid.
+    """
+    u = g.real_grid(uh)
+    ux = g.real_grid(g.dx(uh))
+    nl = g.project(g.to_spectral(u * ux))
+    uxx_h = (1j * g.Q) ** 2 * uh
+    uxxxx_h = (1j * g.Q) ** 4 * uh
+    rh = -(1.0 / T) * g.ds(uh) - nl - uxx_h - uxxxx_h
+    return rh, u, ux
+
+
+def cost(rh: np.ndarray, g: Grid) -> float:
+    """J = int int r^2 dx ds (Eq. cost_function), as L x the grid mean of r^2.
+
+    r is band limited, so r^2 has no aliased modes and the grid mean equals the integral
+    over the unit s-period divided by L.
+    """
+    r = g.real_grid(rh)
+    return float(g.L * np.mean(r * r))
+
+
+def adjoint_T(uh: np.ndarray, rh: np.ndarray, T: float, g: Grid) -> float:
+    """L^dag_2 = int int (1/T^2) u_s r dx ds (Eq. KS_L_dagger).
+
+    Evaluated as the paper does for the period update (Sec. 4.2): the integrand is formed
+    on the grid, transformed, and the (0,0) Fourier mode times L is the integral.
+    """
+    us = g.real_grid(g.ds(uh))
+    r = g.real_grid(rh)
+    prod_h = g.to_spectral(us * r / (T * T))
+    i0 = g.Ns // 2  # index of k = 0 on axis 0
+    j0 = g.Nx // 2  # index of j = 0 on axis 1
+    return float(g.L * prod_h[i0, j0].real)
+
+
+def adjoint_u_hat(uh: np.ndarray, rh: np.ndarray, T: float, g: Grid, u=None) -> np.ndarray:
+    """Spectral L^dag_1 r = (1/T) r_s + u r_x - r_xx - r_xxxx (Eq. KS_L_dagger, App. B).
+
+    The u r_x product is formed on the grid and truncated to the band (Sec. 4.2).
+    """
+    if u is None:
+        u = g.real_grid(uh)
+    rx = g.real_grid(g.dx(rh))
+    nl = g.project(g.to_spectral(u * rx))
+    rs_h = g.ds(rh)
+    rxx_h = (1j * g.Q) ** 2 * rh
+    rxxxx_h = (1j * g.Q) ** 4 * rh
+    return (1.0 / T) * rs_h + nl - rxx_h - rxxxx_h
+
+
+def residual(u: np.ndarray, T: float, L: float) -> dict:
+    """Residual of the loop [P u; T] on the grid, with J and dJ/dT (Eq. KS_R, cost_function)."""
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L)
+    rh, _, _ = residual_hat(uh, T, g)
+    J = cost(rh, g)
+    L2 = adjoint_T(uh, rh, T, g)
+    return {"uh": uh, "rh": rh, "r": g.real_grid(rh), "J": J, "L2": L2, "dJdT": 2.0 * L2}
+
+
+def adjoint_grad(u: np.ndarray, T: float, L: float) -> dict:
+    """G = +L^dag_1 r on the grid and dJ/dT = 2 L^dag_2, at the loop [P u; T]."""
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L)
+    rh, ug, _ = residual_hat(uh, T, g)
+    Gh = adjoint_u_hat(uh, rh, T, g, u=ug)
+    L2 = adjoint_T(uh, rh, T, g)
+    return {"uh": uh, "rh": rh, "Gh": Gh, "G": g.real_grid(Gh), "J": cost(rh, g),
+            "L2": L2, "dJdT": 2.0 * L2}
+
+
+# ---------------------------------------------------------------------------------------
+# Linear symbol and tau-integration (Sec. 4.2)
+# ---------------------------------------------------------------------------------------
+
+def linear_symbol(T: float, g: Grid) -> np.ndarray:
+    """Lambda_jk = -(2 pi k / T)^2 - q^8 + 2 q^6 - q^4, q = 2 pi j / L (Sec. 4.2)."""
+    Q, W = g.Q, g.W
+    return -(W / T) ** 2 - Q ** 8 + 2.0 * Q ** 6 - Q ** 4
+
+
+def step_hat(uh: np.ndarray, T: float, g: Grid, dtau: float, scheme: int):
+    """One tau-step of Eq. KS_G from the band state (uh, T).
+
+    Returns (uh_next, T_next, J, L2) where J and L2 are evaluated at the input state.
+    IMEX (Sec. 4.2): (uh' - uh)/dtau = Lambda uh' + G_NL with G_NL the field flow minus
+    its linear part, G_NL = -L^dag_1 r - Lambda uh; explicit Euler for T.
+    """
+    rh, u, _ = residual_hat(uh, T, g)
+    J = cost(rh, g)
+    L2 = adjoint_T(uh, rh, T, g)
+    Gh = adjoint_u_hat(uh, rh, T, g, u=u)
+    flow = -Gh                      # du/dtau = -L^dag_1 (Eq. KS_G)
+    if scheme == IMEX:
+        lam = linear_symbol(T, g)
+        g_nl = flow - lam * uh
+        uh_next = g.project((uh + dtau * g_nl) / (1.0 - dtau * lam))
+    elif scheme == EXPLICIT:
+        uh_next = g.project(uh + dtau * flow)
+    else:
+        raise ValueError("scheme must be EXPLICIT (0) or IMEX (1)")
+    T_next = T - dtau * L2          # dT/dtau = -L^dag_2, explicit Euler
+    return uh_next, T_next, J, L2
+
+
+def descend(u: np.ndarray, T: float, L: float, dtau: float, scheme: int, nsteps: int,
+            tol: float = 0.0, record: bool = False) -> dict:
+    """Advance the loop [P u; T] by up to ``nsteps`` tau-steps.
+
+    Stops before a step whose starting state already has sqrt(J) < tol (the convergence
+    test of Sec. 4.3).  Returns the final grid field, T, the step count, sqrt(J) of the final
+    state and, optionally, the sqrt(J) history (one value per evaluated state).
+    """
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L)
+    hist = []
+    steps = 0
+    while True:
+        rh, _, _ = residual_hat(uh, T, g)
+        J = cost(rh, g)
+        sq = math.sqrt(max(J, 0.0))
+        if record:
+            hist.append(sq)
+        if (tol > 0.0 and sq < tol) or steps >= nsteps:
+            break
+        uh, T, _, _ = step_hat(uh, T, g, dtau, scheme)
+        steps += 1
+    out = {"u": g.real_grid(uh), "uh": uh, "T": T, "steps": steps, "sqrtJ": sq}
+    if record:
+        out["hist"] = np.array(hist)
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Independent forms used only to pin the above (App. B; Eq. KS_G_1)
+# ---------------------------------------------------------------------------------------
+
+def directional_derivative(u: np.ndarray, T: float, v: np.ndarray, v2: float, L: float):
+    """Field part of the directional derivative of the residual along [v; v2] (App. B):
+
+        (v2 / T^2) u_s - (1/T) v_s - (u v)_x - v_xx - v_xxxx,
+
+    with the product u v formed on the grid and truncated to the band.  Returns grid values.
+    """
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L)
+    vh = band_state(v, L)
+    ug = g.real_grid(uh)
+    vg = g.real_grid(vh)
+    uvh = g.project(g.to_spectral(ug * vg))
+    out_h = ((v2 / (T * T)) * g.ds(uh) - (1.0 / T) * g.ds(vh) - g.dx(uvh)
+             - (1j * g.Q) ** 2 * vh - (1j * g.Q) ** 4 * vh)
+    return g.real_grid(out_h)
+
+
+def adjoint_operator(u: np.ndarray, T: float, w: np.ndarray, L: float):
+    """Generalized-loop adjoint applied to [w; 0] (App. B): returns (field part on the grid,
+    scalar part) = ((1/T) w_s + u w_x - w_xx - w_xxxx, int int (1/T^2) u_s w)."""
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L)
+    wh = band_state(w, L)
+    f_h = adjoint_u_hat(uh, wh, T, g)
+    return g.real_grid(f_h), adjoint_T(uh, wh, T, g)
+
+
+def flow_expanded(u: np.ndarray, T: float, L: float) -> np.ndarray:
+    """du/dtau written out in u alone, G_1,L + G_1,NL of Eq. KS_G_1 (Sec. 4.2).
+
+    Every derivative is spectral; every product is formed on the grid and the sum is
+    truncated to the band once.  For loops whose band is narrow enough that the cubic
+    products do not alias, this equals -L^dag_1 r from the two-stage evaluation.
+    """
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L)
+    D = lambda a, b: g.real_grid((1j * g.Q) ** a * (1j * g.W) ** b * uh)  # noqa: E731
+    u0 = D(0, 0)
+    ux, uxx, uxxx, uxxxx = D(1, 0), D(2, 0), D(3, 0), D(4, 0)
+    us, uss, uxs = D(0, 1), D(0, 2), D(1, 1)
+    lin_h = ((1j * g.W) ** 2 / (T * T) - (1j * g.Q) ** 8 - 2.0 * (1j * g.Q) ** 6
+             - (1j * g.Q) ** 4) * uh
+    nl = (-5.0 * uxxxx * ux - 10.0 * uxxx * uxx - 3.0 * uxx * ux + u0 * u0 * uxx
+          + u0 * ux * ux + (2.0 / T) * u0 * uxs + (1.0 / T) * ux * us)
+    return g.real_grid(lin_h + g.project(g.to_spectral(nl)))
+
+
+# ---------------------------------------------------------------------------------------
+# Batched helpers (a batch is a list of independent loops)
+# ---------------------------------------------------------------------------------------
+
+def residual_batch(us, Ts, L):
+    return [residual(u, T, L) for u, T in zip(us, Ts)]
+
+
+def adjoint_grad_batch(us, Ts, L):
+    return [adjoint_grad(u, T, L) for u, T in zip(us, Ts)]
+
+
+def descend_batch(us, Ts, L, dtau, scheme, nsteps, tol=0.0):
+    return [descend(u, T, L, dtau, scheme, nsteps, tol) for u, T in zip(us, Ts)]

@@ -1,0 +1,125 @@
+"""Seeded synthetic loops for the KS tau-descent workloads.
+
+This module only draws inputs; it holds none of the descent's arithmetic.  Both the CUDA
+path's tests/benchmarks and the CPU oracle's tests take their inputs from here.
+
+Recipe (per loop b, generator ``numpy.random.default_rng(seed_b)``, draws in this order):
+
+1. if the workload gives a set of N_s values, ``N_s = rng.choice(set)``;
+2. if the workload gives a period range, ``T0 = rng.uniform(lo, hi)``, else T0 is fixed;
+3. ``re, im = rng.standard_normal((Kx+1, 2Ks+1))`` twice, for the half-spectrum modes
+   j = 0..Kx, k = -Ks..Ks of the 2/3 band (Kx = N_x // 3, Ks = N_s // 3);
+4. coefficient c_jk = (re + i im) * exp(-|j| / d_x) * exp(-|k| / d_s); the j = 0 column is
+   set to zero (zero spatial mean); modes with j < 0 are the complex conjugates
+   c_{-j,-k} = conj(c_{j,k}) so the field is real;
+5. u(x_m, s_n) = sum_jk c_jk exp(2 pi i (m j / N_x + n k / N_s)), then u is scaled so that its
+   grid rms is 1.
+
+The loops are band limited by construction, so the 2/3-rule projection leaves them unchanged
+up to rounding.  The paper draws its initial loops from recurrences of a chaotic KS run
+(Sec. 4.3); these seeded spectral loops stand in for that data, which is not available.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    L: float
+    nx: int
+    ns: List[int]
+    T0: List[float]
+    u: List[np.ndarray]          # grid fields u[n, m], float64
+    scheme: int                  # 0 explicit, 1 IMEX
+    dtau: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def batch(self) -> int:
+        return len(self.ns)
+
+    @property
+    def gridpoints(self) -> int:
+        return int(sum(n * self.nx for n in self.ns))
+
+    def packed(self) -> np.ndarray:
+        """Ragged-packed [sum_b Ns_b * Nx] float64 array, loop-major, m fastest."""
+        return np.concatenate([a.reshape(-1) for a in self.u]) if self.u else np.zeros(0)
+
+
+def spectral_loop(seed: int, nx: int, L: float, ns: Optional[int] = None,
+                  ns_choices: Optional[Sequence[int]] = None, T0: Optional[float] = None,
+                  T_range: Optional[Tuple[float, float]] = None, decay=(2.0, 2.0),
+                  rms: float = 1.0):
+    """One seeded loop (u grid [Ns, Nx] float64, T0, Ns) following the module recipe."""
+    rng = np.random.default_rng(seed)
+    if ns_choices is not None:
+        ns = int(rng.choice(np.asarray(ns_choices)))
+    if ns is None:
+        raise ValueError("give ns or ns_choices")
+    if T_range is not None:
+        T = float(rng.uniform(T_range[0], T_range[1]))
+    else:
+        T = float(T0)
+    kx, ks = nx // 3, ns // 3
+    re = rng.standard_normal((kx + 1, 2 * ks + 1))
+    im = rng.standard_normal((kx + 1, 2 * ks + 1))
+    j = np.arange(kx + 1)
+    k = np.arange(-ks, ks + 1)
+    amp = np.exp(-j / decay[0])[:, None] * np.exp(-np.abs(k) / decay[1])[None, :]
+    c = (re + 1j * im) * amp
+    c[0, :] = 0.0
+    # real synthesis: u = 2 Re sum_{j>=1} sum_k c_jk e^{2 pi i (m j / Nx + n k / Ns)}
+    m = np.arange(nx)
+    n = np.arange(ns)
+    ex = np.exp(2j * np.pi * np.outer(j, m) / nx)          # [j, m]
+    es = np.exp(2j * np.pi * np.outer(n, k) / ns)          # [n, k]
+    u = 2.0 * (es @ c.T @ ex).real                          # [n, m]
+    s = float(np.sqrt(np.mean(u * u)))
+    if s > 0:
+        u *= rms / s
+    return u, T, ns
+
+
+def make_loops(name: str, nx: int, L: float, seeds: Sequence[int], *, ns=None, ns_choices=None,
+               T0=None, T_range=None, decay=(2.0, 2.0), scheme=1, dtau=0.15, meta=None):
+    us, Ts, nss = [], [], []
+    for sd in seeds:
+        u, T, n = spectral_loop(sd, nx, L, ns=ns, ns_choices=ns_choices, T0=T0,
+                                T_range=T_range, decay=decay)
+        us.append(u)
+        Ts.append(T)
+        nss.append(n)
+    return Workload(name, float(L), int(nx), nss, Ts, us, scheme, float(dtau), dict(meta or {}))
+
+
+# The five workloads: sizes, periods and init decay rates of the descent benchmarks.
+def workload(name: str, batch: Optional[int] = None) -> Workload:
+    if name == "single_32x32_explicit":
+        return make_loops(name, 32, 22.0, [0], ns=32, T0=40.0, scheme=0, dtau=1e-4,
+                          meta={"steps": 2000})
+    if name == "single_64x128_imex":
+        return make_loops(name, 64, 22.0, [0], ns=128, T_range=(20.0, 80.0), scheme=1,
+                          dtau=0.15, meta={"tol": 1e-10, "max_steps": 1_000_000})
+    if name == "batch16_64x64":
+        b = 16 if batch is None else batch
+        return make_loops(name, 64, 22.0, range(b), ns=64, T_range=(20.0, 80.0), scheme=1,
+                          dtau=0.15)
+    if name == "ragged256_64xNs":
+        b = 256 if batch is None else batch
+        return make_loops(name, 64, 22.0, range(b), ns_choices=(32, 64, 128, 256),
+                          T_range=(10.0, 100.0), scheme=1, dtau=0.15)
+    if name == "large8_256x1024":
+        b = 8 if batch is None else batch
+        return make_loops(name, 256, 100.0, range(b), ns=1024, T0=120.0, decay=(8.0, 8.0),
+                          scheme=1, dtau=0.15, meta={"switch_tol": 1e-5, "tol": 1e-10})
+    raise KeyError(name)
+
+
+WORKLOADS = ("single_32x32_explicit", "single_64x128_imex", "batch16_64x64",
+             "ragged256_64xNs", "large8_256x1024")
