@@ -1,0 +1,178 @@
+/*
+ * ks_loop.h - C ABI of the GB300 (sm_103a) tau-descent library for Kuramoto-Sivashinsky
+ * loops, after Azimi, Ashtari & Schneider, "Adjoint-based variational method for
+ * constructing periodic orbits of high-dimensional chaotic systems" (arXiv:2007.06427).
+ *
+ * A loop is l = [u(x, s); T]: a field on [0, L) x [0, 1), periodic in both directions, and a
+ * period T > 0 (Sec. 2, Eq. loop_def).  Its residual is r = -(1/T) u_s - u u_x - u_xx - u_xxxx
+ * (Sec. 4.1, Eq. KS_R), its cost J = int_0^1 int_0^L r^2 dx ds (Sec. 2, Eq. cost_function), and
+ * the loop flow is du/dtau = -L^dag_1, dT/dtau = -L^dag_2 with
+ * L^dag_1 = (1/T) r_s + u r_x - r_xx - r_xxxx and L^dag_2 = int int (1/T^2) u_s r dx ds
+ * (Sec. 4.1, Eq. KS_L_dagger and Eq. KS_G; App. B).  Fields are discretised with Nx x Ns Fourier
+ * modes on the uniform grid (m L / Nx, n / Ns) (Sec. 4.2, Eq. 2D_Fourier), derivatives are
+ * spectral, products are formed on the grid, and every product is truncated to the 2/3 band
+ * |j| <= Nx/3, |k| <= Ns/3 (Sec. 4.2).  One tau-step is IMEX Euler for u (the diagonal linear
+ * symbol Lambda_jk implicit) and explicit Euler for T (Sec. 4.2); an explicit Euler scheme is
+ * also provided.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every compute call runs on the GPU; there is no CPU path.  A call made without a usable
+ *    CUDA device returns KS_ERR_CUDA.
+ *  - A batch holds `batch` independent loops sharing L and Nx; loop b has its own Ns_b.
+ *  - Grid fields (u, r, G) are ragged-packed: loop b occupies Ns_b * Nx consecutive values,
+ *    laid out [n][m] with the x-index m fastest; loops follow one another in batch order.
+ *    Their element type is double for KS_FP64 and KS_MIXED handles and float for KS_FP32.
+ *  - Every input field is first projected onto the 2/3 band; all results are those of the
+ *    projected loop.
+ *  - T and the per-loop outputs are double arrays of length `batch` (steps: long long,
+ *    status: int).
+ *  - Pointers may be device pointers or ordinary host pointers; the library tells them apart
+ *    with cudaPointerGetAttributes and stages host buffers through its own device memory
+ *    (synchronising the stream before it returns).  The caller owns every buffer it passes.
+ *  - `stream` is a cudaStream_t (NULL for the legacy default stream).  Calls with device
+ *    buffers only are stream ordered; ks_descend always synchronises `stream` (it reads the
+ *    convergence state back between chunks).
+ *  - Return value: KS_OK (0) or a negative KS_ERR_* code; ks_last_error() gives a message
+ *    for the last failing call on the calling thread.  A handle is not thread safe: calls on
+ *    one handle must not overlap.
+ */
+#ifndef KS_LOOP_H
+#define KS_LOOP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(KS_BUILD_SO) && defined(__GNUC__)
+#define KS_API __attribute__((visibility("default")))
+#else
+#define KS_API
+#endif
+
+typedef struct ks_loop* ks_loop_t;
+
+/* arithmetic mode of a handle */
+enum {
+    KS_FP64 = 0,   /* every step in double */
+    KS_FP32 = 1,   /* every step in float; reductions finished in double; T in double */
+    KS_MIXED = 2   /* ks_descend: float steps until sqrt(J) <= switch_tol or the float descent
+                      stalls, then double steps to the end; other calls compute in double */
+};
+
+/* tau-integration scheme (Sec. 4.2) */
+enum {
+    KS_EXPLICIT = 0, /* u <- u - dtau * L^dag_1 r */
+    KS_IMEX = 1      /* (u' - u)/dtau = Lambda u' + (flow - Lambda u): the paper's scheme */
+};
+
+/* return codes */
+enum {
+    KS_OK = 0,
+    KS_ERR_ARG = -1,     /* bad argument: null pointer, size out of range, L <= 0, dtau <= 0 */
+    KS_ERR_CUDA = -2,    /* a CUDA runtime call failed, or no device */
+    KS_ERR_OOM = -3,     /* device allocation failed */
+    KS_ERR_TIMEOUT = -4, /* a bounded in-kernel wait gave up (persistent kernel) */
+    KS_ERR_STATE = -5    /* call needs a resident state that was never set */
+};
+
+/* per-loop outcome of a descent (status array) */
+enum {
+    KS_RUNNING = 0,   /* still descending */
+    KS_CONVERGED = 1, /* sqrt(J) < tol reached */
+    KS_STEP_CAP = 2,  /* max_steps taken without convergence */
+    KS_STALLED = 3,   /* double descent stopped making progress: a local minimum with J > 0 */
+    KS_DIVERGED = 4   /* J not finite or T <= 0 */
+};
+
+typedef struct {
+    double L;            /* domain length, > 0 */
+    int nx;              /* Nx: power of two, 8 <= Nx <= 1024 */
+    int batch;           /* number of loops, >= 1 */
+    const int* ns;       /* host array [batch]: Ns_b, power of two, 8 <= Ns_b <= 1024 */
+    int mode;            /* KS_FP64, KS_FP32 or KS_MIXED */
+    int scheme;          /* KS_EXPLICIT or KS_IMEX */
+    double dtau;         /* fictitious-time step, > 0 (the paper uses 0.15 with IMEX) */
+    double tol;          /* default sqrt(J) tolerance of ks_descend (used when its tol < 0) */
+    double switch_tol;   /* KS_MIXED: switch to double once sqrt(J) <= switch_tol */
+    long long max_steps; /* default step cap of ks_descend (used when its max_steps < 0) */
+    int chunk;           /* tau-steps between convergence read-backs in ks_descend (> 0) */
+    int autotune;        /* 0: default launch shapes; 1: time the candidates once at create */
+} ks_config;
+
+/* Create a handle: validates cfg, allocates the device workspace for the batch (band states,
+ * transform scratch, per-loop scalars) and uploads the twiddle tables.  The current CUDA
+ * device is used.  On success *out owns the workspace until ks_destroy. */
+KS_API int ks_loop_create(const ks_config* cfg, ks_loop_t* out);
+
+/* Release a handle and all of its device memory (NULL is accepted). */
+KS_API int ks_destroy(ks_loop_t h);
+
+/* Residual of each loop (Eq. KS_R) at [P u; T].
+ *   u  : in,  grid field (packed, mode element type)
+ *   T  : in,  double[batch]
+ *   r  : out, grid field, nullable
+ *   J  : out, double[batch]: J = int int r^2 (Eq. cost_function), nullable
+ * Does not touch the resident descent state. */
+KS_API int ks_residual(ks_loop_t h, const void* u, const double* T, void* r, double* J, void* stream);
+
+/* Adjoint gradient at [P u; T] (Eq. KS_L_dagger):
+ *   G    : out, grid field G = +L^dag_1 r (the ascent direction of the paper's flow)
+ *   dJdT : out, double[batch]: dJ/dT = 2 L^dag_2, nullable
+ * The exact gradient of J with respect to the grid values is (2 L / (Nx Ns_b)) G.
+ * Does not touch the resident descent state. */
+KS_API int ks_adjoint_grad(ks_loop_t h, const void* u, const double* T, void* G, double* dJdT,
+                    void* stream);
+
+/* Tau-descent of every loop from [P u; T] (Eq. KS_G integrated as in Sec. 4.2).
+ *   u, T     : in/out: initial loop, overwritten by the final one
+ *   max_steps: step cap per loop (< 0: the handle's default)
+ *   tol      : stop a loop when sqrt(J) < tol at the start of a step (< 0: the handle's)
+ *   steps    : out, long long[batch], steps taken (nullable)
+ *   sqrtJ    : out, double[batch], sqrt(J) of the final loop (nullable)
+ *   status   : out, int[batch], KS_CONVERGED / KS_STEP_CAP / KS_STALLED / KS_DIVERGED
+ *              (nullable)
+ * Loops are frozen individually when they converge or diverge; the call returns when every
+ * loop is frozen or has taken max_steps steps.  The final state also stays resident. */
+KS_API int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, double tol,
+               long long* steps, double* sqrtJ, int* status, void* stream);
+
+/* Resident state: load [P u; T] as the handle's descent state (status reset to running,
+ * step counters to zero). */
+KS_API int ks_set_state(ks_loop_t h, const void* u, const double* T, void* stream);
+
+/* Advance the resident state by nsteps tau-steps with no read-back (loops that converge
+ * below tol or diverge freeze on the device).  tol < 0: the handle's tol. */
+KS_API int ks_step(ks_loop_t h, long long nsteps, double tol, void* stream);
+
+/* Copy the resident state out: u (grid, nullable), T (nullable), and the per-loop step
+ * counters, sqrt(J) of the last evaluated state and status (each nullable). */
+KS_API int ks_get_state(ks_loop_t h, void* u, double* T, long long* steps, double* sqrtJ, int* status,
+                 void* stream);
+
+/* Per-kernel timing: while enabled, every kernel the handle launches is bracketed by two CUDA
+ * events on its launch stream and the elapsed time is accumulated per kernel kind (a name such
+ * as "cols_resid_f64").  Launches are always counted. */
+KS_API int ks_profile(ks_loop_t h, int enable);
+
+/* Read the profile: for up to n kinds, names (n x 48 chars, NUL terminated), accumulated
+ * milliseconds and launch counts; total_launches gets every launch since the last reset (all
+ * outputs nullable).  Synchronises on the recorded events.  reset != 0 clears the counters.
+ * Returns the number of kinds (>= 0) or a negative KS_ERR_* code. */
+KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long long* launches,
+                           long long* total_launches, int reset);
+
+/* Message for the last non-zero return on the calling thread ("" if none). */
+KS_API const char* ks_last_error(void);
+
+/* Library version string. */
+KS_API const char* ks_version(void);
+
+/* sizeof(ks_config) as compiled into the library (lets bindings check their struct layout). */
+KS_API unsigned long long ks_config_sizeof(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KS_LOOP_H */

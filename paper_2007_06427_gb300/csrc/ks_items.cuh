@@ -1,0 +1,594 @@
+// ks_items.cuh - per-CTA work items of one tau-step of the KS loop descent.
+//
+// One tau-step (Sec. 4.2 of the paper; steps listed in order):
+//   a1  u_x = i q_j u_hat (spectral derivative)
+//   a2  inverse 2-D transform of u_hat and (u_x)_hat to the grid
+//   a3  pointwise product u u_x
+//   a4  forward 2-D transform of the product, truncated to the 2/3 band
+//   a5  r_hat = (-i w_k / T + q_j^2 - q_j^4) u_hat - F[P(u u_x)]               (Eq. KS_R)
+//   a6  J = L sum |r_hat|^2 and L^dag_2 = (L/T^2) sum Re(conj(i w_k u_hat) r_hat)
+//   a7  r_x = inverse transform of i q_j r_hat
+//   a8  forward transform of u r_x, truncated
+//   a9  G_hat = (+i w_k / T + q_j^2 - q_j^4) r_hat + F[P(u r_x)] = L^dag_1 r    (Eq. KS_L_dagger)
+//   a10 u_hat -= dtau G_hat (explicit) or dtau G_hat / (1 - dtau Lambda_jk(T)) (IMEX, Sec. 4.2),
+//       T -= dtau L^dag_2 (explicit Euler)
+//
+// The 2-D transforms are split into x-passes (one grid row n at a time, length Nx) and
+// s-passes (one retained x-mode column j at a time, length Ns).  The band state lives in a
+// half spectrum j = 0..Kx, k = -Ks..Ks.  Between the passes the data sits in the "mixed"
+// array M[b][j][n] (x-mode j, time sample n).  A step is four phases, each a set of
+// independent CTA work items:
+//   ROW_NONLIN  (rows)    : M = v (u_hat s-inverted) -> u, u_x rows -> U grid, p = u u_x -> M = P
+//   COL_RESID   (columns) : M = P -> r_hat (a5), partial J / L^dag_2 (a6), M = s-inverse of i q r_hat
+//   ROW_ADJ     (rows)    : M = rho -> r_x rows, w = u r_x -> M = W
+//   COL_UPDATE  (columns) : M = W -> G_hat (a9), update (a10), M = s-inverse of the new u_hat
+// plus the analysis (grid -> band) and synthesis (band -> grid) items used at the boundary.
+//
+// Every loop inside an item is a CTA-strided loop separated by KS_SYNC(), so the source also
+// compiles as sequential host code (KS_HOST_EMULATION) for index checks.
+#pragma once
+
+#include <cstdint>
+#include <cmath>
+
+#ifdef KS_HOST_EMULATION
+#define KS_HD inline
+#define KS_TID 0
+#define KS_NT 1
+#define KS_SYNC() ((void)0)
+#else
+#define KS_HD __device__ __forceinline__
+#define KS_TID ((int)threadIdx.x)
+#define KS_NT ((int)blockDim.x)
+#define KS_SYNC() __syncthreads()
+#endif
+
+namespace ks {
+
+constexpr int NMAX = 1024;  // largest transform length (Nx and Ns)
+constexpr int LGNMAX = 10;
+
+// per-loop status values (match the public header)
+constexpr int ST_RUNNING = 0;
+constexpr int ST_CONVERGED = 1;
+constexpr int ST_STEP_CAP = 2;
+constexpr int ST_STALLED = 3;
+constexpr int ST_DIVERGED = 4;
+constexpr int ST_SWITCH = 5;  // internal: float phase reached the switch criterion
+
+template <typename R>
+struct cpx {
+    R x, y;
+};
+
+template <typename R>
+KS_HD cpx<R> mk(R a, R b) {
+    cpx<R> c;
+    c.x = a;
+    c.y = b;
+    return c;
+}
+template <typename R>
+KS_HD cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R>
+KS_HD cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R>
+KS_HD cpx<R> cmul(cpx<R> a, cpx<R> b) {
+    return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R>
+KS_HD cpx<R> conj(cpx<R> a) { return mk<R>(a.x, -a.y); }
+template <typename R>
+KS_HD cpx<R> scale(cpx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+// multiply by i*sgn (sgn = +1 or -1)
+template <typename R>
+KS_HD cpx<R> mul_i(cpx<R> a, int sgn) { return sgn > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
+
+struct RowItem {
+    int b, n0, nr, pad;  // loop, first row, rows in the tile (even)
+};
+
+// Shape of the batch (shared by all loops of a handle).
+struct Dims {
+    int B;         // loops
+    int nx, lgnx;  // Nx = 2^lgnx
+    int kx, nkx;   // Kx = Nx / 3, nkx = Kx + 1 retained x-modes (half spectrum)
+    double L;
+    double dtau;
+    int scheme;    // 0 explicit, 1 IMEX
+};
+
+// Device buffers of one precision, plus the per-loop scalars (always double / int).
+template <typename R>
+struct Bufs {
+    const int* ns;          // [B] Ns_b
+    const int* lgns;        // [B] log2 Ns_b
+    const int* ks;          // [B] Ks_b = Ns_b / 3
+    const long long* boff;  // [B] band offset (complex elements); band is [j][kk], kk = k + Ks
+    const long long* moff;  // [B] mixed-array offset (complex elements); [j][n]
+    const long long* goff;  // [B] grid offset (real elements); [n][m]
+    cpx<R>* uh;             // band state u_hat
+    cpx<R>* rh;             // band residual r_hat
+    cpx<R>* gh;             // band adjoint G_hat (gradient calls only)
+    cpx<R>* M;              // mixed array
+    R* U;                   // grid u (kept from ROW_NONLIN for ROW_ADJ)
+    R* io;                  // grid in/out for analysis / synthesis items
+    double* T;              // [2][B] period, double-buffered by step parity
+    double* Jpart;          // [B][nkx] per-column partial of sum w_j |r_hat|^2
+    double* L2part;         // [B][nkx] per-column partial of sum w_j w_k Im(conj(u_hat) r_hat)
+    int* status;            // [B]
+    const int* prec;        // [B] 0 double, 1 float: the precision the loop currently runs in
+    long long* steps;       // [B]
+    double* sqrtJ;          // [B]
+    const cpx<R>* tw;       // [NMAX] exp(+2 pi i t / NMAX)
+    const R* qv;            // [nkx] q_j = 2 pi j / L in this precision
+    const RowItem* rows;    // row work items
+    const int* colorder;    // loop order of the column items (longest Ns first)
+    int myprec;             // precision of this kernel set
+    int par;                // step parity: T read from T[par], written to T[par ^ 1]
+    double tol;             // freeze a loop once sqrt(J) < tol
+    double switch_tol;      // float phase of a mixed descent: freeze as ST_SWITCH once sqrt(J) <= switch_tol
+    int check_active;       // 1: skip loops that are not running in this precision
+};
+
+// ------------------------------------------------------------------------------------
+// Batched Stockham FFT in shared memory.
+// `cnt` transforms of length n = 2^lg, stored contiguously (stride n) in `a`; `b` is scratch
+// of the same size.  dir = -1: X_k = sum_m x_m e^{-2 pi i m k / n}; dir = +1: e^{+...}.
+// No scaling.  Radix-4 passes (one radix-2 pass first when lg is odd); natural order in and
+// out.  Returns the buffer holding the result (a or b).  The caller synchronises before the
+// call; the function synchronises after every pass.
+// ------------------------------------------------------------------------------------
+template <typename R>
+KS_HD cpx<R> twid(const cpx<R>* tw, int t, int dir) {
+    cpx<R> w = tw[t];
+    if (dir < 0) w.y = -w.y;
+    return w;
+}
+
+template <typename R>
+KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw) {
+    const int n = 1 << lg;
+    int span = 1;  // size of the sub-transforms completed so far
+    int p = lg;
+    if (p & 1) {
+        // radix-2 pass with span 1: no twiddles
+        const int nb = n >> 1;
+        const int total = cnt * nb;
+        for (int i = KS_TID; i < total; i += KS_NT) {
+            const int f = i >> (lg - 1);
+            const int j = i & (nb - 1);
+            const cpx<R>* s = a + (size_t)f * n;
+            cpx<R>* d = b + (size_t)f * n;
+            const cpx<R> v0 = s[j], v1 = s[j + nb];
+            d[2 * j] = v0 + v1;
+            d[2 * j + 1] = v0 - v1;
+        }
+        KS_SYNC();
+        cpx<R>* t = a;
+        a = b;
+        b = t;
+        span = 2;
+        p -= 1;
+    }
+    while (p > 0) {
+        const int nb = n >> 2;
+        const int total = cnt * nb;
+        const int tu = NMAX / (span * 4);
+        for (int i = KS_TID; i < total; i += KS_NT) {
+            const int f = i >> (lg - 2);
+            const int j = i & (nb - 1);
+            const cpx<R>* s = a + (size_t)f * n;
+            cpx<R>* d = b + (size_t)f * n;
+            cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+            const int jm = j & (span - 1);
+            if (span > 1) {
+                const int t = jm * tu;
+                v1 = cmul(v1, twid(tw, t, dir));
+                v2 = cmul(v2, twid(tw, 2 * t, dir));
+                v3 = cmul(v3, twid(tw, 3 * t, dir));
+            }
+            const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
+            const cpx<R> t3 = mul_i(v1 - v3, dir);
+            const int od = ((j - jm) << 2) + jm;
+            d[od] = t0 + t2;
+            d[od + span] = t1 + t3;
+            d[od + 2 * span] = t0 - t2;
+            d[od + 3 * span] = t1 - t3;
+        }
+        KS_SYNC();
+        cpx<R>* t = a;
+        a = b;
+        b = t;
+        span <<= 2;
+        p -= 2;
+    }
+    return a;
+}
+
+// Block-wide sum of two doubles per thread; red has room for 2 * KS_NT doubles.  The result
+// is valid in every thread after the call.
+KS_HD void block_sum2(double* red, double& s0, double& s1) {
+    const int t = KS_TID, nt = KS_NT;
+    red[t] = s0;
+    red[nt + t] = s1;
+    KS_SYNC();
+    if (t == 0) {
+        double a = 0.0, c = 0.0;
+        for (int i = 0; i < nt; ++i) {
+            a += red[i];
+            c += red[nt + i];
+        }
+        red[2 * nt] = a;
+        red[2 * nt + 1] = c;
+    }
+    KS_SYNC();
+    s0 = red[2 * nt];
+    s1 = red[2 * nt + 1];
+    KS_SYNC();
+}
+
+KS_HD double qj(const Dims& d, int j) { return 2.0 * 3.14159265358979323846 * (double)j / d.L; }
+
+// is the loop processed by this kernel set?
+template <typename R>
+KS_HD bool loop_live(const Bufs<R>& p, int b) {
+    if (!p.check_active) return true;
+    return p.prec[b] == p.myprec && p.status[b] == ST_RUNNING;
+}
+
+// ------------------------------------------------------------------------------------
+// Row items (x-direction work on a tile of rows of one loop)
+// ------------------------------------------------------------------------------------
+enum RowMode { ROW_ANALYZE = 0, ROW_NONLIN = 1, ROW_ADJ = 2, ROW_SYNTH = 3 };
+
+// Fill A[pair][J] (J in [0, Nx)) with the Hermitian-extended spectra of two rows (a = 2*pair,
+// b = 2*pair + 1) read from M: Z_J = X^a_J + i X^b_J with X_{-j} = conj(X_j).  `mulq` = 1
+// multiplies X_j by i q_j first (x-derivative).
+template <typename R>
+KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, int npairs,
+                             cpx<R>* A, bool mulq, const R* p_qv) {
+    const int nx = d.nx, kx = d.kx;
+    const int total = npairs * nx;
+    for (int i = KS_TID; i < total; i += KS_NT) {
+        const int J = i / npairs;
+        const int pr = i - J * npairs;
+        cpx<R> z = mk<R>(0, 0);
+        int j = -1;
+        bool neg = false;
+        if (J <= kx) {
+            j = J;
+        } else if (J >= nx - kx) {
+            j = nx - J;
+            neg = true;
+        }
+        if (j >= 0) {
+            const cpx<R>* col = Mb + (size_t)j * ns + n0 + 2 * pr;
+            cpx<R> xa = col[0], xb = col[1];
+            if (mulq) {
+                const R q = p_qv[j];
+                xa = mk<R>(-q * xa.y, q * xa.x);
+                xb = mk<R>(-q * xb.y, q * xb.x);
+            }
+            if (neg) {
+                xa = conj(xa);
+                xb = conj(xb);
+            }
+            z = xa + mul_i(xb, 1);
+        }
+        A[(size_t)pr * nx + J] = z;
+    }
+}
+
+// From Y = FFT(y_a + i y_b) (forward, unscaled) extract the half spectra of the two real rows,
+// scaled by 1/Nx, for j = 0..Kx, and store them to M[j][n0 + 2 pr + {0,1}].
+template <typename R>
+KS_HD void store_pair_spectra(const Dims& d, const cpx<R>* Y, cpx<R>* Mb, int ns, int n0,
+                              int npairs) {
+    const int nx = d.nx;
+    const R h = (R)(0.5 / (double)nx);
+    const int total = npairs * d.nkx;
+    for (int i = KS_TID; i < total; i += KS_NT) {
+        const int j = i / npairs;
+        const int pr = i - j * npairs;
+        const cpx<R> yj = Y[(size_t)pr * nx + j];
+        const cpx<R> ym = conj(Y[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
+        const cpx<R> s = yj + ym;   // 2 X^a
+        const cpx<R> df = yj - ym;  // 2 i X^b
+        cpx<R>* col = Mb + (size_t)j * ns + n0 + 2 * pr;
+        col[0] = scale(s, h);
+        col[1] = mk<R>(df.y * h, -df.x * h);
+    }
+}
+
+template <typename R, int MODE>
+KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem) {
+    const RowItem it = p.rows[item];
+    const int b = it.b;
+    if constexpr (MODE == ROW_NONLIN || MODE == ROW_ADJ) {
+        if (!loop_live(p, b)) return;
+    }
+    const int nx = d.nx, lgnx = d.lgnx, kx = d.kx;
+    const int ns = p.ns[b];
+    const int n0 = it.n0, nr = it.nr, npairs = nr >> 1;
+    cpx<R>* A = reinterpret_cast<cpx<R>*>(smem);
+    cpx<R>* Bf = A + (size_t)nr * nx;
+    cpx<R>* Mb = p.M + p.moff[b];
+    R* Ub = p.U + p.goff[b];
+    R* Ib = p.io ? p.io + p.goff[b] : nullptr;
+
+    if constexpr (MODE == ROW_ANALYZE) {
+        // y = u_a + i u_b for each row pair, forward transform, split
+        const int total = npairs * nx;
+        for (int i = KS_TID; i < total; i += KS_NT) {
+            const int pr = i >> lgnx;
+            const int m = i & (nx - 1);
+            const R* ra = Ib + (size_t)(n0 + 2 * pr) * nx;
+            A[i] = mk<R>(ra[m], ra[nx + m]);
+        }
+        KS_SYNC();
+        cpx<R>* Y = fft_batch(A, Bf, lgnx, npairs, -1, p.tw);
+        store_pair_spectra(d, Y, Mb, ns, n0, npairs);
+        KS_SYNC();
+        return;
+    }
+    if constexpr (MODE == ROW_SYNTH) {
+        load_pair_spectra(d, Mb, ns, n0, npairs, A, false, p.qv);
+        KS_SYNC();
+        cpx<R>* z = fft_batch(A, Bf, lgnx, npairs, +1, p.tw);
+        const int total = npairs * nx;
+        for (int i = KS_TID; i < total; i += KS_NT) {
+            const int pr = i >> lgnx;
+            const int m = i & (nx - 1);
+            R* ra = Ib + (size_t)(n0 + 2 * pr) * nx;
+            ra[m] = z[i].x;
+            ra[nx + m] = z[i].y;
+        }
+        KS_SYNC();
+        return;
+    }
+    if constexpr (MODE == ROW_NONLIN) {
+        // z = u + i u_x per row: Z_j = (1 - q_j) v_j, Z_{-j} = (1 + q_j) conj(v_j)   (a1, a2)
+        const int total = nr * nx;
+        for (int i = KS_TID; i < total; i += KS_NT) {
+            const int J = i / nr;
+            const int r = i - J * nr;
+            cpx<R> z = mk<R>(0, 0);
+            if (J <= kx) {
+                const R q = p.qv[J];
+                z = scale(Mb[(size_t)J * ns + n0 + r], (R)1 - q);
+            } else if (J >= nx - kx) {
+                const int j = nx - J;
+                const R q = p.qv[j];
+                z = scale(conj(Mb[(size_t)j * ns + n0 + r]), (R)1 + q);
+            }
+            A[(size_t)r * nx + J] = z;
+        }
+        KS_SYNC();
+        cpx<R>* z = fft_batch(A, Bf, lgnx, nr, +1, p.tw);
+        cpx<R>* Y = (z == A) ? Bf : A;
+        // keep u, form p = u u_x for the row pairs (a3)
+        const int tp = npairs * nx;
+        for (int i = KS_TID; i < tp; i += KS_NT) {
+            const int pr = i >> lgnx;
+            const int m = i & (nx - 1);
+            const cpx<R> za = z[(size_t)(2 * pr) * nx + m];
+            const cpx<R> zb = z[(size_t)(2 * pr + 1) * nx + m];
+            R* ua = Ub + (size_t)(n0 + 2 * pr) * nx;
+            ua[m] = za.x;
+            ua[nx + m] = zb.x;
+            Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
+        }
+        KS_SYNC();
+        cpx<R>* F = fft_batch(Y, z, lgnx, npairs, -1, p.tw);  // a4 (x-pass)
+        store_pair_spectra(d, F, Mb, ns, n0, npairs);
+        KS_SYNC();
+        return;
+    }
+    if constexpr (MODE == ROW_ADJ) {
+        // r_x rows from i q_j rho_j (rho already carries i q_j from the column pass)  (a7)
+        load_pair_spectra(d, Mb, ns, n0, npairs, A, false, p.qv);
+        KS_SYNC();
+        cpx<R>* z = fft_batch(A, Bf, lgnx, npairs, +1, p.tw);
+        cpx<R>* Y = (z == A) ? Bf : A;
+        const int tp = npairs * nx;
+        for (int i = KS_TID; i < tp; i += KS_NT) {
+            const int pr = i >> lgnx;
+            const int m = i & (nx - 1);
+            const R* ua = Ub + (size_t)(n0 + 2 * pr) * nx;
+            const cpx<R> rx = z[i];
+            Y[i] = mk<R>(ua[m] * rx.x, ua[nx + m] * rx.y);  // w = u r_x  (a8)
+        }
+        KS_SYNC();
+        cpx<R>* F = fft_batch(Y, z, lgnx, npairs, -1, p.tw);
+        store_pair_spectra(d, F, Mb, ns, n0, npairs);
+        KS_SYNC();
+        return;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Column items (s-direction work on one retained x-mode j of one loop)
+// ------------------------------------------------------------------------------------
+enum ColMode {
+    COL_ANALYZE = 0,  // M -> band u_hat (forward, 1/Ns, truncate)
+    COL_SYNTH_U = 1,  // band u_hat -> M (inverse)
+    COL_SYNTH_R = 2,  // band r_hat -> M
+    COL_SYNTH_G = 3,  // band G_hat -> M
+    COL_RESID = 4,    // M = P -> r_hat, partials, M = s-inverse of i q r_hat
+    COL_UPDATE = 5,   // M = W -> G_hat, update u_hat and T, M = s-inverse of new u_hat
+    COL_GRAD = 6      // M = W -> G_hat band (no update)
+};
+
+template <typename R, int MODE>
+KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem) {
+    const int nkx = d.nkx;
+    const int b = p.colorder[item / nkx];
+    const int j = item - (item / nkx) * nkx;
+    const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b];
+    const int nk = 2 * ks + 1;
+    cpx<R>* A = reinterpret_cast<cpx<R>*>(smem);
+    cpx<R>* Bf = A + ns;
+    double* red = reinterpret_cast<double*>(Bf + ns);
+    cpx<R>* col = p.M + p.moff[b] + (size_t)j * ns;
+    const size_t bo = (size_t)p.boff[b] + (size_t)j * nk;
+    const int B = d.B;
+    const double* Tc = p.T + (size_t)p.par * B;
+    double* Tn = p.T + (size_t)(p.par ^ 1) * B;
+
+    if constexpr (MODE == COL_RESID || MODE == COL_GRAD) {
+        if (!loop_live(p, b)) return;
+    }
+    if constexpr (MODE == COL_UPDATE) {
+        if (p.check_active && p.prec[b] != p.myprec) return;
+        if (p.check_active && p.status[b] != ST_RUNNING) {
+            if (j == 0 && KS_TID == 0) Tn[b] = Tc[b];
+            return;
+        }
+    }
+
+    if constexpr (MODE == COL_SYNTH_U || MODE == COL_SYNTH_R || MODE == COL_SYNTH_G) {
+        const cpx<R>* src = (MODE == COL_SYNTH_U) ? p.uh : (MODE == COL_SYNTH_R) ? p.rh : p.gh;
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            const int k = (i < (ns >> 1)) ? i : i - ns;
+            A[i] = (k >= -ks && k <= ks) ? src[bo + (k + ks)] : mk<R>(0, 0);
+        }
+        KS_SYNC();
+        cpx<R>* v = fft_batch(A, Bf, lg, 1, +1, p.tw);
+        for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
+        KS_SYNC();
+        return;
+    } else {
+        // the remaining modes start with a forward s-transform of the column of M
+        for (int i = KS_TID; i < ns; i += KS_NT) A[i] = col[i];
+        KS_SYNC();
+        cpx<R>* F = fft_batch(A, Bf, lg, 1, -1, p.tw);
+        cpx<R>* X = (F == A) ? Bf : A;
+        const R ins = (R)(1.0 / (double)ns);
+
+        if constexpr (MODE == COL_ANALYZE) {
+            for (int kk = KS_TID; kk < nk; kk += KS_NT) {
+                const int k = kk - ks;
+                p.uh[bo + kk] = scale(F[k & (ns - 1)], ins);
+            }
+            KS_SYNC();
+            return;
+        }
+
+        const double T = Tc[b];
+        const double q = qj(d, j);
+        const R a_lin = (R)(q * q - q * q * q * q);   // q^2 - q^4 (from -u_xx - u_xxxx)
+        const R w_over_T = (R)(2.0 * 3.14159265358979323846 / T);  // omega_k / T = k * (2 pi / T)
+        const R rq = (R)q;
+        const double wj = (j == 0) ? 1.0 : 2.0;      // x-conjugate pairs counted twice
+
+        if constexpr (MODE == COL_RESID) {
+            double sJ = 0.0, sL = 0.0;
+            R pJ = 0, pL = 0;
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                const int k = (i < (ns >> 1)) ? i : i - ns;
+                cpx<R> x = mk<R>(0, 0);
+                if (k >= -ks && k <= ks) {
+                    const cpx<R> ph = scale(F[i], ins);
+                    const cpx<R> u = p.uh[bo + (k + ks)];
+                    const R bk = -(R)k * w_over_T;            // -omega_k / T
+                    // r_hat = (a + i bk) u_hat - p_hat                                    (a5)
+                    const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
+                    p.rh[bo + (k + ks)] = r;
+                    pJ += r.x * r.x + r.y * r.y;              // a6
+                    pL += (R)k * (u.x * r.y - u.y * r.x);      // omega_k Im(conj(u) r) / (2 pi)
+                    x = mk<R>(-rq * r.y, rq * r.x);           // i q_j r_hat                 (a7)
+                }
+                X[i] = x;
+            }
+            sJ = (double)pJ;
+            sL = (double)pL;
+            KS_SYNC();
+            cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
+            for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
+            block_sum2(red, sJ, sL);
+            if (KS_TID == 0) {
+                p.Jpart[(size_t)b * nkx + j] = wj * sJ;
+                p.L2part[(size_t)b * nkx + j] = wj * sL;
+            }
+            KS_SYNC();
+            return;
+        }
+
+        if constexpr (MODE == COL_GRAD) {
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                const int k = (i < (ns >> 1)) ? i : i - ns;
+                if (k >= -ks && k <= ks) {
+                    const cpx<R> wh = scale(F[i], ins);
+                    const cpx<R> r = p.rh[bo + (k + ks)];
+                    const R bk = (R)k * w_over_T;             // +omega_k / T
+                    p.gh[bo + (k + ks)] = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                }
+            }
+            KS_SYNC();
+            return;
+        }
+
+        if constexpr (MODE == COL_UPDATE) {
+            // J and L^dag_2 of this loop from the column partials (same fixed order in every CTA)
+            double J = 0.0, L2 = 0.0;
+            const double* jp = p.Jpart + (size_t)b * nkx;
+            const double* lp = p.L2part + (size_t)b * nkx;
+            for (int c = 0; c < nkx; ++c) {
+                J += jp[c];
+                L2 += lp[c];
+            }
+            J *= d.L;
+            L2 *= d.L * 2.0 * 3.14159265358979323846 / (T * T);
+            const double sq = sqrt(J);
+            int st = ST_RUNNING;
+            if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
+            else if (sq < p.tol) st = ST_CONVERGED;
+            else if (p.myprec == 1 && p.switch_tol > 0.0 && sq <= p.switch_tol) st = ST_SWITCH;
+            if (j == 0 && KS_TID == 0) p.sqrtJ[b] = sq;
+            if (st != ST_RUNNING) {
+                if (j == 0 && KS_TID == 0) {
+                    p.status[b] = st;
+                    Tn[b] = T;
+                }
+                return;
+            }
+            const R dt = (R)d.dtau;
+            const double cq = q * q * q * q * (q * q - 1.0) * (q * q - 1.0);  // q^4 (q^2 - 1)^2
+            const R wT2 = w_over_T * w_over_T;
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                const int k = (i < (ns >> 1)) ? i : i - ns;
+                cpx<R> x = mk<R>(0, 0);
+                if (k >= -ks && k <= ks) {
+                    const cpx<R> wh = scale(F[i], ins);
+                    const cpx<R> r = p.rh[bo + (k + ks)];
+                    const R bk = (R)k * w_over_T;
+                    // G_hat = (a + i omega/T) r_hat + F[P(u r_x)]                          (a9)
+                    const cpx<R> G = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    R f = dt;
+                    if (d.scheme == 1) {
+                        // IMEX: dtau / (1 - dtau Lambda), Lambda = -(omega/T)^2 - q^4 (q^2-1)^2  (a10)
+                        const R kk2 = (R)k * (R)k;
+                        f = dt / ((R)1 + dt * (kk2 * wT2 + (R)cq));
+                    }
+                    cpx<R> u = p.uh[bo + (k + ks)];
+                    u = u - scale(G, f);
+                    p.uh[bo + (k + ks)] = u;
+                    x = u;
+                }
+                X[i] = x;
+            }
+            KS_SYNC();
+            cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
+            for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
+            if (j == 0 && KS_TID == 0) {
+                Tn[b] = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
+                p.steps[b] += 1;
+            }
+            KS_SYNC();
+            return;
+        }
+    }
+}
+
+}  // namespace ks

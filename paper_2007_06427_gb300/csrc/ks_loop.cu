@@ -1,0 +1,1069 @@
+// ks_loop.cu - kernels and C-ABI of the KS loop tau-descent library (sm_103a).
+//
+// The kernels wrap the per-CTA items of ks_items.cuh: every launch runs one phase of a
+// tau-step over all work items of the batch.  The host side owns the handle (device
+// workspace, tables, launch shapes) and sequences the phases for the public calls declared
+// in include/ks_loop.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ks_items.cuh"
+#include "ks_loop.h"
+
+using namespace ks;
+
+#define KS_VERSION_STRING "ks_loop 0.1 (sm_103a)"
+
+// ------------------------------------------------------------------------------------------
+// Kernels
+// ------------------------------------------------------------------------------------------
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_rows(Dims d, Bufs<R> p, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) row_item<R, MODE>(d, p, it, smem);
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_cols(Dims d, Bufs<R> p, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) col_item<R, MODE>(d, p, it, smem);
+}
+
+// J = L sum_j Jpart, dJ/dT = 2 L^dag_2 = 2 (2 pi L / T^2) sum_j L2part, per loop.
+// only loops with prec[b] == myprec are written when mask != 0.
+__global__ void k_finalize(int B, int nkx, double L, const double* Jpart, const double* L2part,
+                           const double* T, const int* prec, int myprec, int mask, double* J,
+                           double* dJdT, double* sqrtJ) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (mask && prec[b] != myprec) return;
+    double sj = 0.0, sl = 0.0;
+    for (int c = 0; c < nkx; ++c) {
+        sj += Jpart[(size_t)b * nkx + c];
+        sl += L2part[(size_t)b * nkx + c];
+    }
+    const double Tb = T[b];
+    const double Jb = L * sj;
+    if (J) J[b] = Jb;
+    if (dJdT) dJdT[b] = 2.0 * L * 2.0 * 3.14159265358979323846 * sl / (Tb * Tb);
+    if (sqrtJ) sqrtJ[b] = sqrt(Jb);
+}
+
+// float band -> double band for the loops flagged in sel[b] (mixed-precision switch).
+__global__ void k_band_f2d(const cpx<float>* src, cpx<double>* dst, const long long* boff,
+                           const int* sel, int B, int nkx, const int* ks) {
+    const int b = blockIdx.y;
+    if (b >= B || !sel[b]) return;
+    const long long n = (long long)nkx * (2 * ks[b] + 1);
+    const long long o = boff[b];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cpx<float> v = src[o + i];
+        dst[o + i] = mk<double>((double)v.x, (double)v.y);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Error reporting
+// ------------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define KS_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? KS_ERR_OOM : KS_ERR_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+#define KS_TRY(expr)                \
+    do {                            \
+        int rc_ = (expr);           \
+        if (rc_ != KS_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// Handle
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int P64 = 0, P32 = 1;
+
+struct Work {
+    void* uh[2] = {nullptr, nullptr};
+    void* rh[2] = {nullptr, nullptr};
+    void* gh[2] = {nullptr, nullptr};
+    void* M[2] = {nullptr, nullptr};
+    void* U[2] = {nullptr, nullptr};
+    void* io[2] = {nullptr, nullptr};
+    double* T = nullptr;       // [2][B]
+    double* Jpart = nullptr;   // [B][nkx]
+    double* L2part = nullptr;  // [B][nkx]
+    int* status = nullptr;
+    int* prec = nullptr;
+    long long* steps = nullptr;
+    double* sqrtJ = nullptr;
+    double* J = nullptr;       // [B] finalize outputs
+    double* dJdT = nullptr;    // [B]
+    int* sel = nullptr;        // [B] selection flags (switch)
+    int par = 0;
+    bool mix_valid[2] = {false, false};
+};
+
+struct Launch {
+    int threads = 128;
+    int grid = 0;
+    size_t smem = 0;
+};
+
+}  // namespace
+
+struct ks_loop {
+    int dev = 0;
+    Dims d{};
+    int mode = KS_FP64;
+    double tol = 1e-10, switch_tol = 0.0;
+    long long max_steps = 1000000;
+    int chunk = 1000;
+    int autotune = 0;
+    long long stall_window = 20000;
+    double stall_drop = 1e-3;
+    std::vector<int> ns, lgns, ksv;
+    std::vector<long long> boff, moff, goff;
+    long long nband = 0, nmix = 0, ngrid = 0;
+    int nsmax = 0;
+    int rows_per_tile = 8;
+    std::vector<RowItem> rows;
+    std::vector<int> colorder;
+    bool need[2] = {false, false};  // precisions allocated for the state workspace
+    int api_prec = P64;
+    // device tables
+    int *d_ns = nullptr, *d_lgns = nullptr, *d_ks = nullptr, *d_colorder = nullptr;
+    long long *d_boff = nullptr, *d_moff = nullptr, *d_goff = nullptr;
+    RowItem* d_rows = nullptr;
+    void* d_tw[2] = {nullptr, nullptr};
+    void* d_qv[2] = {nullptr, nullptr};
+    Work st;   // resident descent state
+    Work api;  // scratch for ks_residual / ks_adjoint_grad
+    Launch lrow[2], lcol[2];
+    bool state_set = false;
+    std::vector<void*> allocs;
+    // profiling: per-kind event pairs around every launch when enabled
+    bool prof = false;
+    long long launches = 0;
+    std::vector<std::string> kind_names;
+    std::vector<double> kind_ms;
+    std::vector<long long> kind_count;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    // host mirrors
+    std::vector<int> h_status, h_prec;
+    std::vector<double> h_sqrtJ;
+    std::vector<long long> h_steps;
+};
+
+namespace {
+
+int dev_alloc(ks_loop* h, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? KS_ERR_OOM : KS_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*p);
+    return KS_OK;
+}
+
+template <typename T>
+int upload(ks_loop* h, T** dptr, const std::vector<T>& v) {
+    void* p = nullptr;
+    KS_TRY(dev_alloc(h, &p, v.size() * sizeof(T)));
+    if (!v.empty()) KS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dptr = reinterpret_cast<T*>(p);
+    return KS_OK;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// exp(2 pi i t / NMAX) with octant symmetry so that the table is exactly symmetric.
+void twiddles(std::vector<double>& re, std::vector<double>& im) {
+    const int N = NMAX;
+    re.assign(N, 0.0);
+    im.assign(N, 0.0);
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<double> c(N / 4 + 1), s(N / 4 + 1);
+    for (int t = 0; t <= N / 8; ++t) {
+        c[t] = std::cos(two_pi * t / N);
+        s[t] = std::sin(two_pi * t / N);
+    }
+    for (int t = N / 8 + 1; t <= N / 4; ++t) {
+        c[t] = s[N / 4 - t];
+        s[t] = c[N / 4 - t];
+    }
+    for (int t = 0; t < N; ++t) {
+        const int qd = t / (N / 4), r = t % (N / 4);
+        double a = c[r], b = s[r];
+        switch (qd) {
+            case 0: re[t] = a; im[t] = b; break;
+            case 1: re[t] = -b; im[t] = a; break;
+            case 2: re[t] = -a; im[t] = -b; break;
+            default: re[t] = b; im[t] = -a; break;
+        }
+    }
+}
+
+int alloc_work(ks_loop* h, Work& w, const bool* precs) {
+    const int B = h->d.B;
+    for (int pr = 0; pr < 2; ++pr) {
+        if (!precs[pr]) continue;
+        const size_t cs = pr == P64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+        const size_t rs = pr == P64 ? sizeof(double) : sizeof(float);
+        KS_TRY(dev_alloc(h, &w.uh[pr], h->nband * cs));
+        KS_TRY(dev_alloc(h, &w.rh[pr], h->nband * cs));
+        KS_TRY(dev_alloc(h, &w.gh[pr], h->nband * cs));
+        KS_TRY(dev_alloc(h, &w.M[pr], h->nmix * cs));
+        KS_TRY(dev_alloc(h, &w.U[pr], h->ngrid * rs));
+        KS_TRY(dev_alloc(h, &w.io[pr], h->ngrid * rs));
+        KS_CUDA(cudaMemset(w.uh[pr], 0, h->nband * cs));
+        KS_CUDA(cudaMemset(w.rh[pr], 0, h->nband * cs));
+        KS_CUDA(cudaMemset(w.gh[pr], 0, h->nband * cs));
+    }
+    void* p = nullptr;
+    KS_TRY(dev_alloc(h, &p, 2 * B * sizeof(double)));
+    w.T = (double*)p;
+    KS_TRY(dev_alloc(h, &p, (size_t)B * h->d.nkx * sizeof(double)));
+    w.Jpart = (double*)p;
+    KS_TRY(dev_alloc(h, &p, (size_t)B * h->d.nkx * sizeof(double)));
+    w.L2part = (double*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(int)));
+    w.status = (int*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(int)));
+    w.prec = (int*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(long long)));
+    w.steps = (long long*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(double)));
+    w.sqrtJ = (double*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(double)));
+    w.J = (double*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(double)));
+    w.dJdT = (double*)p;
+    KS_TRY(dev_alloc(h, &p, B * sizeof(int)));
+    w.sel = (int*)p;
+    KS_CUDA(cudaMemset(w.status, 0, B * sizeof(int)));
+    KS_CUDA(cudaMemset(w.steps, 0, B * sizeof(long long)));
+    KS_CUDA(cudaMemset(w.sqrtJ, 0, B * sizeof(double)));
+    KS_CUDA(cudaMemset(w.T, 0, 2 * B * sizeof(double)));
+    return KS_OK;
+}
+
+template <typename R>
+Bufs<R> make_bufs(ks_loop* h, const Work& w, int pr, int check_active, double tol,
+                  double switch_tol, R* io) {
+    Bufs<R> p{};
+    p.ns = h->d_ns;
+    p.lgns = h->d_lgns;
+    p.ks = h->d_ks;
+    p.boff = h->d_boff;
+    p.moff = h->d_moff;
+    p.goff = h->d_goff;
+    p.uh = (cpx<R>*)w.uh[pr];
+    p.rh = (cpx<R>*)w.rh[pr];
+    p.gh = (cpx<R>*)w.gh[pr];
+    p.M = (cpx<R>*)w.M[pr];
+    p.U = (R*)w.U[pr];
+    p.io = io;
+    p.T = w.T;
+    p.Jpart = w.Jpart;
+    p.L2part = w.L2part;
+    p.status = w.status;
+    p.prec = w.prec;
+    p.steps = w.steps;
+    p.sqrtJ = w.sqrtJ;
+    p.tw = (const cpx<R>*)h->d_tw[pr];
+    p.qv = (const R*)h->d_qv[pr];
+    p.rows = h->d_rows;
+    p.colorder = h->d_colorder;
+    p.myprec = pr;
+    p.par = w.par;
+    p.tol = tol;
+    p.switch_tol = switch_tol;
+    p.check_active = check_active;
+    return p;
+}
+
+const char* const kRowNames[] = {"rows_analyze", "rows_nonlin", "rows_adj", "rows_synth"};
+const char* const kColNames[] = {"cols_analyze", "cols_synth_u", "cols_synth_r", "cols_synth_g",
+                                 "cols_resid", "cols_update", "cols_grad"};
+
+int kind_id(ks_loop* h, const std::string& name) {
+    for (size_t i = 0; i < h->kind_names.size(); ++i)
+        if (h->kind_names[i] == name) return (int)i;
+    h->kind_names.push_back(name);
+    h->kind_ms.push_back(0.0);
+    h->kind_count.push_back(0);
+    return (int)h->kind_names.size() - 1;
+}
+
+cudaEvent_t take_event(ks_loop* h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// bracket a launch with events when profiling; count it always
+struct LaunchScope {
+    ks_loop* h;
+    cudaStream_t s;
+    int kind = -1;
+    cudaEvent_t a = nullptr;
+    LaunchScope(ks_loop* h_, cudaStream_t s_, const std::string& name) : h(h_), s(s_) {
+        if (h->prof) {
+            kind = kind_id(h, name);
+            a = take_event(h);
+            cudaEventRecord(a, s);
+        }
+    }
+    void done() {
+        h->launches++;
+        if (h->prof && a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, s);
+            h->pending.push_back(ks_loop::Rec{kind, a, b});
+        }
+    }
+};
+
+std::string prec_suffix(int pr) { return pr == 0 ? "_f64" : "_f32"; }
+
+template <typename R, int MODE>
+int launch_rows(ks_loop* h, const Bufs<R>& p, cudaStream_t s) {
+    const int pr = std::is_same<R, double>::value ? P64 : P32;
+    const Launch& l = h->lrow[pr];
+    const int n = (int)h->rows.size();
+    LaunchScope ls(h, s, std::string(kRowNames[MODE]) + prec_suffix(pr));
+    k_rows<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n);
+    KS_CUDA(cudaGetLastError());
+    ls.done();
+    return KS_OK;
+}
+
+template <typename R, int MODE>
+int launch_cols(ks_loop* h, const Bufs<R>& p, cudaStream_t s) {
+    const int pr = std::is_same<R, double>::value ? P64 : P32;
+    const Launch& l = h->lcol[pr];
+    const int n = h->d.B * h->d.nkx;
+    LaunchScope ls(h, s, std::string(kColNames[MODE]) + prec_suffix(pr));
+    k_cols<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n);
+    KS_CUDA(cudaGetLastError());
+    ls.done();
+    return KS_OK;
+}
+
+template <typename R>
+int set_smem_attrs(ks_loop* h) {
+    const int pr = std::is_same<R, double>::value ? P64 : P32;
+    const int rs = (int)h->lrow[pr].smem, cs = (int)h->lcol[pr].smem;
+#define KS_ATTR(kern, bytes) \
+    KS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))
+    KS_ATTR((k_rows<R, ROW_ANALYZE>), rs);
+    KS_ATTR((k_rows<R, ROW_NONLIN>), rs);
+    KS_ATTR((k_rows<R, ROW_ADJ>), rs);
+    KS_ATTR((k_rows<R, ROW_SYNTH>), rs);
+    KS_ATTR((k_cols<R, COL_ANALYZE>), cs);
+    KS_ATTR((k_cols<R, COL_SYNTH_U>), cs);
+    KS_ATTR((k_cols<R, COL_SYNTH_R>), cs);
+    KS_ATTR((k_cols<R, COL_SYNTH_G>), cs);
+    KS_ATTR((k_cols<R, COL_RESID>), cs);
+    KS_ATTR((k_cols<R, COL_UPDATE>), cs);
+    KS_ATTR((k_cols<R, COL_GRAD>), cs);
+#undef KS_ATTR
+    return KS_OK;
+}
+
+// grid -> band (u_hat) for every loop, from io
+template <typename R>
+int run_analyze(ks_loop* h, Work& w, int pr, R* io, cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 0, 0.0, 0.0, io);
+    KS_TRY((launch_rows<R, ROW_ANALYZE>(h, p, s)));
+    KS_TRY((launch_cols<R, COL_ANALYZE>(h, p, s)));
+    w.mix_valid[pr] = false;
+    return KS_OK;
+}
+
+// band (u_hat / r_hat / G_hat) -> grid io, every loop
+template <typename R, int CMODE>
+int run_synth(ks_loop* h, Work& w, int pr, R* io, cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 0, 0.0, 0.0, io);
+    KS_TRY((launch_cols<R, CMODE>(h, p, s)));
+    KS_TRY((launch_rows<R, ROW_SYNTH>(h, p, s)));
+    w.mix_valid[pr] = false;
+    return KS_OK;
+}
+
+// M = s-inverse of u_hat (the input of ROW_NONLIN)
+template <typename R>
+int run_prime(ks_loop* h, Work& w, int pr, cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 0, 0.0, 0.0, (R*)nullptr);
+    KS_TRY((launch_cols<R, COL_SYNTH_U>(h, p, s)));
+    w.mix_valid[pr] = true;
+    return KS_OK;
+}
+
+// one tau-step of every live loop of precision pr (M must hold s-inverse of u_hat)
+template <typename R>
+int run_step(ks_loop* h, Work& w, int pr, double tol, double switch_tol, cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 1, tol, switch_tol, (R*)nullptr);
+    KS_TRY((launch_rows<R, ROW_NONLIN>(h, p, s)));
+    KS_TRY((launch_cols<R, COL_RESID>(h, p, s)));
+    KS_TRY((launch_rows<R, ROW_ADJ>(h, p, s)));
+    KS_TRY((launch_cols<R, COL_UPDATE>(h, p, s)));
+    return KS_OK;
+}
+
+// residual pass (no update): J partials and r_hat for every loop of the workspace
+template <typename R>
+int run_residual(ks_loop* h, Work& w, int pr, cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 0, 0.0, 0.0, (R*)nullptr);
+    KS_TRY((launch_cols<R, COL_SYNTH_U>(h, p, s)));
+    KS_TRY((launch_rows<R, ROW_NONLIN>(h, p, s)));
+    KS_TRY((launch_cols<R, COL_RESID>(h, p, s)));
+    w.mix_valid[pr] = false;
+    return KS_OK;
+}
+
+template <typename R>
+int run_gradient(ks_loop* h, Work& w, int pr, cudaStream_t s) {
+    KS_TRY(run_residual<R>(h, w, pr, s));
+    Bufs<R> p = make_bufs<R>(h, w, pr, 0, 0.0, 0.0, (R*)nullptr);
+    KS_TRY((launch_rows<R, ROW_ADJ>(h, p, s)));
+    KS_TRY((launch_cols<R, COL_GRAD>(h, p, s)));
+    return KS_OK;
+}
+
+int run_finalize(ks_loop* h, Work& w, const double* T, int myprec, int mask,
+                 cudaStream_t s) {
+    const int B = h->d.B;
+    LaunchScope ls(h, s, "finalize");
+    k_finalize<<<(B + 127) / 128, 128, 0, s>>>(B, h->d.nkx, h->d.L, w.Jpart, w.L2part, T,
+                                                w.prec, myprec, mask, w.J, w.dJdT, w.sqrtJ);
+    KS_CUDA(cudaGetLastError());
+    ls.done();
+    return KS_OK;
+}
+
+// ---- pointer staging ----
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return KS_OK;
+    KS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return KS_OK;
+}
+
+size_t elem_size(int pr) { return pr == P64 ? sizeof(double) : sizeof(float); }
+
+int check_handle(ks_loop* h) {
+    if (!h) return fail(KS_ERR_ARG, "null handle");
+    KS_CUDA(cudaSetDevice(h->dev));
+    return KS_OK;
+}
+
+// load [P u; T] into workspace w in precision pr (io holds u already when io_loaded)
+int load_state(ks_loop* h, Work& w, int pr, const void* u, const double* T, cudaStream_t s) {
+    const size_t gb = (size_t)h->ngrid * elem_size(pr);
+    const void* usrc = u;
+    void* io = w.io[pr];
+    if (is_device_ptr(u)) {
+        io = const_cast<void*>(u);
+    } else {
+        KS_TRY(copy_in(io, usrc, gb, s));
+    }
+    KS_TRY(copy_in(w.T, T, h->d.B * sizeof(double), s));
+    w.par = 0;
+    if (pr == P64) KS_TRY(run_analyze<double>(h, w, pr, (double*)io, s));
+    else KS_TRY(run_analyze<float>(h, w, pr, (float*)io, s));
+    return KS_OK;
+}
+
+// copy a device result buffer to the caller's pointer (device or host)
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (!dst || bytes == 0) return KS_OK;
+    KS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return KS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Public API
+// ------------------------------------------------------------------------------------------
+extern "C" const char* ks_last_error(void) { return g_err.c_str(); }
+extern "C" const char* ks_version(void) { return KS_VERSION_STRING; }
+extern "C" unsigned long long ks_config_sizeof(void) { return sizeof(ks_config); }
+
+extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
+    g_err.clear();
+    if (!cfg || !out) return fail(KS_ERR_ARG, "null cfg or out");
+    *out = nullptr;
+    if (!(cfg->L > 0.0) || !std::isfinite(cfg->L)) return fail(KS_ERR_ARG, "L must be > 0");
+    if (!is_pow2(cfg->nx) || cfg->nx < 8 || cfg->nx > NMAX)
+        return fail(KS_ERR_ARG, "nx must be a power of two in [8, 1024]");
+    if (cfg->batch < 1 || !cfg->ns) return fail(KS_ERR_ARG, "batch must be >= 1 with ns given");
+    if (cfg->mode < KS_FP64 || cfg->mode > KS_MIXED) return fail(KS_ERR_ARG, "bad mode");
+    if (cfg->scheme != KS_EXPLICIT && cfg->scheme != KS_IMEX) return fail(KS_ERR_ARG, "bad scheme");
+    if (!(cfg->dtau > 0.0) || !std::isfinite(cfg->dtau)) return fail(KS_ERR_ARG, "dtau must be > 0");
+    if (cfg->chunk < 0) return fail(KS_ERR_ARG, "chunk must be >= 0");
+    for (int b = 0; b < cfg->batch; ++b)
+        if (!is_pow2(cfg->ns[b]) || cfg->ns[b] < 8 || cfg->ns[b] > NMAX)
+            return fail(KS_ERR_ARG, "every ns must be a power of two in [8, 1024]");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(KS_ERR_CUDA, "no CUDA device");
+    }
+
+    ks_loop* h = new ks_loop();
+    cudaGetDevice(&h->dev);
+    const int B = cfg->batch;
+    h->d.B = B;
+    h->d.nx = cfg->nx;
+    h->d.lgnx = ilog2(cfg->nx);
+    h->d.kx = cfg->nx / 3;
+    h->d.nkx = h->d.kx + 1;
+    h->d.L = cfg->L;
+    h->d.dtau = cfg->dtau;
+    h->d.scheme = cfg->scheme;
+    h->mode = cfg->mode;
+    h->tol = cfg->tol;
+    h->switch_tol = cfg->switch_tol;
+    h->max_steps = cfg->max_steps;
+    h->chunk = cfg->chunk > 0 ? cfg->chunk : 1000;
+    h->autotune = cfg->autotune;
+    h->ns.resize(B);
+    h->lgns.resize(B);
+    h->ksv.resize(B);
+    h->boff.resize(B);
+    h->moff.resize(B);
+    h->goff.resize(B);
+    long long bo = 0, mo = 0, go = 0;
+    for (int b = 0; b < B; ++b) {
+        const int n = cfg->ns[b];
+        h->ns[b] = n;
+        h->lgns[b] = ilog2(n);
+        h->ksv[b] = n / 3;
+        h->boff[b] = bo;
+        h->moff[b] = mo;
+        h->goff[b] = go;
+        bo += (long long)h->d.nkx * (2 * (n / 3) + 1);
+        mo += (long long)h->d.nkx * n;
+        go += (long long)n * cfg->nx;
+        h->nsmax = std::max(h->nsmax, n);
+    }
+    h->nband = bo;
+    h->nmix = mo;
+    h->ngrid = go;
+    // row tiles: rows_per_tile rows of one loop (even, divides Ns); two double tile buffers of
+    // rows_per_tile x Nx complex values stay within 96 KB of shared memory
+    h->rows_per_tile = 8;
+    while (h->rows_per_tile > 2 && 2 * (size_t)h->rows_per_tile * cfg->nx * sizeof(cpx<double>) > 96 * 1024)
+        h->rows_per_tile >>= 1;
+    for (int b = 0; b < B; ++b) {
+        const int nr = std::min(h->rows_per_tile, h->ns[b]);
+        for (int n0 = 0; n0 < h->ns[b]; n0 += nr) h->rows.push_back(RowItem{b, n0, nr, 0});
+    }
+    // columns: longest loops first
+    h->colorder.resize(B);
+    for (int b = 0; b < B; ++b) h->colorder[b] = b;
+    std::stable_sort(h->colorder.begin(), h->colorder.end(),
+                     [&](int a, int c) { return h->ns[a] > h->ns[c]; });
+    h->need[P64] = (h->mode == KS_FP64 || h->mode == KS_MIXED);
+    h->need[P32] = (h->mode == KS_FP32 || h->mode == KS_MIXED);
+    h->api_prec = (h->mode == KS_FP32) ? P32 : P64;
+
+    auto cleanup = [&](int rc) {
+        ks_destroy(h);
+        return rc;
+    };
+    int rc;
+    if ((rc = upload(h, &h->d_ns, h->ns)) || (rc = upload(h, &h->d_lgns, h->lgns)) ||
+        (rc = upload(h, &h->d_ks, h->ksv)) || (rc = upload(h, &h->d_boff, h->boff)) ||
+        (rc = upload(h, &h->d_moff, h->moff)) || (rc = upload(h, &h->d_goff, h->goff)) ||
+        (rc = upload(h, &h->d_rows, h->rows)) || (rc = upload(h, &h->d_colorder, h->colorder)))
+        return cleanup(rc);
+    {
+        std::vector<double> re, im;
+        twiddles(re, im);
+        std::vector<cpx<double>> t64(NMAX);
+        std::vector<cpx<float>> t32(NMAX);
+        for (int t = 0; t < NMAX; ++t) {
+            t64[t].x = re[t];
+            t64[t].y = im[t];
+            t32[t].x = (float)re[t];
+            t32[t].y = (float)im[t];
+        }
+        std::vector<double> q64(h->d.nkx);
+        std::vector<float> q32(h->d.nkx);
+        for (int j = 0; j < h->d.nkx; ++j) {
+            q64[j] = 2.0 * 3.14159265358979323846 * (double)j / h->d.L;
+            q32[j] = (float)q64[j];
+        }
+        cpx<double>* p64 = nullptr;
+        cpx<float>* p32 = nullptr;
+        double* qq64 = nullptr;
+        float* qq32 = nullptr;
+        if ((rc = upload(h, &p64, t64)) || (rc = upload(h, &p32, t32)) ||
+            (rc = upload(h, &qq64, q64)) || (rc = upload(h, &qq32, q32)))
+            return cleanup(rc);
+        h->d_tw[P64] = p64;
+        h->d_tw[P32] = p32;
+        h->d_qv[P64] = qq64;
+        h->d_qv[P32] = qq32;
+    }
+    bool api_need[2] = {h->api_prec == P64, h->api_prec == P32};
+    if ((rc = alloc_work(h, h->st, h->need)) || (rc = alloc_work(h, h->api, api_need)))
+        return cleanup(rc);
+    // launch shapes
+    for (int pr = 0; pr < 2; ++pr) {
+        const size_t cs = pr == P64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+        Launch& lr = h->lrow[pr];
+        lr.threads = 128;
+        lr.smem = 2 * (size_t)h->rows_per_tile * h->d.nx * cs;
+        lr.grid = 152 * 16;
+        Launch& lc = h->lcol[pr];
+        lc.threads = 128;
+        lc.smem = 2 * (size_t)h->nsmax * cs + (2 * lc.threads + 2) * sizeof(double);
+        lc.grid = 152 * 16;
+    }
+    if ((rc = set_smem_attrs<double>(h)) || (rc = set_smem_attrs<float>(h))) return cleanup(rc);
+    h->h_status.assign(B, 0);
+    h->h_prec.assign(B, 0);
+    h->h_sqrtJ.assign(B, 0.0);
+    h->h_steps.assign(B, 0);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cleanup(fail(KS_ERR_CUDA, cudaGetErrorString(e)));
+    *out = h;
+    return KS_OK;
+}
+
+extern "C" int ks_destroy(ks_loop_t h) {
+    if (!h) return KS_OK;
+    cudaSetDevice(h->dev);
+    cudaDeviceSynchronize();
+    for (auto& r : h->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+    return KS_OK;
+}
+
+extern "C" int ks_residual(ks_loop_t h, const void* u, const double* T, void* r, double* J,
+                           void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!u || !T) return fail(KS_ERR_ARG, "u and T are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int pr = h->api_prec;
+    Work& w = h->api;
+    KS_TRY(load_state(h, w, pr, u, T, s));
+    if (pr == P64) KS_TRY(run_residual<double>(h, w, pr, s));
+    else KS_TRY(run_residual<float>(h, w, pr, s));
+    KS_TRY(run_finalize(h, w, w.T, pr, 0, s));
+    const int B = h->d.B;
+    if (r) {
+        void* dst = is_device_ptr(r) ? r : w.io[pr];
+        if (pr == P64) KS_TRY((run_synth<double, COL_SYNTH_R>(h, w, pr, (double*)dst, s)));
+        else KS_TRY((run_synth<float, COL_SYNTH_R>(h, w, pr, (float*)dst, s)));
+        if (dst != r) KS_TRY(copy_out(r, dst, (size_t)h->ngrid * elem_size(pr), s));
+    }
+    KS_TRY(copy_out(J, w.J, B * sizeof(double), s));
+    if ((r && !is_device_ptr(r)) || (J && !is_device_ptr(J)) || !is_device_ptr(u))
+        KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+extern "C" int ks_adjoint_grad(ks_loop_t h, const void* u, const double* T, void* G, double* dJdT,
+                               void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!u || !T || !G) return fail(KS_ERR_ARG, "u, T and G are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int pr = h->api_prec;
+    Work& w = h->api;
+    KS_TRY(load_state(h, w, pr, u, T, s));
+    if (pr == P64) KS_TRY(run_gradient<double>(h, w, pr, s));
+    else KS_TRY(run_gradient<float>(h, w, pr, s));
+    KS_TRY(run_finalize(h, w, w.T, pr, 0, s));
+    void* dst = is_device_ptr(G) ? G : w.io[pr];
+    if (pr == P64) KS_TRY((run_synth<double, COL_SYNTH_G>(h, w, pr, (double*)dst, s)));
+    else KS_TRY((run_synth<float, COL_SYNTH_G>(h, w, pr, (float*)dst, s)));
+    if (dst != G) KS_TRY(copy_out(G, dst, (size_t)h->ngrid * elem_size(pr), s));
+    KS_TRY(copy_out(dJdT, w.dJdT, h->d.B * sizeof(double), s));
+    if (!is_device_ptr(G) || (dJdT && !is_device_ptr(dJdT)) || !is_device_ptr(u))
+        KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+namespace {
+
+// initial precision of the resident state
+int start_prec(ks_loop* h) { return h->mode == KS_FP32 || h->mode == KS_MIXED ? P32 : P64; }
+
+}  // namespace
+
+__global__ void k_band_d2f(const cpx<double>* src, cpx<float>* dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = mk<float>((float)src[i].x, (float)src[i].y);
+}
+
+// dst[b] = band of loop b in double, taken from the float band for loops running in float
+__global__ void k_band_merge(const cpx<float>* s32, const cpx<double>* s64, cpx<double>* dst,
+                             const long long* boff, const int* prec, int B, int nkx,
+                             const int* ks) {
+    const int b = blockIdx.y;
+    if (b >= B) return;
+    const long long n = (long long)nkx * (2 * ks[b] + 1);
+    const long long o = boff[b];
+    const bool f = prec[b] == 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        dst[o + i] = f ? mk<double>((double)s32[o + i].x, (double)s32[o + i].y) : s64[o + i];
+    }
+}
+
+namespace {
+
+int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
+    const int B = h->d.B;
+    Work& w = h->st;
+    const int pr0 = start_prec(h);
+    if (h->mode == KS_MIXED) {
+        // the caller's field is double: project in double, round the band to float
+        KS_TRY(load_state(h, w, P64, u, T, s));
+        const long long n = h->nband;
+        k_band_d2f<<<(int)std::min<long long>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+            (const cpx<double>*)w.uh[P64], (cpx<float>*)w.uh[P32], n);
+        KS_CUDA(cudaGetLastError());
+    } else {
+        KS_TRY(load_state(h, w, pr0, u, T, s));
+    }
+    KS_CUDA(cudaMemsetAsync(w.status, 0, B * sizeof(int), s));
+    KS_CUDA(cudaMemsetAsync(w.steps, 0, B * sizeof(long long), s));
+    KS_CUDA(cudaMemsetAsync(w.sqrtJ, 0, B * sizeof(double), s));
+    h->h_prec.assign(B, pr0);
+    KS_CUDA(cudaMemcpyAsync(w.prec, h->h_prec.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    h->h_status.assign(B, KS_RUNNING);
+    h->h_steps.assign(B, 0);
+    w.mix_valid[P64] = w.mix_valid[P32] = false;
+    h->state_set = true;
+    return KS_OK;
+}
+
+// run n steps of the resident state on the precisions that have live loops
+int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s) {
+    Work& w = h->st;
+    bool live[2] = {false, false};
+    for (int b = 0; b < h->d.B; ++b)
+        if (h->h_status[b] == KS_RUNNING) live[h->h_prec[b]] = true;
+    for (int pr = 0; pr < 2; ++pr) {
+        if (live[pr] && !w.mix_valid[pr]) {
+            if (pr == P64) KS_TRY(run_prime<double>(h, w, pr, s));
+            else KS_TRY(run_prime<float>(h, w, pr, s));
+        }
+    }
+    const double swt = (h->mode == KS_MIXED) ? h->switch_tol : 0.0;
+    for (long long i = 0; i < n; ++i) {
+        if (live[P32]) KS_TRY(run_step<float>(h, w, P32, tol, swt, s));
+        if (live[P64]) KS_TRY(run_step<double>(h, w, P64, tol, 0.0, s));
+        w.par ^= 1;
+    }
+    return KS_OK;
+}
+
+int readback(ks_loop* h, cudaStream_t s) {
+    Work& w = h->st;
+    const int B = h->d.B;
+    KS_CUDA(cudaMemcpyAsync(h->h_status.data(), w.status, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(h->h_sqrtJ.data(), w.sqrtJ, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(h->h_steps.data(), w.steps, B * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+// move the loops flagged in sel (host) from float to double
+int switch_to_double(ks_loop* h, const std::vector<int>& sel, cudaStream_t s) {
+    Work& w = h->st;
+    const int B = h->d.B;
+    KS_CUDA(cudaMemcpyAsync(w.sel, sel.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    dim3 g(8, B);
+    k_band_f2d<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (cpx<double>*)w.uh[P64], h->d_boff,
+                                 w.sel, B, h->d.nkx, h->d_ks);
+    KS_CUDA(cudaGetLastError());
+    for (int b = 0; b < B; ++b)
+        if (sel[b]) {
+            h->h_prec[b] = P64;
+            h->h_status[b] = KS_RUNNING;
+        }
+    KS_CUDA(cudaMemcpyAsync(w.prec, h->h_prec.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemcpyAsync(w.status, h->h_status.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    w.mix_valid[P64] = false;
+    return KS_OK;
+}
+
+int set_status(ks_loop* h, cudaStream_t s) {
+    KS_CUDA(cudaMemcpyAsync(h->st.status, h->h_status.data(), h->d.B * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    return KS_OK;
+}
+
+// evaluate J at the current resident state of every loop (per precision) into sqrtJ
+int final_eval(ks_loop* h, cudaStream_t s) {
+    Work& w = h->st;
+    for (int pr = 0; pr < 2; ++pr) {
+        if (!h->need[pr]) continue;
+        bool any = false;
+        for (int b = 0; b < h->d.B; ++b) any |= (h->h_prec[b] == pr);
+        if (!any) continue;
+        const double* Tc = w.T + (size_t)w.par * h->d.B;
+        if (pr == P64) KS_TRY(run_residual<double>(h, w, pr, s));
+        else KS_TRY(run_residual<float>(h, w, pr, s));
+        KS_TRY(run_finalize(h, w, Tc, pr, 1, s));
+    }
+    return KS_OK;
+}
+
+// write the resident state to u (grid) in the handle's I/O precision
+int get_state_impl(ks_loop* h, void* u, double* T, cudaStream_t s) {
+    Work& w = h->st;
+    const int B = h->d.B;
+    if (u) {
+        if (h->mode == KS_MIXED) {
+            // gather both precisions into the double band of the API workspace, synthesise there
+            Work& a = h->api;
+            dim3 g(8, B);
+            k_band_merge<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (const cpx<double>*)w.uh[P64],
+                                           (cpx<double>*)a.uh[P64], h->d_boff, w.prec, B, h->d.nkx,
+                                           h->d_ks);
+            KS_CUDA(cudaGetLastError());
+            void* dst = is_device_ptr(u) ? u : a.io[P64];
+            KS_TRY((run_synth<double, COL_SYNTH_U>(h, a, P64, (double*)dst, s)));
+            if (dst != u) KS_TRY(copy_out(u, dst, (size_t)h->ngrid * sizeof(double), s));
+        } else {
+            const int pr = (h->mode == KS_FP32) ? P32 : P64;
+            void* dst = is_device_ptr(u) ? u : w.io[pr];
+            if (pr == P64) KS_TRY((run_synth<double, COL_SYNTH_U>(h, w, pr, (double*)dst, s)));
+            else KS_TRY((run_synth<float, COL_SYNTH_U>(h, w, pr, (float*)dst, s)));
+            if (dst != u) KS_TRY(copy_out(u, dst, (size_t)h->ngrid * elem_size(pr), s));
+        }
+    }
+    if (T) KS_TRY(copy_out(T, w.T + (size_t)w.par * B, B * sizeof(double), s));
+    return KS_OK;
+}
+
+}  // namespace
+
+extern "C" int ks_set_state(ks_loop_t h, const void* u, const double* T, void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!u || !T) return fail(KS_ERR_ARG, "u and T are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    KS_TRY(set_state_full(h, u, T, s));
+    if (!is_device_ptr(u) || !is_device_ptr(T)) KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+extern "C" int ks_step(ks_loop_t h, long long nsteps, double tol, void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!h->state_set) return fail(KS_ERR_STATE, "ks_step before ks_set_state");
+    if (nsteps < 0) return fail(KS_ERR_ARG, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double t = tol < 0.0 ? h->tol : tol;
+    KS_TRY(steps_impl(h, nsteps, t, s));
+    if (h->mode == KS_MIXED) {
+        // hand loops that met the switch criterion to the double kernels
+        KS_TRY(readback(h, s));
+        std::vector<int> sel(h->d.B, 0);
+        bool any = false;
+        for (int b = 0; b < h->d.B; ++b)
+            if (h->h_status[b] == ST_SWITCH) {
+                sel[b] = 1;
+                any = true;
+            }
+        if (any) KS_TRY(switch_to_double(h, sel, s));
+    }
+    return KS_OK;
+}
+
+extern "C" int ks_get_state(ks_loop_t h, void* u, double* T, long long* steps, double* sqrtJ,
+                            int* status, void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!h->state_set) return fail(KS_ERR_STATE, "ks_get_state before ks_set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    KS_TRY(readback(h, s));
+    KS_TRY(get_state_impl(h, u, T, s));
+    const int B = h->d.B;
+    Work& w = h->st;
+    KS_TRY(copy_out(steps, w.steps, B * sizeof(long long), s));
+    KS_TRY(copy_out(sqrtJ, w.sqrtJ, B * sizeof(double), s));
+    if (status) {
+        // report the internal switch marker as running
+        std::vector<int> st = h->h_status;
+        for (int& v : st)
+            if (v == ST_SWITCH) v = KS_RUNNING;
+        KS_CUDA(cudaMemcpyAsync(status, st.data(), B * sizeof(int), cudaMemcpyDefault, s));
+    }
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, double tol,
+                          long long* steps, double* sqrtJ, int* status, void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!u || !T) return fail(KS_ERR_ARG, "u and T are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long cap = max_steps < 0 ? h->max_steps : max_steps;
+    const double tl = tol < 0.0 ? h->tol : tol;
+    const int B = h->d.B;
+    KS_TRY(set_state_full(h, u, T, s));
+    // stall detection: sqrt(J) at the start of the current window
+    std::vector<double> win_val(B, -1.0);
+    std::vector<long long> win_step(B, 0);
+    long long done = 0;
+    while (done < cap) {
+        const long long c = std::min<long long>(h->chunk, cap - done);
+        KS_TRY(steps_impl(h, c, tl, s));
+        done += c;
+        KS_TRY(readback(h, s));
+        std::vector<int> sel(B, 0);
+        bool any_switch = false, any_live = false, status_dirty = false;
+        for (int b = 0; b < B; ++b) {
+            int& stb = h->h_status[b];
+            if (stb == ST_SWITCH) {
+                sel[b] = 1;
+                any_switch = true;
+                continue;
+            }
+            if (stb != KS_RUNNING) continue;
+            // no-progress test over a window of stall_window steps
+            const double v = h->h_sqrtJ[b];
+            if (win_val[b] < 0.0) {
+                win_val[b] = v;
+                win_step[b] = h->h_steps[b];
+            } else if (h->h_steps[b] - win_step[b] >= h->stall_window) {
+                if (v > (1.0 - h->stall_drop) * win_val[b]) {
+                    if (h->mode == KS_MIXED && h->h_prec[b] == P32) {
+                        sel[b] = 1;
+                        any_switch = true;
+                    } else {
+                        stb = KS_STALLED;
+                        status_dirty = true;
+                    }
+                }
+                win_val[b] = v;
+                win_step[b] = h->h_steps[b];
+            }
+            if (stb == KS_RUNNING && !sel[b]) any_live = true;
+        }
+        if (any_switch) {
+            KS_TRY(switch_to_double(h, sel, s));
+            for (int b = 0; b < B; ++b)
+                if (sel[b]) {
+                    win_val[b] = -1.0;
+                    any_live = true;
+                }
+        }
+        if (status_dirty) KS_TRY(set_status(h, s));
+        if (!any_live) break;
+    }
+    // final residual at the resident state, step-cap status for the loops still running
+    KS_TRY(final_eval(h, s));
+    KS_TRY(readback(h, s));
+    for (int b = 0; b < B; ++b)
+        if (h->h_status[b] == KS_RUNNING || h->h_status[b] == ST_SWITCH) h->h_status[b] = KS_STEP_CAP;
+    KS_TRY(set_status(h, s));
+    KS_TRY(get_state_impl(h, u, T, s));
+    Work& w = h->st;
+    KS_TRY(copy_out(steps, w.steps, B * sizeof(long long), s));
+    KS_TRY(copy_out(sqrtJ, w.sqrtJ, B * sizeof(double), s));
+    KS_TRY(copy_out(status, w.status, B * sizeof(int), s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+extern "C" int ks_profile(ks_loop_t h, int enable) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    h->prof = enable != 0;
+    return KS_OK;
+}
+
+extern "C" int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long long* launches,
+                               long long* total_launches, int reset) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    for (auto& r : h->pending) {
+        KS_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        KS_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        h->kind_ms[r.kind] += (double)t;
+        h->kind_count[r.kind] += 1;
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->pending.clear();
+    const int k = (int)h->kind_names.size();
+    for (int i = 0; i < k && i < n; ++i) {
+        if (names) {
+            std::strncpy(names + (size_t)i * 48, h->kind_names[i].c_str(), 47);
+            names[(size_t)i * 48 + 47] = 0;
+        }
+        if (ms) ms[i] = h->kind_ms[i];
+        if (launches) launches[i] = h->kind_count[i];
+    }
+    if (total_launches) *total_launches = h->launches;
+    if (reset) {
+        for (auto& v : h->kind_ms) v = 0.0;
+        for (auto& v : h->kind_count) v = 0;
+        h->launches = 0;
+    }
+    return k;
+}

@@ -1,0 +1,74 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every function declared
+in include/ks_loop.h, agrees on the ks_config layout, and rejects bad arguments (or the
+missing device) with an error code instead of computing anything on the CPU."""
+import os
+import re
+
+import pytest
+
+from paper_2007_06427_gb300 import ks_loop as K
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ks_loop.h")).read()
+    return sorted(set(re.findall(r"^KS_API\s+[\w\s\*]+?\b(ks_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(K.LIB_PATH):
+        from paper_2007_06427_gb300 import build
+        build.build()
+    return K.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("ks_loop_create", "ks_residual", "ks_adjoint_grad", "ks_descend", "ks_destroy"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) == set(K._EXPORTS)
+
+
+def test_config_layout(lib):
+    import ctypes
+    assert lib.ks_config_sizeof() == ctypes.sizeof(K.ks_config)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(L=22.0, nx=48, ns=[32]),          # nx not a power of two
+    dict(L=22.0, nx=4, ns=[32]),           # nx too small
+    dict(L=22.0, nx=2048, ns=[32]),        # nx too large
+    dict(L=22.0, nx=32, ns=[24]),          # ns not a power of two
+    dict(L=22.0, nx=32, ns=[32, 2048]),    # one ns too large
+    dict(L=-1.0, nx=32, ns=[32]),          # L <= 0
+    dict(L=22.0, nx=32, ns=[32], dtau=0.0),
+    dict(L=22.0, nx=32, ns=[32], mode=7),
+    dict(L=22.0, nx=32, ns=[32], scheme=3),
+])
+def test_bad_arguments_rejected(lib, kw):
+    with pytest.raises(K.KsError) as e:
+        K.ks_loop_create(**kw)
+    assert e.value.code == K.KS_ERR_ARG
+
+
+def test_null_handle_rejected(lib):
+    import numpy as np
+    with pytest.raises(K.KsError) as e:
+        K.ks_residual(None, np.zeros(4), np.zeros(1))
+    assert e.value.code == K.KS_ERR_ARG
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(K.KsError) as e:
+        K.ks_loop_create(22.0, 32, [32])
+    assert e.value.code == K.KS_ERR_CUDA

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle, element by element.
+
+Tolerances: FP64 mode 1e-12 relative (||x_gpu - x_oracle|| / ||x_oracle|| over each loop) on
+r and G and on J, dJ/dT; FP32 mode 1e-5 relative.  Shapes cover every workload's (Nx, Ns)
+plus tiny and ragged batches (several transform tiles, ragged row tiles, loops of unequal Ns).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ks_oracle as ko
+from paper_2007_06427_gb300 import ks_loop as K
+from paper_2007_06427_gb300.inputs import spectral_loop
+
+pytestmark = pytest.mark.gpu
+
+TOL = {K.KS_FP64: 1e-12, K.KS_FP32: 1e-5}
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+
+
+def make(nx, nss, L=22.0, seed0=0, T_range=(20.0, 80.0), decay=(2.0, 2.0)):
+    us, Ts = [], []
+    for i, n in enumerate(nss):
+        u, T, _ = spectral_loop(seed0 + i, nx, L, ns=n, T_range=T_range, decay=decay)
+        us.append(u)
+        Ts.append(T)
+    return us, Ts
+
+
+def dev_tensors(us, Ts, mode):
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    u = torch.from_numpy(np.concatenate([a.ravel() for a in us])).to("cuda", dt)
+    T = torch.tensor(Ts, dtype=torch.float64, device="cuda")
+    return u, T
+
+
+def split(flat, nx, nss):
+    out, o = [], 0
+    for n in nss:
+        out.append(flat[o:o + n * nx].reshape(n, nx))
+        o += n * nx
+    return out
+
+
+SHAPES = [
+    (32, [32]),                 # single 32 x 32 explicit workload
+    (64, [128]),                # single 64 x 128 workload
+    (64, [64, 64, 64]),         # batch of 64 x 64 loops
+    (64, [32, 64, 128, 256]),   # ragged Ns
+    (8, [8]),                   # smallest transform
+    (16, [8, 16, 32]),          # ragged, odd log2 lengths
+    (128, [16]),
+]
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+@pytest.mark.parametrize("nx,nss", SHAPES)
+def test_residual_and_gradient_match_oracle(nx, nss, mode):
+    L = 22.0
+    us, Ts = make(nx, nss, L)
+    u, T = dev_tensors(us, Ts, mode)
+    with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15) as h:
+        r = torch.empty_like(u)
+        G = torch.empty_like(u)
+        J = torch.empty(len(nss), dtype=torch.float64, device="cuda")
+        dJdT = torch.empty_like(J)
+        K.ks_residual(h.handle, u, T, r, J)
+        K.ks_adjoint_grad(h.handle, u, T, G, dJdT)
+        torch.cuda.synchronize()
+    rs = split(r.double().cpu().numpy(), nx, nss)
+    Gs = split(G.double().cpu().numpy(), nx, nss)
+    tol = TOL[mode]
+    for b in range(len(nss)):
+        ref = ko.adjoint_grad(us[b], Ts[b], L)
+        r_ref = ko.grid(nx, nss[b], L).real_grid(ref["rh"])
+        assert rel(rs[b], r_ref) < tol, (b, rel(rs[b], r_ref))
+        assert rel(Gs[b], ref["G"]) < tol, (b, rel(Gs[b], ref["G"]))
+        assert abs(J[b].item() - ref["J"]) <= tol * ref["J"]
+        assert abs(dJdT[b].item() - ref["dJdT"]) <= tol * abs(ref["dJdT"]) + 1e-300
+
+
+def test_large_domain_sampled():
+    """256 x 1024 at L = 100 (the large-domain workload's shape): full r and G of one loop."""
+    L, nx, ns = 100.0, 256, 1024
+    us, Ts = make(nx, [ns], L, T_range=(120.0, 120.0), decay=(8.0, 8.0))
+    u, T = dev_tensors(us, Ts, K.KS_FP64)
+    with K.KSLoop(L, nx, [ns], K.KS_FP64) as h:
+        G = torch.empty_like(u)
+        dJdT = torch.empty(1, dtype=torch.float64, device="cuda")
+        K.ks_adjoint_grad(h.handle, u, T, G, dJdT)
+        torch.cuda.synchronize()
+    ref = ko.adjoint_grad(us[0], Ts[0], L)
+    assert rel(G.cpu().numpy().reshape(ns, nx), ref["G"]) < 1e-12
+    assert abs(dJdT.item() - ref["dJdT"]) <= 1e-12 * abs(ref["dJdT"])
+
+
+@pytest.mark.parametrize("scheme,dtau,nsteps", [(K.KS_IMEX, 0.15, 20), (K.KS_EXPLICIT, 1e-4, 50)])
+def test_descent_trajectory_matches_oracle(scheme, dtau, nsteps):
+    L, nx, nss = 22.0, 32, [32, 16, 64]
+    us, Ts = make(nx, nss, L)
+    u, T = dev_tensors(us, Ts, K.KS_FP64)
+    B = len(nss)
+    steps = torch.zeros(B, dtype=torch.int64, device="cuda")
+    sq = torch.zeros(B, dtype=torch.float64, device="cuda")
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    with K.KSLoop(L, nx, nss, K.KS_FP64, scheme, dtau, chunk=7) as h:
+        K.ks_descend(h.handle, u, T, nsteps, 0.0, steps, sq, st)
+    us_out = split(u.cpu().numpy(), nx, nss)
+    for b in range(B):
+        d = ko.descend(us[b], Ts[b], L, dtau, scheme, nsteps)
+        assert rel(us_out[b], d["u"]) < 1e-12
+        assert abs(T[b].item() - d["T"]) < 1e-12 * d["T"]
+        assert abs(sq[b].item() - d["sqrtJ"]) < 1e-11 * d["sqrtJ"]
+        assert int(steps[b]) == nsteps
+        assert int(st[b]) == K.KS_STEP_CAP
+
+
+def test_explicit_2000_steps_single_32x32():
+    """The 32 x 32 explicit workload: 2000 steps at dtau = 1e-4 against the oracle."""
+    L, nx = 22.0, 32
+    u0, T0, _ = spectral_loop(0, nx, L, ns=32, T0=40.0)
+    u, T = dev_tensors([u0], [T0], K.KS_FP64)
+    with K.KSLoop(L, nx, [32], K.KS_FP64, K.KS_EXPLICIT, 1e-4, chunk=500) as h:
+        sq = torch.zeros(1, dtype=torch.float64, device="cuda")
+        K.ks_descend(h.handle, u, T, 2000, 0.0, None, sq, None)
+    d = ko.descend(u0, T0, L, 1e-4, ko.EXPLICIT, 2000)
+    assert rel(u.cpu().numpy().reshape(32, 32), d["u"]) < 1e-11
+    assert abs(T.item() - d["T"]) < 1e-12 * d["T"]
+    assert sq.item() == pytest.approx(d["sqrtJ"], rel=1e-10)
+
+
+def test_fp32_descent_tracks_oracle():
+    L, nx, nss = 22.0, 64, [64, 128]
+    us, Ts = make(nx, nss, L)
+    u, T = dev_tensors(us, Ts, K.KS_FP32)
+    with K.KSLoop(L, nx, nss, K.KS_FP32, K.KS_IMEX, 0.15) as h:
+        K.ks_descend(h.handle, u, T, 10, 0.0)
+    us_out = split(u.double().cpu().numpy(), nx, nss)
+    for b in range(len(nss)):
+        d = ko.descend(us[b], Ts[b], L, 0.15, ko.IMEX, 10)
+        assert rel(us_out[b], d["u"]) < 1e-5
+        assert abs(T[b].item() - d["T"]) < 1e-5 * d["T"]
+
+
+def test_host_buffers_match_device_buffers():
+    L, nx, nss = 22.0, 32, [32, 64]
+    us, Ts = make(nx, nss, L)
+    u, T = dev_tensors(us, Ts, K.KS_FP64)
+    uh = np.concatenate([a.ravel() for a in us])
+    Th = np.array(Ts)
+    with K.KSLoop(L, nx, nss, K.KS_FP64) as h:
+        G_d = torch.empty_like(u)
+        K.ks_adjoint_grad(h.handle, u, T, G_d)
+        G_h = np.empty_like(uh)
+        dJ_h = np.empty(2)
+        K.ks_adjoint_grad(h.handle, uh, Th, G_h, dJ_h)
+        st_h = np.zeros(2, dtype=np.int32)
+        K.ks_descend(h.handle, uh, Th, 5, 0.0, None, None, st_h)
+        K.ks_descend(h.handle, u, T, 5, 0.0)
+    np.testing.assert_array_equal(G_h, G_d.cpu().numpy())
+    np.testing.assert_array_equal(uh, u.cpu().numpy())
+    np.testing.assert_array_equal(Th, T.cpu().numpy())
+    assert list(st_h) == [K.KS_STEP_CAP] * 2
+
+
+def test_resident_state_steps_equal_descend():
+    L, nx, nss = 22.0, 64, [64, 32]
+    us, Ts = make(nx, nss, L)
+    u, T = dev_tensors(us, Ts, K.KS_FP64)
+    with K.KSLoop(L, nx, nss, K.KS_FP64) as h:
+        K.ks_set_state(h.handle, u, T)
+        for _ in range(3):
+            K.ks_step(h.handle, 4, 0.0)
+        u1 = torch.empty_like(u)
+        T1 = torch.empty_like(T)
+        steps = torch.zeros(2, dtype=torch.int64, device="cuda")
+        K.ks_get_state(h.handle, u1, T1, steps)
+        u2, T2 = u.clone(), T.clone()
+        K.ks_descend(h.handle, u2, T2, 12, 0.0)
+    assert steps.tolist() == [12, 12]
+    assert torch.equal(u1, u2) and torch.equal(T1, T2)
+
+
+def test_converged_and_trivial_loops():
+    """u = 0 is an equilibrium (J = 0): converged with zero steps; a loop with T = NaN diverges;
+    the others keep running."""
+    L, nx, nss = 22.0, 32, [32, 32, 32]
+    us, Ts = make(nx, nss, L)
+    us[0] = np.zeros_like(us[0])
+    Ts[2] = float("nan")
+    u, T = dev_tensors(us, Ts, K.KS_FP64)
+    steps = torch.zeros(3, dtype=torch.int64, device="cuda")
+    st = torch.zeros(3, dtype=torch.int32, device="cuda")
+    with K.KSLoop(L, nx, nss, K.KS_FP64) as h:
+        K.ks_descend(h.handle, u, T, 10, 1e-10, steps, None, st)
+    assert st.tolist() == [K.KS_CONVERGED, K.KS_STEP_CAP, K.KS_DIVERGED]
+    assert steps.tolist()[:2] == [0, 10]
