@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--switch-tol", type=float, default=1e-5)
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
+                    help="profiling case: load the workload, run 3 x K tau-steps, no timing")
     return ap.parse_args()
 
 
@@ -406,8 +408,29 @@ def run_to_tol(args, w, dev):
     return out
 
 
+def ncu_case(args):
+    """Small fixed case for ncu captures: set the state, 3 calls of K tau-steps, synchronise."""
+    import torch
+    from paper_2007_06427_gb300 import ks_loop as K
+    from paper_2007_06427_gb300.inputs import workload
+    w = workload(args.workload)
+    mode = K.KS_FP32 if args.mode == "fp32" else K.KS_FP64
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    u = torch.from_numpy(w.packed()).cuda().to(dt)
+    T = torch.tensor(w.T0, dtype=torch.float64, device="cuda")
+    with K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau) as h:
+        K.ks_set_state(h.handle, u, T)
+        for _ in range(3):
+            K.ks_step(h.handle, args.ncu_case, 0.0)
+        torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": w.name, "mode": args.mode, "steps": 3 * args.ncu_case}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        return ncu_case(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)

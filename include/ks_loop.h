@@ -162,6 +162,17 @@ KS_API int ks_profile(ks_loop_t h, int enable);
 KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long long* launches,
                            long long* total_launches, int reset);
 
+/* Tuning knobs of a handle (KS_ERR_ARG for an unknown key or a bad value):
+ *   "persistent"     1 (default): each ks_step / descent chunk runs as one cooperative launch
+ *                    whose CTAs step through the four phases with grid-wide barriers; 0: four
+ *                    launches per tau-step.
+ *   "stall_window"   tau-steps over which ks_descend measures progress (default 20000)
+ *   "stall_drop_ppm" a loop whose sqrt(J) fell by less than this many parts per million over
+ *                    a window is stalled (default 1000): the float phase of a mixed descent
+ *                    then switches to double, a double descent stops with KS_STALLED
+ *   "chunk"          tau-steps between read-backs in ks_descend */
+KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
+
 /* Message for the last non-zero return on the calling thread ("" if none). */
 KS_API const char* ks_last_error(void);
 

@@ -85,7 +85,7 @@ template <typename R>
 KS_HD cpx<R> mul_i(cpx<R> a, int sgn) { return sgn > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
 
 struct RowItem {
-    int b, n0, nr, pad;  // loop, first row, rows in the tile (even)
+    int b, n0, nr, lgnr;  // loop, first row, rows in the tile (even power of two), log2 nr
 };
 
 // Shape of the batch (shared by all loops of a handle).
@@ -96,6 +96,7 @@ struct Dims {
     double L;
     double dtau;
     int scheme;    // 0 explicit, 1 IMEX
+    double hx;     // 0.5 / Nx (forward x-pass scale with the pair split)
 };
 
 // Device buffers of one precision, plus the per-loop scalars (always double / int).
@@ -114,6 +115,7 @@ struct Bufs {
     R* U;                   // grid u (kept from ROW_NONLIN for ROW_ADJ)
     R* io;                  // grid in/out for analysis / synthesis items
     double* T;              // [2][B] period, double-buffered by step parity
+    double* wT;             // [2][B] 2 pi / T, same parity as T
     double* Jpart;          // [B][nkx] per-column partial of sum w_j |r_hat|^2
     double* L2part;         // [B][nkx] per-column partial of sum w_j w_k Im(conj(u_hat) r_hat)
     int* status;            // [B]
@@ -122,6 +124,9 @@ struct Bufs {
     double* sqrtJ;          // [B]
     const cpx<R>* tw;       // [NMAX] exp(+2 pi i t / NMAX)
     const R* qv;            // [nkx] q_j = 2 pi j / L in this precision
+    const R* lin;           // [nkx] q_j^2 - q_j^4 (symbol of -u_xx - u_xxxx)
+    const R* cq;            // [nkx] q_j^4 (q_j^2 - 1)^2 (x part of -Lambda_jk)
+    const R* insv;          // [B] 1 / Ns_b
     const RowItem* rows;    // row work items
     const int* colorder;    // loop order of the column items (longest Ns first)
     int myprec;             // precision of this kernel set
@@ -206,29 +211,76 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
     return a;
 }
 
-// Block-wide sum of two doubles per thread; red has room for 2 * KS_NT doubles.  The result
-// is valid in every thread after the call.
+// Block-wide sum of two doubles per thread (warp shuffles, then one warp over the warp sums);
+// red has room for 2 * (warps + 1) doubles.  The result is valid in every thread after the call.
 KS_HD void block_sum2(double* red, double& s0, double& s1) {
-    const int t = KS_TID, nt = KS_NT;
-    red[t] = s0;
-    red[nt + t] = s1;
-    KS_SYNC();
-    if (t == 0) {
-        double a = 0.0, c = 0.0;
-        for (int i = 0; i < nt; ++i) {
-            a += red[i];
-            c += red[nt + i];
-        }
-        red[2 * nt] = a;
-        red[2 * nt + 1] = c;
+#ifdef KS_HOST_EMULATION
+    (void)red;
+#else
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
-    KS_SYNC();
-    s0 = red[2 * nt];
-    s1 = red[2 * nt + 1];
-    KS_SYNC();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) {
+        red[2 * w] = s0;
+        red[2 * w + 1] = s1;
+    }
+    __syncthreads();
+    if (w == 0) {
+        s0 = (l < nw) ? red[2 * l] : 0.0;
+        s1 = (l < nw) ? red[2 * l + 1] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (l == 0) {
+            red[2 * nw] = s0;
+            red[2 * nw + 1] = s1;
+        }
+    }
+    __syncthreads();
+    s0 = red[2 * nw];
+    s1 = red[2 * nw + 1];
+    __syncthreads();
+#endif
 }
 
-KS_HD double qj(const Dims& d, int j) { return 2.0 * 3.14159265358979323846 * (double)j / d.L; }
+// Sum of n doubles a[0..n) and c[0..n) in a fixed order, identical in every CTA: lane l adds
+// a[l], a[l+32], ... then a shuffle tree.  Every thread of the calling warp gets the sums.
+KS_HD void warp_sum_partials(const double* a, const double* c, int n, double& sa, double& sc) {
+#ifdef KS_HOST_EMULATION
+    sa = 0.0;
+    sc = 0.0;
+    double la[32] = {0}, lc[32] = {0};
+    for (int l = 0; l < 32; ++l)
+        for (int i = l; i < n; i += 32) {
+            la[l] += a[i];
+            lc[l] += c[i];
+        }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int l = 0; l < 32; ++l)
+            if ((l & o) == 0 && (l ^ o) < 32) {
+                la[l] += la[l ^ o];
+                lc[l] += lc[l ^ o];
+            }
+    sa = la[0];
+    sc = lc[0];
+#else
+    const int l = threadIdx.x & 31;
+    double x = 0.0, y = 0.0;
+    for (int i = l; i < n; i += 32) {
+        x += a[i];
+        y += c[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    sa = x;
+    sc = y;
+#endif
+}
 
 // is the loop processed by this kernel set?
 template <typename R>
@@ -243,16 +295,16 @@ KS_HD bool loop_live(const Bufs<R>& p, int b) {
 enum RowMode { ROW_ANALYZE = 0, ROW_NONLIN = 1, ROW_ADJ = 2, ROW_SYNTH = 3 };
 
 // Fill A[pair][J] (J in [0, Nx)) with the Hermitian-extended spectra of two rows (a = 2*pair,
-// b = 2*pair + 1) read from M: Z_J = X^a_J + i X^b_J with X_{-j} = conj(X_j).  `mulq` = 1
-// multiplies X_j by i q_j first (x-derivative).
+// b = 2*pair + 1) read from M: Z_J = X^a_J + i X^b_J with X_{-j} = conj(X_j).
 template <typename R>
-KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, int npairs,
-                             cpx<R>* A, bool mulq, const R* p_qv) {
+KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, int lgp,
+                             cpx<R>* A) {
     const int nx = d.nx, kx = d.kx;
-    const int total = npairs * nx;
+    const int npairs = 1 << lgp;
+    const int total = nx << lgp;
     for (int i = KS_TID; i < total; i += KS_NT) {
-        const int J = i / npairs;
-        const int pr = i - J * npairs;
+        const int J = i >> lgp;
+        const int pr = i & (npairs - 1);
         cpx<R> z = mk<R>(0, 0);
         int j = -1;
         bool neg = false;
@@ -265,11 +317,6 @@ KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, in
         if (j >= 0) {
             const cpx<R>* col = Mb + (size_t)j * ns + n0 + 2 * pr;
             cpx<R> xa = col[0], xb = col[1];
-            if (mulq) {
-                const R q = p_qv[j];
-                xa = mk<R>(-q * xa.y, q * xa.x);
-                xb = mk<R>(-q * xb.y, q * xb.x);
-            }
             if (neg) {
                 xa = conj(xa);
                 xb = conj(xb);
@@ -284,19 +331,20 @@ KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, in
 // scaled by 1/Nx, for j = 0..Kx, and store them to M[j][n0 + 2 pr + {0,1}].
 template <typename R>
 KS_HD void store_pair_spectra(const Dims& d, const cpx<R>* Y, cpx<R>* Mb, int ns, int n0,
-                              int npairs) {
+                              int lgp) {
     const int nx = d.nx;
-    const R h = (R)(0.5 / (double)nx);
-    const int total = npairs * d.nkx;
+    const R h = (R)d.hx;
+    const int npairs = 1 << lgp;
+    const int total = d.nkx << lgp;
     for (int i = KS_TID; i < total; i += KS_NT) {
-        const int j = i / npairs;
-        const int pr = i - j * npairs;
+        const int j = i >> lgp;
+        const int pr = i & (npairs - 1);
         const cpx<R> yj = Y[(size_t)pr * nx + j];
         const cpx<R> ym = conj(Y[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
-        const cpx<R> s = yj + ym;   // 2 X^a
+        const cpx<R> sm = yj + ym;  // 2 X^a
         const cpx<R> df = yj - ym;  // 2 i X^b
         cpx<R>* col = Mb + (size_t)j * ns + n0 + 2 * pr;
-        col[0] = scale(s, h);
+        col[0] = scale(sm, h);
         col[1] = mk<R>(df.y * h, -df.x * h);
     }
 }
@@ -310,7 +358,8 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
     }
     const int nx = d.nx, lgnx = d.lgnx, kx = d.kx;
     const int ns = p.ns[b];
-    const int n0 = it.n0, nr = it.nr, npairs = nr >> 1;
+    const int n0 = it.n0, nr = it.nr, lgnr = it.lgnr;
+    const int lgp = lgnr - 1, npairs = nr >> 1;
     cpx<R>* A = reinterpret_cast<cpx<R>*>(smem);
     cpx<R>* Bf = A + (size_t)nr * nx;
     cpx<R>* Mb = p.M + p.moff[b];
@@ -328,12 +377,10 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         }
         KS_SYNC();
         cpx<R>* Y = fft_batch(A, Bf, lgnx, npairs, -1, p.tw);
-        store_pair_spectra(d, Y, Mb, ns, n0, npairs);
+        store_pair_spectra(d, Y, Mb, ns, n0, lgp);
         KS_SYNC();
-        return;
-    }
-    if constexpr (MODE == ROW_SYNTH) {
-        load_pair_spectra(d, Mb, ns, n0, npairs, A, false, p.qv);
+    } else if constexpr (MODE == ROW_SYNTH) {
+        load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
         cpx<R>* z = fft_batch(A, Bf, lgnx, npairs, +1, p.tw);
         const int total = npairs * nx;
@@ -345,22 +392,18 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             ra[nx + m] = z[i].y;
         }
         KS_SYNC();
-        return;
-    }
-    if constexpr (MODE == ROW_NONLIN) {
+    } else if constexpr (MODE == ROW_NONLIN) {
         // z = u + i u_x per row: Z_j = (1 - q_j) v_j, Z_{-j} = (1 + q_j) conj(v_j)   (a1, a2)
         const int total = nr * nx;
         for (int i = KS_TID; i < total; i += KS_NT) {
-            const int J = i / nr;
-            const int r = i - J * nr;
+            const int J = i >> lgnr;
+            const int r = i & (nr - 1);
             cpx<R> z = mk<R>(0, 0);
             if (J <= kx) {
-                const R q = p.qv[J];
-                z = scale(Mb[(size_t)J * ns + n0 + r], (R)1 - q);
+                z = scale(Mb[(size_t)J * ns + n0 + r], (R)1 - p.qv[J]);
             } else if (J >= nx - kx) {
                 const int j = nx - J;
-                const R q = p.qv[j];
-                z = scale(conj(Mb[(size_t)j * ns + n0 + r]), (R)1 + q);
+                z = scale(conj(Mb[(size_t)j * ns + n0 + r]), (R)1 + p.qv[j]);
             }
             A[(size_t)r * nx + J] = z;
         }
@@ -381,13 +424,11 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         }
         KS_SYNC();
         cpx<R>* F = fft_batch(Y, z, lgnx, npairs, -1, p.tw);  // a4 (x-pass)
-        store_pair_spectra(d, F, Mb, ns, n0, npairs);
+        store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
-        return;
-    }
-    if constexpr (MODE == ROW_ADJ) {
-        // r_x rows from i q_j rho_j (rho already carries i q_j from the column pass)  (a7)
-        load_pair_spectra(d, Mb, ns, n0, npairs, A, false, p.qv);
+    } else if constexpr (MODE == ROW_ADJ) {
+        // r_x rows from the column pass output rho = s-inverse of i q_j r_hat   (a7)
+        load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
         cpx<R>* z = fft_batch(A, Bf, lgnx, npairs, +1, p.tw);
         cpx<R>* Y = (z == A) ? Bf : A;
@@ -401,9 +442,8 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         }
         KS_SYNC();
         cpx<R>* F = fft_batch(Y, z, lgnx, npairs, -1, p.tw);
-        store_pair_spectra(d, F, Mb, ns, n0, npairs);
+        store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
-        return;
     }
 }
 
@@ -420,8 +460,11 @@ enum ColMode {
     COL_GRAD = 6      // M = W -> G_hat band (no update)
 };
 
+// Shared-memory bytes a column item needs beyond its two transform buffers.
+constexpr int COL_RED_DOUBLES = 2 * (256 / 32 + 1) + 4;
+
 template <typename R, int MODE>
-KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem) {
+KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem, int par) {
     const int nkx = d.nkx;
     const int b = p.colorder[item / nkx];
     const int j = item - (item / nkx) * nkx;
@@ -433,8 +476,10 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
     cpx<R>* col = p.M + p.moff[b] + (size_t)j * ns;
     const size_t bo = (size_t)p.boff[b] + (size_t)j * nk;
     const int B = d.B;
-    const double* Tc = p.T + (size_t)p.par * B;
-    double* Tn = p.T + (size_t)(p.par ^ 1) * B;
+    const double* Tc = p.T + (size_t)par * B;
+    double* Tn = p.T + (size_t)(par ^ 1) * B;
+    const double* wTc = p.wT + (size_t)par * B;
+    double* wTn = p.wT + (size_t)(par ^ 1) * B;
 
     if constexpr (MODE == COL_RESID || MODE == COL_GRAD) {
         if (!loop_live(p, b)) return;
@@ -442,7 +487,10 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
     if constexpr (MODE == COL_UPDATE) {
         if (p.check_active && p.prec[b] != p.myprec) return;
         if (p.check_active && p.status[b] != ST_RUNNING) {
-            if (j == 0 && KS_TID == 0) Tn[b] = Tc[b];
+            if (j == 0 && KS_TID == 0) {
+                Tn[b] = Tc[b];
+                wTn[b] = wTc[b];
+            }
             return;
         }
     }
@@ -457,14 +505,13 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         cpx<R>* v = fft_batch(A, Bf, lg, 1, +1, p.tw);
         for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
         KS_SYNC();
-        return;
     } else {
         // the remaining modes start with a forward s-transform of the column of M
         for (int i = KS_TID; i < ns; i += KS_NT) A[i] = col[i];
         KS_SYNC();
         cpx<R>* F = fft_batch(A, Bf, lg, 1, -1, p.tw);
         cpx<R>* X = (F == A) ? Bf : A;
-        const R ins = (R)(1.0 / (double)ns);
+        const R ins = p.insv[b];
 
         if constexpr (MODE == COL_ANALYZE) {
             for (int kk = KS_TID; kk < nk; kk += KS_NT) {
@@ -475,16 +522,14 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             return;
         }
 
-        const double T = Tc[b];
-        const double q = qj(d, j);
-        const R a_lin = (R)(q * q - q * q * q * q);   // q^2 - q^4 (from -u_xx - u_xxxx)
-        const R w_over_T = (R)(2.0 * 3.14159265358979323846 / T);  // omega_k / T = k * (2 pi / T)
-        const R rq = (R)q;
-        const double wj = (j == 0) ? 1.0 : 2.0;      // x-conjugate pairs counted twice
+        const R a_lin = p.lin[j];       // q^2 - q^4 (from -u_xx - u_xxxx)
+        const R w_over_T = (R)wTc[b];   // omega_k / T = k * (2 pi / T)
+        const R rq = p.qv[j];
+        const double wj = (j == 0) ? 1.0 : 2.0;  // x-conjugate pairs counted twice
 
         if constexpr (MODE == COL_RESID) {
-            double sJ = 0.0, sL = 0.0;
-            R pJ = 0, pL = 0;
+            R pJ = 0;
+            double pL = 0.0;
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
                 cpx<R> x = mk<R>(0, 0);
@@ -496,13 +541,14 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
                     p.rh[bo + (k + ks)] = r;
                     pJ += r.x * r.x + r.y * r.y;              // a6
-                    pL += (R)k * (u.x * r.y - u.y * r.x);      // omega_k Im(conj(u) r) / (2 pi)
+                    // omega_k Im(conj(u) r) / (2 pi), accumulated in double: the sum over k
+                    // cancels strongly, so float terms would lose its leading digits
+                    pL += (double)k * ((double)u.x * (double)r.y - (double)u.y * (double)r.x);
                     x = mk<R>(-rq * r.y, rq * r.x);           // i q_j r_hat                 (a7)
                 }
                 X[i] = x;
             }
-            sJ = (double)pJ;
-            sL = (double)pL;
+            double sJ = (double)pJ, sL = pL;
             KS_SYNC();
             cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
@@ -512,10 +558,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 p.L2part[(size_t)b * nkx + j] = wj * sL;
             }
             KS_SYNC();
-            return;
-        }
-
-        if constexpr (MODE == COL_GRAD) {
+        } else if constexpr (MODE == COL_GRAD) {
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
                 if (k >= -ks && k <= ks) {
@@ -526,35 +569,36 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 }
             }
             KS_SYNC();
-            return;
-        }
-
-        if constexpr (MODE == COL_UPDATE) {
-            // J and L^dag_2 of this loop from the column partials (same fixed order in every CTA)
-            double J = 0.0, L2 = 0.0;
-            const double* jp = p.Jpart + (size_t)b * nkx;
-            const double* lp = p.L2part + (size_t)b * nkx;
-            for (int c = 0; c < nkx; ++c) {
-                J += jp[c];
-                L2 += lp[c];
+        } else if constexpr (MODE == COL_UPDATE) {
+            // J and L^dag_2 of this loop from the column partials: warp 0 sums them in a fixed
+            // order (identical in every CTA of the loop, so all CTAs take the same decision)
+            const double T = Tc[b];
+            if (KS_TID < 32) {
+                double sJ, sL;
+                warp_sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
+                if (KS_TID == 0) {
+                    red[0] = sJ * d.L;
+                    red[1] = sL * d.L * wTc[b] / T;  // (L / T^2) * 2 pi * sum
+                }
             }
-            J *= d.L;
-            L2 *= d.L * 2.0 * 3.14159265358979323846 / (T * T);
-            const double sq = sqrt(J);
+            KS_SYNC();
+            const double J = red[0], L2 = red[1];
             int st = ST_RUNNING;
             if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
-            else if (sq < p.tol) st = ST_CONVERGED;
-            else if (p.myprec == 1 && p.switch_tol > 0.0 && sq <= p.switch_tol) st = ST_SWITCH;
-            if (j == 0 && KS_TID == 0) p.sqrtJ[b] = sq;
+            else if (J < p.tol * p.tol) st = ST_CONVERGED;
+            else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
+            if (j == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
             if (st != ST_RUNNING) {
                 if (j == 0 && KS_TID == 0) {
                     p.status[b] = st;
                     Tn[b] = T;
+                    wTn[b] = wTc[b];
                 }
+                KS_SYNC();
                 return;
             }
             const R dt = (R)d.dtau;
-            const double cq = q * q * q * q * (q * q - 1.0) * (q * q - 1.0);  // q^4 (q^2 - 1)^2
+            const R cqj = p.cq[j];
             const R wT2 = w_over_T * w_over_T;
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
@@ -569,7 +613,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     if (d.scheme == 1) {
                         // IMEX: dtau / (1 - dtau Lambda), Lambda = -(omega/T)^2 - q^4 (q^2-1)^2  (a10)
                         const R kk2 = (R)k * (R)k;
-                        f = dt / ((R)1 + dt * (kk2 * wT2 + (R)cq));
+                        f = dt / ((R)1 + dt * (kk2 * wT2 + cqj));
                     }
                     cpx<R> u = p.uh[bo + (k + ks)];
                     u = u - scale(G, f);
@@ -582,11 +626,12 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             if (j == 0 && KS_TID == 0) {
-                Tn[b] = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
+                const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
+                Tn[b] = Tnew;
+                wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
                 p.steps[b] += 1;
             }
             KS_SYNC();
-            return;
         }
     }
 }

@@ -32,7 +32,96 @@ __global__ void __launch_bounds__(256) k_rows(Dims d, Bufs<R> p, int nitems) {
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) k_cols(Dims d, Bufs<R> p, int nitems) {
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) col_item<R, MODE>(d, p, it, smem);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) col_item<R, MODE>(d, p, it, smem, p.par);
+}
+
+// float grid -> double grid
+__global__ void k_grid_f2d(const float* src, double* dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+// double band -> float band (every loop)
+__global__ void k_band_d2f(const cpx<double>* src, cpx<float>* dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = mk<float>((float)src[i].x, (float)src[i].y);
+}
+
+// 2 pi / T for parity 0 after a state load
+__global__ void k_prep_wT(const double* T, double* wT, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) wT[b] = 2.0 * 3.14159265358979323846 / T[b];
+}
+
+// ---- grid-wide barrier with a bounded wait -------------------------------------------------
+// Sense-free generation barrier: each CTA reads the generation, arrives on the counter; the
+// last arrival resets the counter and bumps the generation.  Waiters give up after
+// KS_SPIN_LIMIT polls (about a second), set the error word and leave; every CTA then returns
+// at its next barrier, so an inconsistent launch ends instead of hanging.
+struct GridBar {
+    unsigned int* count;
+    unsigned int* gen;
+    int* err;
+};
+
+#define KS_SPIN_LIMIT (1u << 23)
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_sync(const GridBar& g) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int my = ld_acquire_gpu(g.gen);
+        __threadfence();
+        const unsigned int a = atomicAdd(g.count, 1u);
+        int good = 1;
+        if (a == gridDim.x - 1) {
+            atomicExch(g.count, 0u);
+            __threadfence();
+            atomicAdd(g.gen, 1u);
+        } else {
+            unsigned int it = 0;
+            while (ld_acquire_gpu(g.gen) == my) {
+                if (++it > KS_SPIN_LIMIT) {
+                    atomicExch(g.err, 1);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)g.err) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// All phases of nsteps tau-steps in one cooperative launch: every CTA walks the row items,
+// barrier, the column items, barrier, ... (four phases per step).
+template <typename R>
+__global__ void __launch_bounds__(256) k_persist(Dims d, Bufs<R> p, int nsteps, int par0,
+                                                 int nrow, int ncol, GridBar bar) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int s = 0; s < nsteps; ++s) {
+        const int par = (par0 + s) & 1;
+        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_NONLIN>(d, p, it, smem);
+        if (!grid_sync(bar)) return;
+        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_RESID>(d, p, it, smem, par);
+        if (!grid_sync(bar)) return;
+        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ>(d, p, it, smem);
+        if (!grid_sync(bar)) return;
+        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_UPDATE>(d, p, it, smem, par);
+        if (s + 1 < nsteps && !grid_sync(bar)) return;
+    }
 }
 
 // J = L sum_j Jpart, dJ/dT = 2 L^dag_2 = 2 (2 pi L / T^2) sum_j L2part, per loop.
@@ -108,6 +197,7 @@ struct Work {
     void* U[2] = {nullptr, nullptr};
     void* io[2] = {nullptr, nullptr};
     double* T = nullptr;       // [2][B]
+    double* wT = nullptr;      // [2][B] 2 pi / T
     double* Jpart = nullptr;   // [B][nkx]
     double* L2part = nullptr;  // [B][nkx]
     int* status = nullptr;
@@ -154,6 +244,15 @@ struct ks_loop {
     RowItem* d_rows = nullptr;
     void* d_tw[2] = {nullptr, nullptr};
     void* d_qv[2] = {nullptr, nullptr};
+    void* d_lin[2] = {nullptr, nullptr};
+    void* d_cq[2] = {nullptr, nullptr};
+    void* d_insv[2] = {nullptr, nullptr};
+    // persistent kernel
+    bool persistent = true;
+    int pgrid[2] = {0, 0};
+    size_t psmem[2] = {0, 0};
+    unsigned int* d_bar = nullptr;  // count, gen
+    int* d_err = nullptr;
     Work st;   // resident descent state
     Work api;  // scratch for ks_residual / ks_adjoint_grad
     Launch lrow[2], lcol[2];
@@ -250,6 +349,8 @@ int alloc_work(ks_loop* h, Work& w, const bool* precs) {
     void* p = nullptr;
     KS_TRY(dev_alloc(h, &p, 2 * B * sizeof(double)));
     w.T = (double*)p;
+    KS_TRY(dev_alloc(h, &p, 2 * B * sizeof(double)));
+    w.wT = (double*)p;
     KS_TRY(dev_alloc(h, &p, (size_t)B * h->d.nkx * sizeof(double)));
     w.Jpart = (double*)p;
     KS_TRY(dev_alloc(h, &p, (size_t)B * h->d.nkx * sizeof(double)));
@@ -292,6 +393,7 @@ Bufs<R> make_bufs(ks_loop* h, const Work& w, int pr, int check_active, double to
     p.U = (R*)w.U[pr];
     p.io = io;
     p.T = w.T;
+    p.wT = w.wT;
     p.Jpart = w.Jpart;
     p.L2part = w.L2part;
     p.status = w.status;
@@ -300,6 +402,9 @@ Bufs<R> make_bufs(ks_loop* h, const Work& w, int pr, int check_active, double to
     p.sqrtJ = w.sqrtJ;
     p.tw = (const cpx<R>*)h->d_tw[pr];
     p.qv = (const R*)h->d_qv[pr];
+    p.lin = (const R*)h->d_lin[pr];
+    p.cq = (const R*)h->d_cq[pr];
+    p.insv = (const R*)h->d_insv[pr];
     p.rows = h->d_rows;
     p.colorder = h->d_colorder;
     p.myprec = pr;
@@ -404,6 +509,41 @@ int set_smem_attrs(ks_loop* h) {
     return KS_OK;
 }
 
+// co-resident grid size and shared memory of the persistent kernel of one precision
+template <typename R>
+int setup_persistent(ks_loop* h) {
+    const int pr = std::is_same<R, double>::value ? P64 : P32;
+    const size_t sm = std::max(h->lrow[pr].smem, h->lcol[pr].smem);
+    KS_CUDA(cudaFuncSetAttribute(k_persist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0, sms = 0, coop = 0;
+    KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R>, 128, sm));
+    KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    KS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
+    const int items = std::max((int)h->rows.size(), h->d.B * h->d.nkx);
+    h->psmem[pr] = sm;
+    h->pgrid[pr] = (coop && per_sm > 0) ? std::min(items, per_sm * sms) : 0;
+    return KS_OK;
+}
+
+// nsteps tau-steps of the live loops of precision pr in one cooperative launch
+template <typename R>
+int run_persist(ks_loop* h, Work& w, int pr, long long nsteps, double tol, double switch_tol,
+                cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 1, tol, switch_tol, (R*)nullptr);
+    Dims d = h->d;
+    int ns_i = (int)nsteps;
+    int par0 = w.par;
+    int nrow = (int)h->rows.size();
+    int ncol = h->d.B * h->d.nkx;
+    GridBar bar{h->d_bar, h->d_bar + 1, h->d_err};
+    void* args[] = {&d, &p, &ns_i, &par0, &nrow, &ncol, &bar};
+    LaunchScope ls(h, s, std::string("persist") + prec_suffix(pr));
+    KS_CUDA(cudaLaunchCooperativeKernel((const void*)k_persist<R>, dim3(h->pgrid[pr]), dim3(128),
+                                        args, h->psmem[pr], s));
+    ls.done();
+    return KS_OK;
+}
+
 // grid -> band (u_hat) for every loop, from io
 template <typename R>
 int run_analyze(ks_loop* h, Work& w, int pr, R* io, cudaStream_t s) {
@@ -502,19 +642,35 @@ int check_handle(ks_loop* h) {
 }
 
 // load [P u; T] into workspace w in precision pr (io holds u already when io_loaded)
+// The projection onto the band always runs in double: a float field is widened first and the
+// projected band is rounded to float afterwards, so the band of a float handle carries only
+// the rounding of its coefficients, not the transform noise of a float analysis.
 int load_state(ks_loop* h, Work& w, int pr, const void* u, const double* T, cudaStream_t s) {
     const size_t gb = (size_t)h->ngrid * elem_size(pr);
-    const void* usrc = u;
     void* io = w.io[pr];
     if (is_device_ptr(u)) {
         io = const_cast<void*>(u);
     } else {
-        KS_TRY(copy_in(io, usrc, gb, s));
+        KS_TRY(copy_in(io, u, gb, s));
     }
     KS_TRY(copy_in(w.T, T, h->d.B * sizeof(double), s));
     w.par = 0;
-    if (pr == P64) KS_TRY(run_analyze<double>(h, w, pr, (double*)io, s));
-    else KS_TRY(run_analyze<float>(h, w, pr, (float*)io, s));
+    k_prep_wT<<<(h->d.B + 127) / 128, 128, 0, s>>>(w.T, w.wT, h->d.B);
+    KS_CUDA(cudaGetLastError());
+    if (pr == P64) {
+        KS_TRY(run_analyze<double>(h, w, P64, (double*)io, s));
+    } else {
+        const long long n = h->ngrid;
+        const int g = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+        k_grid_f2d<<<g, 256, 0, s>>>((const float*)io, (double*)w.io[P64], n);
+        KS_CUDA(cudaGetLastError());
+        KS_TRY(run_analyze<double>(h, w, P64, (double*)w.io[P64], s));
+        const long long nb = h->nband;
+        k_band_d2f<<<(int)std::max<long long>(1, std::min<long long>((nb + 255) / 256, 152 * 8)), 256, 0, s>>>(
+            (const cpx<double>*)w.uh[P64], (cpx<float>*)w.uh[P32], nb);
+        KS_CUDA(cudaGetLastError());
+        w.mix_valid[P32] = false;
+    }
     return KS_OK;
 }
 
@@ -566,6 +722,7 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     h->d.L = cfg->L;
     h->d.dtau = cfg->dtau;
     h->d.scheme = cfg->scheme;
+    h->d.hx = 0.5 / (double)cfg->nx;
     h->mode = cfg->mode;
     h->tol = cfg->tol;
     h->switch_tol = cfg->switch_tol;
@@ -595,14 +752,20 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     h->nband = bo;
     h->nmix = mo;
     h->ngrid = go;
-    // row tiles: rows_per_tile rows of one loop (even, divides Ns); two double tile buffers of
-    // rows_per_tile x Nx complex values stay within 96 KB of shared memory
-    h->rows_per_tile = 8;
-    while (h->rows_per_tile > 2 && 2 * (size_t)h->rows_per_tile * cfg->nx * sizeof(cpx<double>) > 96 * 1024)
-        h->rows_per_tile >>= 1;
+    // row tiles: rows_per_tile rows of one loop (even power of two, divides Ns).  Two double
+    // tile buffers of rows_per_tile x Nx complex values stay within 96 KB of shared memory, and
+    // small batches get smaller tiles so that at least two row items exist per SM.
+    {
+        long long rows_total = go / cfg->nx;
+        h->rows_per_tile = 8;
+        while (h->rows_per_tile > 2 &&
+               (2 * (size_t)h->rows_per_tile * cfg->nx * sizeof(cpx<double>) > 96 * 1024 ||
+                rows_total / h->rows_per_tile < 2 * 152))
+            h->rows_per_tile >>= 1;
+    }
     for (int b = 0; b < B; ++b) {
         const int nr = std::min(h->rows_per_tile, h->ns[b]);
-        for (int n0 = 0; n0 < h->ns[b]; n0 += nr) h->rows.push_back(RowItem{b, n0, nr, 0});
+        for (int n0 = 0; n0 < h->ns[b]; n0 += nr) h->rows.push_back(RowItem{b, n0, nr, ilog2(nr)});
     }
     // columns: longest loops first
     h->colorder.resize(B);
@@ -634,26 +797,55 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
             t32[t].x = (float)re[t];
             t32[t].y = (float)im[t];
         }
-        std::vector<double> q64(h->d.nkx);
-        std::vector<float> q32(h->d.nkx);
+        // per retained x-mode: q_j, q_j^2 - q_j^4, q_j^4 (q_j^2 - 1)^2; per loop: 1 / Ns
+        std::vector<double> q64(h->d.nkx), l64(h->d.nkx), c64(h->d.nkx), i64v(B);
+        std::vector<float> q32(h->d.nkx), l32(h->d.nkx), c32(h->d.nkx), i32v(B);
         for (int j = 0; j < h->d.nkx; ++j) {
-            q64[j] = 2.0 * 3.14159265358979323846 * (double)j / h->d.L;
+            const double q = 2.0 * 3.14159265358979323846 * (double)j / h->d.L;
+            q64[j] = q;
+            l64[j] = q * q - q * q * q * q;
+            c64[j] = q * q * q * q * (q * q - 1.0) * (q * q - 1.0);
             q32[j] = (float)q64[j];
+            l32[j] = (float)l64[j];
+            c32[j] = (float)c64[j];
+        }
+        for (int b = 0; b < B; ++b) {
+            i64v[b] = 1.0 / (double)h->ns[b];
+            i32v[b] = (float)i64v[b];
         }
         cpx<double>* p64 = nullptr;
         cpx<float>* p32 = nullptr;
-        double* qq64 = nullptr;
-        float* qq32 = nullptr;
+        double *qq64 = nullptr, *ll64 = nullptr, *cc64 = nullptr, *ii64 = nullptr;
+        float *qq32 = nullptr, *ll32 = nullptr, *cc32 = nullptr, *ii32 = nullptr;
         if ((rc = upload(h, &p64, t64)) || (rc = upload(h, &p32, t32)) ||
-            (rc = upload(h, &qq64, q64)) || (rc = upload(h, &qq32, q32)))
+            (rc = upload(h, &qq64, q64)) || (rc = upload(h, &qq32, q32)) ||
+            (rc = upload(h, &ll64, l64)) || (rc = upload(h, &ll32, l32)) ||
+            (rc = upload(h, &cc64, c64)) || (rc = upload(h, &cc32, c32)) ||
+            (rc = upload(h, &ii64, i64v)) || (rc = upload(h, &ii32, i32v)))
             return cleanup(rc);
         h->d_tw[P64] = p64;
         h->d_tw[P32] = p32;
         h->d_qv[P64] = qq64;
         h->d_qv[P32] = qq32;
+        h->d_lin[P64] = ll64;
+        h->d_lin[P32] = ll32;
+        h->d_cq[P64] = cc64;
+        h->d_cq[P32] = cc32;
+        h->d_insv[P64] = ii64;
+        h->d_insv[P32] = ii32;
+        void* pb = nullptr;
+        if ((rc = dev_alloc(h, &pb, 4 * sizeof(unsigned int)))) return cleanup(rc);
+        h->d_bar = (unsigned int*)pb;
+        if ((rc = dev_alloc(h, &pb, sizeof(int)))) return cleanup(rc);
+        h->d_err = (int*)pb;
+        if (cudaMemset(h->d_bar, 0, 4 * sizeof(unsigned int)) != cudaSuccess ||
+            cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess)
+            return cleanup(fail(KS_ERR_CUDA, "barrier init failed"));
     }
-    bool api_need[2] = {h->api_prec == P64, h->api_prec == P32};
-    if ((rc = alloc_work(h, h->st, h->need)) || (rc = alloc_work(h, h->api, api_need)))
+    // double buffers always exist: every projection onto the band runs in double
+    bool st_need[2] = {true, h->need[P32]};
+    bool api_need[2] = {true, h->api_prec == P32};
+    if ((rc = alloc_work(h, h->st, st_need)) || (rc = alloc_work(h, h->api, api_need)))
         return cleanup(rc);
     // launch shapes
     for (int pr = 0; pr < 2; ++pr) {
@@ -664,10 +856,11 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
         lr.grid = 152 * 16;
         Launch& lc = h->lcol[pr];
         lc.threads = 128;
-        lc.smem = 2 * (size_t)h->nsmax * cs + (2 * lc.threads + 2) * sizeof(double);
+        lc.smem = 2 * (size_t)h->nsmax * cs + COL_RED_DOUBLES * sizeof(double);
         lc.grid = 152 * 16;
     }
     if ((rc = set_smem_attrs<double>(h)) || (rc = set_smem_attrs<float>(h))) return cleanup(rc);
+    if ((rc = setup_persistent<double>(h)) || (rc = setup_persistent<float>(h))) return cleanup(rc);
     h->h_status.assign(B, 0);
     h->h_prec.assign(B, 0);
     h->h_sqrtJ.assign(B, 0.0);
@@ -746,11 +939,6 @@ int start_prec(ks_loop* h) { return h->mode == KS_FP32 || h->mode == KS_MIXED ? 
 
 }  // namespace
 
-__global__ void k_band_d2f(const cpx<double>* src, cpx<float>* dst, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        dst[i] = mk<float>((float)src[i].x, (float)src[i].y);
-}
 
 // dst[b] = band of loop b in double, taken from the float band for loops running in float
 __global__ void k_band_merge(const cpx<float>* s32, const cpx<double>* s64, cpx<double>* dst,
@@ -808,6 +996,20 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s) {
         }
     }
     const double swt = (h->mode == KS_MIXED) ? h->switch_tol : 0.0;
+    const bool pers[2] = {h->persistent && h->pgrid[P64] > 0, h->persistent && h->pgrid[P32] > 0};
+    if ((!live[P32] || pers[P32]) && (!live[P64] || pers[P64])) {
+        // loops are independent, so each precision's kernel may run all n steps in turn; both
+        // start from the same parity and frozen loops carry T forward in either kernel
+        const long long kMaxPerLaunch = 1 << 14;
+        for (long long done = 0; done < n;) {
+            const long long c = std::min(kMaxPerLaunch, n - done);
+            if (live[P32]) KS_TRY(run_persist<float>(h, w, P32, c, tol, swt, s));
+            if (live[P64]) KS_TRY(run_persist<double>(h, w, P64, c, tol, 0.0, s));
+            if (c & 1) w.par ^= 1;
+            done += c;
+        }
+        return KS_OK;
+    }
     for (long long i = 0; i < n; ++i) {
         if (live[P32]) KS_TRY(run_step<float>(h, w, P32, tol, swt, s));
         if (live[P64]) KS_TRY(run_step<double>(h, w, P64, tol, 0.0, s));
@@ -822,7 +1024,16 @@ int readback(ks_loop* h, cudaStream_t s) {
     KS_CUDA(cudaMemcpyAsync(h->h_status.data(), w.status, B * sizeof(int), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaMemcpyAsync(h->h_sqrtJ.data(), w.sqrtJ, B * sizeof(double), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaMemcpyAsync(h->h_steps.data(), w.steps, B * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    int err = 0;
+    KS_CUDA(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+        // a bounded barrier wait gave up: clear the barrier for the next launch and report it
+        KS_CUDA(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), s));
+        KS_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+        KS_CUDA(cudaStreamSynchronize(s));
+        return fail(KS_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
+    }
     return KS_OK;
 }
 
@@ -1066,4 +1277,26 @@ extern "C" int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long
         h->launches = 0;
     }
     return k;
+}
+
+extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!key) return fail(KS_ERR_ARG, "null option name");
+    const std::string k(key);
+    if (k == "persistent") {
+        h->persistent = value != 0;
+    } else if (k == "stall_window") {
+        if (value < 1) return fail(KS_ERR_ARG, "stall_window must be >= 1");
+        h->stall_window = value;
+    } else if (k == "stall_drop_ppm") {
+        if (value < 0 || value >= 1000000) return fail(KS_ERR_ARG, "stall_drop_ppm in [0, 1e6)");
+        h->stall_drop = (double)value * 1e-6;
+    } else if (k == "chunk") {
+        if (value < 1) return fail(KS_ERR_ARG, "chunk must be >= 1");
+        h->chunk = (int)std::min<long long>(value, 1 << 30);
+    } else {
+        return fail(KS_ERR_ARG, "unknown option " + k);
+    }
+    return KS_OK;
 }
