@@ -173,6 +173,11 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *   "chunk"          tau-steps between read-backs in ks_descend */
 KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
 
+/* Read a knob or a derived launch parameter: "path", "cluster_f64", "cluster_f32" (cluster
+ * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
+ * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk". */
+KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
+
 /* Message for the last non-zero return on the calling thread ("" if none). */
 KS_API const char* ks_last_error(void);
 

@@ -1,0 +1,345 @@
+// ks_cluster.cuh - cluster-resident tau-descent: one thread-block cluster per loop.
+//
+// A loop's whole working set lives in the distributed shared memory of one cluster of C CTAs
+// (C = 1, 2, 4, 8 or 16) for a chunk of tau-steps:
+//   * column j (retained x-mode, 0..Kx) is owned by rank j % C, slot j / C: its band values
+//     u_hat, r_hat and its mixed-array column M[j][n] (n = 0..Ns-1) sit in that rank's SMEM;
+//   * rows n are split in contiguous blocks of Ns / C rows per rank (at least two); a rank
+//     keeps the grid values of u for its rows between the two row phases.
+// The four phases of a tau-step (see ks_items.cuh) exchange data through DSMEM: a row phase
+// gathers the columns' values for its rows from the owners and scatters its results back.
+// Phases are separated by hardware cluster barriers; there is no grid-wide synchronisation
+// and no global-memory round trip inside a step.  Every rank sums the column partials of J
+// and L^dag_2 (broadcast to all ranks) in the same fixed order, so all ranks take the same
+// freeze decision and advance T identically.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "ks_items.cuh"
+
+namespace ks {
+
+namespace cgx = cooperative_groups;
+
+// Shared-memory plan of one cluster launch (byte offsets into the dynamic shared memory).
+struct ClusterPlan {
+    int C;        // cluster size
+    int rt;       // rows per x-transform batch (even power of two)
+    int ncmax;    // max columns per rank
+    int nsmax;    // max Ns over the batch
+    int nkmax;    // max 2 Ks + 1
+    int rmax;     // max rows per rank
+    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red;
+    int bytes;
+    int u_global;  // 1: the rank's grid rows of u live in global memory (U array), not SMEM
+};
+
+// FFT of `cnt` columns stored [q][n] at `a` with `b` as scratch; the result is left in `a`.
+template <typename R>
+__device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
+                                                const cpx<R>* tw) {
+    cpx<R>* r = fft_batch(a, b, lg, cnt, dir, tw);
+    if (r != a) {
+        const int n = cnt << lg;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = r[i];
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan cp, int nsteps,
+                                                 int par0, int use_M) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int C = cp.C;
+    const int rank = (int)cl.block_rank();
+    const int cid = blockIdx.x / C;
+    const int ncl = gridDim.x / C;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nx = d.nx, lgnx = d.lgnx, kx = d.kx, nkx = d.nkx, B = d.B;
+    cpx<R>* Mloc = reinterpret_cast<cpx<R>*>(smem + cp.off_M);
+    cpx<R>* uhl = reinterpret_cast<cpx<R>*>(smem + cp.off_uh);
+    cpx<R>* rhl = reinterpret_cast<cpx<R>*>(smem + cp.off_rh);
+    R* Ul = reinterpret_cast<R*>(smem + cp.off_U);  // rows of u kept between the row phases
+    cpx<R>* scr = reinterpret_cast<cpx<R>*>(smem + cp.off_scr);
+    double* part = reinterpret_cast<double*>(smem + cp.off_part);  // [2][nkx]: J, L2 partials
+    double* red = reinterpret_cast<double*>(smem + cp.off_red);
+    const R h = (R)d.hx;
+
+    for (int bi = cid; bi < B; bi += ncl) {
+        const int b = p.colorder[bi];
+        // every rank reads the same global words: the skip is uniform across the cluster
+        if (p.prec[b] != p.myprec || p.status[b] != ST_RUNNING) {
+            if (rank == 0 && tid == 0 && p.status[b] != ST_RUNNING) {
+                p.T[(size_t)(par0 ^ 1) * B + b] = p.T[(size_t)par0 * B + b];
+                p.wT[(size_t)(par0 ^ 1) * B + b] = p.wT[(size_t)par0 * B + b];
+            }
+            continue;
+        }
+        const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b], nk = 2 * ks + 1;
+        const int ncol = (rank < nkx) ? (nkx - rank + C - 1) / C : 0;
+        const int rpr = max(2, ns / C);                  // rows per rank
+        const int row0 = rank * rpr;
+        const int nrow = (row0 < ns) ? min(rpr, ns - row0) : 0;
+        const R ins = p.insv[b];
+        const size_t bo = (size_t)p.boff[b];
+        cpx<R>* Mg = p.M + p.moff[b];
+        double T = p.T[(size_t)par0 * B + b];
+        double wT = p.wT[(size_t)par0 * B + b];
+        if (cp.u_global) Ul = p.U + p.goff[b] + (size_t)row0 * nx;
+
+        // ---- load the band (and the mixed columns, or prime them) --------------------
+        for (int i = tid; i < ncol * nk; i += nt) {
+            const int q = i / nk, kk = i - q * nk;
+            uhl[i] = p.uh[bo + (size_t)(rank + q * C) * nk + kk];
+        }
+        if (use_M) {
+            for (int i = tid; i < ncol << lg; i += nt) {
+                const int q = i >> lg, n = i & (ns - 1);
+                Mloc[i] = Mg[(size_t)(rank + q * C) * ns + n];
+            }
+            __syncthreads();
+        } else {
+            __syncthreads();
+            for (int i = tid; i < ncol << lg; i += nt) {
+                const int q = i >> lg, n = i & (ns - 1);
+                const int k = (n < (ns >> 1)) ? n : n - ns;
+                Mloc[i] = (k >= -ks && k <= ks) ? uhl[q * nk + k + ks] : mk<R>(0, 0);
+            }
+            __syncthreads();
+            col_fft_inplace(Mloc, scr, lg, ncol, +1, p.tw);
+        }
+        cl.sync();
+
+        int done = 0;
+        int st = ST_RUNNING;
+        double Jlast = 0.0;
+        for (int s = 0; s < nsteps; ++s) {
+            // ======== phase A: rows, z = u + i u_x, U, p = u u_x, forward (a1-a4) ========
+            for (int t0 = 0; t0 < nrow; t0 += cp.rt) {
+                const int nr = min(cp.rt, nrow - t0);
+                int lgnr = 0;
+                while ((1 << lgnr) < nr) ++lgnr;
+                const int n0 = row0 + t0;
+                cpx<R>* A = scr;
+                cpx<R>* Bf = scr + (size_t)nr * nx;
+                for (int i = tid; i < nr * nx; i += nt) {
+                    const int J = i >> lgnr, r = i & (nr - 1);
+                    cpx<R> z = mk<R>(0, 0);
+                    if (J <= kx) {
+                        const cpx<R>* src = cl.map_shared_rank(Mloc, J % C) + (size_t)(J / C) * ns;
+                        z = scale(src[n0 + r], (R)1 - p.qv[J]);
+                    } else if (J >= nx - kx) {
+                        const int j = nx - J;
+                        const cpx<R>* src = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns;
+                        z = scale(conj(src[n0 + r]), (R)1 + p.qv[j]);
+                    }
+                    A[(size_t)r * nx + J] = z;
+                }
+                __syncthreads();
+                cpx<R>* z = fft_batch(A, Bf, lgnx, nr, +1, p.tw);
+                cpx<R>* Y = (z == A) ? Bf : A;
+                const int np = nr >> 1;
+                for (int i = tid; i < np * nx; i += nt) {
+                    const int pr = i >> lgnx, m = i & (nx - 1);
+                    const cpx<R> za = z[(size_t)(2 * pr) * nx + m];
+                    const cpx<R> zb = z[(size_t)(2 * pr + 1) * nx + m];
+                    Ul[(size_t)(t0 + 2 * pr) * nx + m] = za.x;
+                    Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] = zb.x;
+                    Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
+                }
+                __syncthreads();
+                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, p.tw);
+                for (int i = tid; i < nkx * np; i += nt) {
+                    const int j = i / np, pr = i - j * np;
+                    const cpx<R> yj = F[(size_t)pr * nx + j];
+                    const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
+                    const cpx<R> sm = yj + ym, df = yj - ym;
+                    cpx<R>* dst = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
+                    dst[0] = scale(sm, h);
+                    dst[1] = mk<R>(df.y * h, -df.x * h);
+                }
+                __syncthreads();
+            }
+            cl.sync();
+
+            // ======== phase B: columns, r_hat, partials, rho = s-inverse of i q r_hat ========
+            if (ncol > 0) {
+                col_fft_inplace(Mloc, scr, lg, ncol, -1, p.tw);
+                const R wTr = (R)wT;
+                for (int q = 0; q < ncol; ++q) {
+                    const int j = rank + q * C;
+                    const R a_lin = p.lin[j], rq = p.qv[j];
+                    R pJ = 0;
+                    double pL = 0.0;
+                    for (int n = tid; n < ns; n += nt) {
+                        const int k = (n < (ns >> 1)) ? n : n - ns;
+                        cpx<R> x = mk<R>(0, 0);
+                        if (k >= -ks && k <= ks) {
+                            const cpx<R> ph = scale(Mloc[(q << lg) + n], ins);
+                            const cpx<R> u = uhl[q * nk + k + ks];
+                            const R bk = -(R)k * wTr;
+                            const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
+                            rhl[q * nk + k + ks] = r;
+                            pJ += r.x * r.x + r.y * r.y;
+                            pL += (double)k * ((double)u.x * (double)r.y - (double)u.y * (double)r.x);
+                            x = mk<R>(-rq * r.y, rq * r.x);
+                        }
+                        scr[(q << lg) + n] = x;
+                    }
+                    double sJ = (double)pJ, sL = pL;
+                    block_sum2(red, sJ, sL);
+                    if (tid < C) {
+                        const double wj = (j == 0) ? 1.0 : 2.0;
+                        double* dstp = cl.map_shared_rank(part, tid);
+                        dstp[j] = wj * sJ;
+                        dstp[nkx + j] = wj * sL;
+                    }
+                }
+                __syncthreads();
+                // inverse of i q r_hat: scr holds the spectra, Mloc is scratch
+                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, p.tw);
+                if (v != Mloc) {
+                    for (int i = tid; i < ncol << lg; i += nt) Mloc[i] = v[i];
+                    __syncthreads();
+                }
+            }
+            cl.sync();
+
+            // ======== phase A': rows, r_x, w = u r_x, forward (a7, a8) ========
+            for (int t0 = 0; t0 < nrow; t0 += cp.rt) {
+                const int nr = min(cp.rt, nrow - t0);
+                const int np = nr >> 1;
+                int lgp = 0;
+                while ((1 << lgp) < np) ++lgp;
+                const int n0 = row0 + t0;
+                cpx<R>* A = scr;
+                cpx<R>* Bf = scr + (size_t)nr * nx;
+                for (int i = tid; i < np * nx; i += nt) {
+                    const int J = i >> lgp, pr = i & (np - 1);
+                    cpx<R> z = mk<R>(0, 0);
+                    int j = -1;
+                    bool neg = false;
+                    if (J <= kx) {
+                        j = J;
+                    } else if (J >= nx - kx) {
+                        j = nx - J;
+                        neg = true;
+                    }
+                    if (j >= 0) {
+                        const cpx<R>* src = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
+                        cpx<R> xa = src[0], xb = src[1];
+                        if (neg) {
+                            xa = conj(xa);
+                            xb = conj(xb);
+                        }
+                        z = xa + mul_i(xb, 1);
+                    }
+                    A[(size_t)pr * nx + J] = z;
+                }
+                __syncthreads();
+                cpx<R>* z = fft_batch(A, Bf, lgnx, np, +1, p.tw);
+                cpx<R>* Y = (z == A) ? Bf : A;
+                for (int i = tid; i < np * nx; i += nt) {
+                    const int pr = i >> lgnx, m = i & (nx - 1);
+                    const cpx<R> rx = z[i];
+                    Y[i] = mk<R>(Ul[(size_t)(t0 + 2 * pr) * nx + m] * rx.x,
+                                 Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
+                }
+                __syncthreads();
+                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, p.tw);
+                for (int i = tid; i < nkx * np; i += nt) {
+                    const int j = i / np, pr = i - j * np;
+                    const cpx<R> yj = F[(size_t)pr * nx + j];
+                    const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
+                    const cpx<R> sm = yj + ym, df = yj - ym;
+                    cpx<R>* dst = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
+                    dst[0] = scale(sm, h);
+                    dst[1] = mk<R>(df.y * h, -df.x * h);
+                }
+                __syncthreads();
+            }
+            cl.sync();
+
+            // ======== phase B': J, L2, freeze test, G_hat, update, v = s-inverse (a9, a10) ===
+            if (tid < 32) {
+                double sJ, sL;
+                warp_sum_partials(part, part + nkx, nkx, sJ, sL);
+                if (tid == 0) {
+                    red[0] = sJ * d.L;
+                    red[1] = sL * d.L * wT / T;
+                }
+            }
+            __syncthreads();
+            const double J = red[0], L2 = red[1];
+            __syncthreads();
+            Jlast = J;
+            if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
+            else if (J < p.tol * p.tol) st = ST_CONVERGED;
+            else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
+            if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
+            if (ncol > 0) {
+                col_fft_inplace(Mloc, scr, lg, ncol, -1, p.tw);
+                const R wTr = (R)wT;
+                const R dt = (R)d.dtau;
+                const R wT2 = wTr * wTr;
+                for (int i = tid; i < ncol << lg; i += nt) {
+                    const int q = i >> lg, n = i & (ns - 1);
+                    const int k = (n < (ns >> 1)) ? n : n - ns;
+                    cpx<R> x = mk<R>(0, 0);
+                    if (k >= -ks && k <= ks) {
+                        const int j = rank + q * C;
+                        const R a_lin = p.lin[j];
+                        const cpx<R> wh = scale(Mloc[i], ins);
+                        const cpx<R> r = rhl[q * nk + k + ks];
+                        const R bk = (R)k * wTr;
+                        const cpx<R> G = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                        R f = dt;
+                        if (d.scheme == 1) {
+                            const R kk2 = (R)k * (R)k;
+                            f = dt / ((R)1 + dt * (kk2 * wT2 + p.cq[j]));
+                        }
+                        cpx<R> u = uhl[q * nk + k + ks];
+                        u = u - scale(G, f);
+                        uhl[q * nk + k + ks] = u;
+                        x = u;
+                    }
+                    scr[i] = x;
+                }
+                __syncthreads();
+                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, p.tw);
+                if (v != Mloc) {
+                    for (int i = tid; i < ncol << lg; i += nt) Mloc[i] = v[i];
+                    __syncthreads();
+                }
+            }
+            T = T - d.dtau * L2;
+            wT = 2.0 * 3.14159265358979323846 / T;
+            ++done;
+            cl.sync();
+        }
+
+        // ---- write the loop back -------------------------------------------------------
+        for (int i = tid; i < ncol * nk; i += nt) {
+            const int q = i / nk, kk = i - q * nk;
+            p.uh[bo + (size_t)(rank + q * C) * nk + kk] = uhl[i];
+        }
+        for (int i = tid; i < ncol << lg; i += nt) {
+            const int q = i >> lg, n = i & (ns - 1);
+            Mg[(size_t)(rank + q * C) * ns + n] = Mloc[i];
+        }
+        if (rank == 0 && tid == 0) {
+            p.T[(size_t)par0 * B + b] = T;
+            p.T[(size_t)(par0 ^ 1) * B + b] = T;
+            p.wT[(size_t)par0 * B + b] = wT;
+            p.wT[(size_t)(par0 ^ 1) * B + b] = wT;
+            p.steps[b] += done;
+            if (done > 0 || st != ST_RUNNING) p.sqrtJ[b] = sqrt(Jlast);
+            if (st != ST_RUNNING) p.status[b] = st;
+        }
+        cl.sync();
+    }
+}
+
+}  // namespace ks

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "ks_cluster.cuh"
 #include "ks_items.cuh"
 #include "ks_loop.h"
 
@@ -247,6 +248,13 @@ struct ks_loop {
     void* d_lin[2] = {nullptr, nullptr};
     void* d_cq[2] = {nullptr, nullptr};
     void* d_insv[2] = {nullptr, nullptr};
+    // launch path: 0 = cluster-resident kernel when its plan fits, else 1; 1 = grid-persistent
+    // cooperative kernel; 2 = four launches per tau-step
+    int path = 0;
+    int force_cluster = 0;          // 0: choose the cluster size; else use this one
+    ClusterPlan cplan[2] = {};      // per precision; C = 0 when the cluster path is unavailable
+    int cthreads = 128;
+    int cgrid[2] = {0, 0};
     // persistent kernel
     bool persistent = true;
     int pgrid[2] = {0, 0};
@@ -522,6 +530,113 @@ int setup_persistent(ks_loop* h) {
     const int items = std::max((int)h->rows.size(), h->d.B * h->d.nkx);
     h->psmem[pr] = sm;
     h->pgrid[pr] = (coop && per_sm > 0) ? std::min(items, per_sm * sms) : 0;
+    return KS_OK;
+}
+
+// Shared-memory plan of the cluster kernel for cluster size C (bytes = 0 if it cannot fit).
+template <typename R>
+ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_limit) {
+    ClusterPlan cp{};
+    const size_t cs = sizeof(cpx<R>), rs = sizeof(R);
+    const int nx = h->d.nx, nkx = h->d.nkx;
+    cp.C = C;
+    cp.ncmax = (nkx + C - 1) / C;
+    cp.nsmax = h->nsmax;
+    cp.nkmax = 2 * (h->nsmax / 3) + 1;
+    int nsmin = h->nsmax;
+    for (int v : h->ns) nsmin = std::min(nsmin, v);
+    cp.rmax = std::max(2, h->nsmax / C);
+    int rt = 2;
+    while (rt * 2 <= std::min(cp.rmax, 16) && 2 * (size_t)(rt * 2) * nx * cs <= 32 * 1024) rt *= 2;
+    cp.rt = rt;
+    cp.u_global = u_global;
+    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    size_t off = 0;
+    cp.off_M = (int)off;
+    off += al((size_t)cp.ncmax * cp.nsmax * cs);
+    cp.off_uh = (int)off;
+    off += al((size_t)cp.ncmax * cp.nkmax * cs);
+    cp.off_rh = (int)off;
+    off += al((size_t)cp.ncmax * cp.nkmax * cs);
+    cp.off_U = (int)off;
+    if (!u_global) off += al((size_t)cp.rmax * nx * rs);
+    cp.off_scr = (int)off;
+    off += al(std::max((size_t)cp.ncmax * cp.nsmax, (size_t)2 * rt * nx) * cs);
+    cp.off_part = (int)off;
+    off += al((size_t)2 * nkx * sizeof(double));
+    cp.off_red = (int)off;
+    off += al((size_t)COL_RED_DOUBLES * sizeof(double));
+    cp.bytes = (off <= (size_t)smem_limit) ? (int)off : 0;
+    return cp;
+}
+
+// pick the cluster size: enough CTAs to cover the GPU (about two per SM), at most 16, and a
+// plan that fits shared memory (grid rows of u in global memory if needed)
+template <typename R>
+int setup_cluster(ks_loop* h) {
+    const int pr = std::is_same<R, double>::value ? P64 : P32;
+    h->cplan[pr] = ClusterPlan{};
+    int limit = 0, sms = 0;
+    KS_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+    KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    int target = 16;
+    while (target > 1 && (long long)target * h->d.B > 2LL * sms) target >>= 1;
+    if (h->force_cluster) target = h->force_cluster;
+    KS_CUDA(cudaFuncSetAttribute(k_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int C = target; C >= 1; C >>= 1) {
+        for (int ug = 0; ug < 2; ++ug) {
+            ClusterPlan cp = make_cluster_plan<R>(h, C, ug, limit);
+            if (!cp.bytes) continue;
+            KS_CUDA(cudaFuncSetAttribute(k_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(h->cthreads);
+            cfg.dynamicSmemBytes = cp.bytes;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_cluster<R>, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                ncl = 0;
+            }
+            if (ncl <= 0) continue;
+            h->cplan[pr] = cp;
+            h->cgrid[pr] = C * std::min(h->d.B, ncl);
+            return KS_OK;
+        }
+        if (h->force_cluster) break;
+    }
+    return KS_OK;
+}
+
+// nsteps tau-steps of the live loops of precision pr, one cluster per loop
+template <typename R>
+int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, double switch_tol,
+                cudaStream_t s) {
+    Bufs<R> p = make_bufs<R>(h, w, pr, 1, tol, switch_tol, (R*)nullptr);
+    const ClusterPlan& cp = h->cplan[pr];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->cgrid[pr]);
+    cfg.blockDim = dim3(h->cthreads);
+    cfg.dynamicSmemBytes = cp.bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cp.C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    LaunchScope ls(h, s, std::string("cluster") + prec_suffix(pr));
+    KS_CUDA(cudaLaunchKernelEx(&cfg, k_cluster<R>, h->d, p, cp, (int)nsteps, w.par,
+                               w.mix_valid[pr] ? 1 : 0));
+    ls.done();
+    w.mix_valid[pr] = true;
     return KS_OK;
 }
 
@@ -861,6 +976,7 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     }
     if ((rc = set_smem_attrs<double>(h)) || (rc = set_smem_attrs<float>(h))) return cleanup(rc);
     if ((rc = setup_persistent<double>(h)) || (rc = setup_persistent<float>(h))) return cleanup(rc);
+    if ((rc = setup_cluster<double>(h)) || (rc = setup_cluster<float>(h))) return cleanup(rc);
     h->h_status.assign(B, 0);
     h->h_prec.assign(B, 0);
     h->h_sqrtJ.assign(B, 0.0);
@@ -990,17 +1106,29 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s) {
     for (int b = 0; b < h->d.B; ++b)
         if (h->h_status[b] == KS_RUNNING) live[h->h_prec[b]] = true;
     for (int pr = 0; pr < 2; ++pr) {
-        if (live[pr] && !w.mix_valid[pr]) {
+        const bool clus_pr = h->path == 0 && h->cplan[pr].bytes > 0;
+        if (live[pr] && !w.mix_valid[pr] && !clus_pr) {
             if (pr == P64) KS_TRY(run_prime<double>(h, w, pr, s));
             else KS_TRY(run_prime<float>(h, w, pr, s));
         }
     }
     const double swt = (h->mode == KS_MIXED) ? h->switch_tol : 0.0;
-    const bool pers[2] = {h->persistent && h->pgrid[P64] > 0, h->persistent && h->pgrid[P32] > 0};
+    const long long kMaxPerLaunch = 1 << 14;
+    const bool clus[2] = {h->path == 0 && h->cplan[P64].bytes > 0, h->path == 0 && h->cplan[P32].bytes > 0};
+    if ((!live[P32] || clus[P32]) && (!live[P64] || clus[P64])) {
+        for (long long done = 0; done < n;) {
+            const long long c = std::min(kMaxPerLaunch, n - done);
+            if (live[P32]) KS_TRY(run_cluster<float>(h, w, P32, c, tol, swt, s));
+            if (live[P64]) KS_TRY(run_cluster<double>(h, w, P64, c, tol, 0.0, s));
+            if (c & 1) w.par ^= 1;
+            done += c;
+        }
+        return KS_OK;
+    }
+    const bool pers[2] = {h->path <= 1 && h->pgrid[P64] > 0, h->path <= 1 && h->pgrid[P32] > 0};
     if ((!live[P32] || pers[P32]) && (!live[P64] || pers[P64])) {
         // loops are independent, so each precision's kernel may run all n steps in turn; both
         // start from the same parity and frozen loops carry T forward in either kernel
-        const long long kMaxPerLaunch = 1 << 14;
         for (long long done = 0; done < n;) {
             const long long c = std::min(kMaxPerLaunch, n - done);
             if (live[P32]) KS_TRY(run_persist<float>(h, w, P32, c, tol, swt, s));
@@ -1285,7 +1413,18 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
     if (!key) return fail(KS_ERR_ARG, "null option name");
     const std::string k(key);
     if (k == "persistent") {
-        h->persistent = value != 0;
+        h->path = value ? 1 : 2;
+    } else if (k == "path") {
+        if (value < 0 || value > 2) return fail(KS_ERR_ARG, "path must be 0, 1 or 2");
+        h->path = (int)value;
+    } else if (k == "cluster") {
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(KS_ERR_ARG, "cluster must be 0 (auto), 1, 2, 4, 8 or 16");
+        h->force_cluster = (int)value;
+        KS_TRY(setup_cluster<double>(h));
+        KS_TRY(setup_cluster<float>(h));
+        if (value && (h->cplan[0].C != value && h->cplan[1].C != value))
+            return fail(KS_ERR_ARG, "requested cluster size does not fit this batch");
     } else if (k == "stall_window") {
         if (value < 1) return fail(KS_ERR_ARG, "stall_window must be >= 1");
         h->stall_window = value;
@@ -1298,5 +1437,22 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
     } else {
         return fail(KS_ERR_ARG, "unknown option " + k);
     }
+    return KS_OK;
+}
+
+extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!key || !value) return fail(KS_ERR_ARG, "null argument");
+    const std::string k(key);
+    if (k == "path") *value = h->path;
+    else if (k == "cluster_f64") *value = h->cplan[0].bytes ? h->cplan[0].C : 0;
+    else if (k == "cluster_f32") *value = h->cplan[1].bytes ? h->cplan[1].C : 0;
+    else if (k == "cluster_smem_f64") *value = h->cplan[0].bytes;
+    else if (k == "cluster_smem_f32") *value = h->cplan[1].bytes;
+    else if (k == "rows_per_tile") *value = h->rows_per_tile;
+    else if (k == "stall_window") *value = h->stall_window;
+    else if (k == "chunk") *value = h->chunk;
+    else return fail(KS_ERR_ARG, "unknown option " + k);
     return KS_OK;
 }

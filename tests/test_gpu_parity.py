@@ -255,3 +255,33 @@ def test_mixed_descent_converges_and_switches():
     # the float bulk takes about as many steps as the double descent
     for b in range(2):
         assert abs(res[K.KS_MIXED][1][b] - res[K.KS_FP64][1][b]) < 0.2 * res[K.KS_FP64][1][b]
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+@pytest.mark.parametrize("nx,nss", [(64, [128]), (32, [32, 16, 64]), (64, [32, 64, 128, 256]),
+                                    (16, [8])])
+@pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
+def test_cluster_kernel_equals_phase_launches(mode, nx, nss, C):
+    """The cluster-resident kernel (one cluster of C CTAs per loop, distributed shared memory)
+    reproduces the per-phase launches bit for bit, including across chunk boundaries."""
+    L = 22.0
+    us, Ts = make(nx, nss, L)
+    outs = []
+    for path in (0, 2):
+        u, T = dev_tensors(us, Ts, mode)
+        steps = torch.zeros(len(nss), dtype=torch.int64, device="cuda")
+        sq = torch.zeros(len(nss), dtype=torch.float64, device="cuda")
+        with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15, chunk=5) as h:
+            K.ks_set_option(h.handle, "path", path)
+            if path == 0:
+                try:
+                    K.ks_set_option(h.handle, "cluster", C)
+                except K.KsError:
+                    pytest.skip(f"cluster size {C} does not fit")
+                key = "cluster_f32" if mode == K.KS_FP32 else "cluster_f64"
+                if K.ks_get_option(h.handle, key) != C:
+                    pytest.skip(f"cluster size {C} does not fit this precision")
+            K.ks_descend(h.handle, u, T, 13, 0.0, steps, sq)
+        outs.append((u.cpu(), T.cpu(), steps.cpu(), sq.cpu()))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
