@@ -1,17 +1,19 @@
 // ks_cluster.cuh - cluster-resident tau-descent: one thread-block cluster per loop.
 //
 // A loop's whole working set lives in the distributed shared memory of one cluster of C CTAs
-// (C = 1, 2, 4, 8 or 16) for a chunk of tau-steps:
+// (1 <= C <= 16) for a chunk of tau-steps:
 //   * column j (retained x-mode, 0..Kx) is owned by rank j % C, slot j / C: its band values
 //     u_hat, r_hat and its mixed-array column M[j][n] (n = 0..Ns-1) sit in that rank's SMEM;
-//   * rows n are split in contiguous blocks of Ns / C rows per rank (at least two); a rank
-//     keeps the grid values of u for its rows between the two row phases.
+//   * rows n are split in contiguous blocks of an even number of rows per rank; a rank keeps
+//     the grid values of u for its rows between the two row phases (in SMEM, or in the global
+//     U array when the plan cannot hold them).
 // The four phases of a tau-step (see ks_items.cuh) exchange data through DSMEM: a row phase
 // gathers the columns' values for its rows from the owners and scatters its results back.
 // Phases are separated by hardware cluster barriers; there is no grid-wide synchronisation
-// and no global-memory round trip inside a step.  Every rank sums the column partials of J
-// and L^dag_2 (broadcast to all ranks) in the same fixed order, so all ranks take the same
-// freeze decision and advance T identically.
+// and no global-memory round trip inside a step.  Column owners broadcast their partials of
+// J and L^dag_2 to every rank; every rank sums them in the same fixed order, so all ranks
+// take the same freeze decision and advance T identically.  The per-element arithmetic and
+// the reduction orders are those of the per-phase items, so results agree bit for bit.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -25,15 +27,22 @@ namespace cgx = cooperative_groups;
 // Shared-memory plan of one cluster launch (byte offsets into the dynamic shared memory).
 struct ClusterPlan {
     int C;        // cluster size
-    int rt;       // rows per x-transform batch (even power of two)
+    int rt;       // largest row batch of one x-transform call (even power of two)
     int ncmax;    // max columns per rank
     int nsmax;    // max Ns over the batch
     int nkmax;    // max 2 Ks + 1
     int rmax;     // max rows per rank
-    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red;
+    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red, off_tw;
     int bytes;
     int u_global;  // 1: the rank's grid rows of u live in global memory (U array), not SMEM
 };
+
+// rows per rank: an even number covering Ns with C ranks
+__host__ __device__ inline int cluster_rows_per_rank(int ns, int C) {
+    int r = (ns + C - 1) / C;
+    r += (r & 1);
+    return r < 2 ? 2 : r;
+}
 
 // FFT of `cnt` columns stored [q][n] at `a` with `b` as scratch; the result is left in `a`.
 template <typename R>
@@ -50,6 +59,7 @@ __device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, in
 template <typename R>
 __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan cp, int nsteps,
                                                  int par0, int use_M) {
+    typedef typename PartT<R>::type Part;
     extern __shared__ __align__(16) unsigned char smem[];
     cgx::cluster_group cl = cgx::this_cluster();
     const int C = cp.C;
@@ -61,11 +71,15 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
     cpx<R>* Mloc = reinterpret_cast<cpx<R>*>(smem + cp.off_M);
     cpx<R>* uhl = reinterpret_cast<cpx<R>*>(smem + cp.off_uh);
     cpx<R>* rhl = reinterpret_cast<cpx<R>*>(smem + cp.off_rh);
-    R* Ul = reinterpret_cast<R*>(smem + cp.off_U);  // rows of u kept between the row phases
+    R* const Us = reinterpret_cast<R*>(smem + cp.off_U);  // rows of u kept between row phases
     cpx<R>* scr = reinterpret_cast<cpx<R>*>(smem + cp.off_scr);
-    double* part = reinterpret_cast<double*>(smem + cp.off_part);  // [2][nkx]: J, L2 partials
+    Part* part = reinterpret_cast<Part*>(smem + cp.off_part);  // [2][nkx]: J, L2 partials
     double* red = reinterpret_cast<double*>(smem + cp.off_red);
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem + cp.off_tw);
     const R h = (R)d.hx;
+
+    for (int i = tid; i < NMAX; i += nt) tws[i] = p.tw[i];
+    __syncthreads();
 
     for (int bi = cid; bi < B; bi += ncl) {
         const int b = p.colorder[bi];
@@ -79,15 +93,15 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
         }
         const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b], nk = 2 * ks + 1;
         const int ncol = (rank < nkx) ? (nkx - rank + C - 1) / C : 0;
-        const int rpr = max(2, ns / C);                  // rows per rank
+        const int rpr = cluster_rows_per_rank(ns, C);
         const int row0 = rank * rpr;
         const int nrow = (row0 < ns) ? min(rpr, ns - row0) : 0;
         const R ins = p.insv[b];
         const size_t bo = (size_t)p.boff[b];
         cpx<R>* Mg = p.M + p.moff[b];
+        R* Ul = cp.u_global ? p.U + p.goff[b] + (size_t)row0 * nx : Us;
         double T = p.T[(size_t)par0 * B + b];
         double wT = p.wT[(size_t)par0 * B + b];
-        if (cp.u_global) Ul = p.U + p.goff[b] + (size_t)row0 * nx;
 
         // ---- load the band (and the mixed columns, or prime them) --------------------
         for (int i = tid; i < ncol * nk; i += nt) {
@@ -108,7 +122,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                 Mloc[i] = (k >= -ks && k <= ks) ? uhl[q * nk + k + ks] : mk<R>(0, 0);
             }
             __syncthreads();
-            col_fft_inplace(Mloc, scr, lg, ncol, +1, p.tw);
+            col_fft_inplace(Mloc, scr, lg, ncol, +1, tws);
         }
         cl.sync();
 
@@ -117,10 +131,12 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
         double Jlast = 0.0;
         for (int s = 0; s < nsteps; ++s) {
             // ======== phase A: rows, z = u + i u_x, U, p = u u_x, forward (a1-a4) ========
-            for (int t0 = 0; t0 < nrow; t0 += cp.rt) {
-                const int nr = min(cp.rt, nrow - t0);
-                int lgnr = 0;
-                while ((1 << lgnr) < nr) ++lgnr;
+            for (int t0 = 0; t0 < nrow;) {
+                int nr = 2, lgnr = 1;
+                while (nr * 2 <= cp.rt && nr * 2 <= nrow - t0) {
+                    nr *= 2;
+                    ++lgnr;
+                }
                 const int n0 = row0 + t0;
                 cpx<R>* A = scr;
                 cpx<R>* Bf = scr + (size_t)nr * nx;
@@ -138,7 +154,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     A[(size_t)r * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<R>* z = fft_batch(A, Bf, lgnx, nr, +1, p.tw);
+                cpx<R>* z = fft_batch(A, Bf, lgnx, nr, +1, tws);
                 cpx<R>* Y = (z == A) ? Bf : A;
                 const int np = nr >> 1;
                 for (int i = tid; i < np * nx; i += nt) {
@@ -150,9 +166,10 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, p.tw);
-                for (int i = tid; i < nkx * np; i += nt) {
-                    const int j = i / np, pr = i - j * np;
+                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, tws);
+                const int lgp = lgnr - 1;
+                for (int i = tid; i < (nkx << lgp); i += nt) {
+                    const int j = i >> lgp, pr = i & (np - 1);
                     const cpx<R> yj = F[(size_t)pr * nx + j];
                     const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<R> sm = yj + ym, df = yj - ym;
@@ -161,18 +178,18 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     dst[1] = mk<R>(df.y * h, -df.x * h);
                 }
                 __syncthreads();
+                t0 += nr;
             }
             cl.sync();
 
             // ======== phase B: columns, r_hat, partials, rho = s-inverse of i q r_hat ========
             if (ncol > 0) {
-                col_fft_inplace(Mloc, scr, lg, ncol, -1, p.tw);
+                col_fft_inplace(Mloc, scr, lg, ncol, -1, tws);
                 const R wTr = (R)wT;
                 for (int q = 0; q < ncol; ++q) {
                     const int j = rank + q * C;
                     const R a_lin = p.lin[j], rq = p.qv[j];
-                    R pJ = 0;
-                    double pL = 0.0;
+                    ColAcc<R> acc;
                     for (int n = tid; n < ns; n += nt) {
                         const int k = (n < (ns >> 1)) ? n : n - ns;
                         cpx<R> x = mk<R>(0, 0);
@@ -182,24 +199,22 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                             const R bk = -(R)k * wTr;
                             const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
                             rhl[q * nk + k + ks] = r;
-                            pJ += r.x * r.x + r.y * r.y;
-                            pL += (double)k * ((double)u.x * (double)r.y - (double)u.y * (double)r.x);
+                            acc.add(u, r, k);
                             x = mk<R>(-rq * r.y, rq * r.x);
                         }
                         scr[(q << lg) + n] = x;
                     }
-                    double sJ = (double)pJ, sL = pL;
-                    block_sum2(red, sJ, sL);
+                    block_reduce(acc, red);
                     if (tid < C) {
                         const double wj = (j == 0) ? 1.0 : 2.0;
-                        double* dstp = cl.map_shared_rank(part, tid);
-                        dstp[j] = wj * sJ;
-                        dstp[nkx + j] = wj * sL;
+                        Part* dstp = cl.map_shared_rank(part, tid);
+                        dstp[j] = acc.part_J(wj);
+                        dstp[nkx + j] = acc.part_L(wj);
                     }
                 }
                 __syncthreads();
                 // inverse of i q r_hat: scr holds the spectra, Mloc is scratch
-                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, p.tw);
+                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, tws);
                 if (v != Mloc) {
                     for (int i = tid; i < ncol << lg; i += nt) Mloc[i] = v[i];
                     __syncthreads();
@@ -208,11 +223,13 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
             cl.sync();
 
             // ======== phase A': rows, r_x, w = u r_x, forward (a7, a8) ========
-            for (int t0 = 0; t0 < nrow; t0 += cp.rt) {
-                const int nr = min(cp.rt, nrow - t0);
+            for (int t0 = 0; t0 < nrow;) {
+                int nr = 2, lgp = 0;
+                while (nr * 2 <= cp.rt && nr * 2 <= nrow - t0) {
+                    nr *= 2;
+                    ++lgp;
+                }
                 const int np = nr >> 1;
-                int lgp = 0;
-                while ((1 << lgp) < np) ++lgp;
                 const int n0 = row0 + t0;
                 cpx<R>* A = scr;
                 cpx<R>* Bf = scr + (size_t)nr * nx;
@@ -239,7 +256,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     A[(size_t)pr * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<R>* z = fft_batch(A, Bf, lgnx, np, +1, p.tw);
+                cpx<R>* z = fft_batch(A, Bf, lgnx, np, +1, tws);
                 cpx<R>* Y = (z == A) ? Bf : A;
                 for (int i = tid; i < np * nx; i += nt) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
@@ -248,9 +265,9 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                                  Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, p.tw);
-                for (int i = tid; i < nkx * np; i += nt) {
-                    const int j = i / np, pr = i - j * np;
+                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, tws);
+                for (int i = tid; i < (nkx << lgp); i += nt) {
+                    const int j = i >> lgp, pr = i & (np - 1);
                     const cpx<R> yj = F[(size_t)pr * nx + j];
                     const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<R> sm = yj + ym, df = yj - ym;
@@ -259,20 +276,26 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     dst[1] = mk<R>(df.y * h, -df.x * h);
                 }
                 __syncthreads();
+                t0 += nr;
             }
             cl.sync();
 
             // ======== phase B': J, L2, freeze test, G_hat, update, v = s-inverse (a9, a10) ===
+            // warp 0 sums the partials; thread 0 forms J, L^dag_2 and the next T, 2 pi / T
             if (tid < 32) {
                 double sJ, sL;
-                warp_sum_partials(part, part + nkx, nkx, sJ, sL);
+                sum_partials(part, part + nkx, nkx, sJ, sL);
                 if (tid == 0) {
-                    red[0] = sJ * d.L;
-                    red[1] = sL * d.L * wT / T;
+                    const double J = sJ * d.L;
+                    const double L2 = sL * d.L * wT / T;  // (L / T^2) 2 pi sum
+                    const double Tn = T - d.dtau * L2;    // explicit Euler for T (Sec. 4.2)
+                    red[0] = J;
+                    red[1] = Tn;
+                    red[2] = 2.0 * 3.14159265358979323846 / Tn;
                 }
             }
             __syncthreads();
-            const double J = red[0], L2 = red[1];
+            const double J = red[0], Tnext = red[1], wTnext = red[2];
             __syncthreads();
             Jlast = J;
             if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
             else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
             if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
             if (ncol > 0) {
-                col_fft_inplace(Mloc, scr, lg, ncol, -1, p.tw);
+                col_fft_inplace(Mloc, scr, lg, ncol, -1, tws);
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;
@@ -308,14 +331,14 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     scr[i] = x;
                 }
                 __syncthreads();
-                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, p.tw);
+                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, tws);
                 if (v != Mloc) {
                     for (int i = tid; i < ncol << lg; i += nt) Mloc[i] = v[i];
                     __syncthreads();
                 }
             }
-            T = T - d.dtau * L2;
-            wT = 2.0 * 3.14159265358979323846 / T;
+            T = Tnext;
+            wT = wTnext;
             ++done;
             cl.sync();
         }

@@ -84,6 +84,80 @@ KS_HD cpx<R> scale(cpx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
 template <typename R>
 KS_HD cpx<R> mul_i(cpx<R> a, int sgn) { return sgn > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
 
+// ---- compensated float arithmetic (error-free transformations) -----------------------------
+// A float-float value hi + lo (|lo| <= ulp(hi) / 2).  Sums use Knuth's TwoSum, products use an
+// FMA to recover the rounding error of a * b exactly.  The float path keeps its reductions of
+// J and L^dag_2 in this form, on the FP32 pipe, and widens only the final value to double.
+struct ff {
+    float hi, lo;
+};
+KS_HD ff two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    ff r;
+    r.hi = s;
+    r.lo = e;
+    return r;
+}
+KS_HD ff ff_add(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    const float e = s.lo + (a.lo + b.lo);
+    return two_sum(s.hi, e);
+}
+KS_HD ff two_prod(float a, float b) {
+    const float p = a * b;
+    ff r;
+    r.hi = p;
+    r.lo = fmaf(a, b, -p);
+    return r;
+}
+
+// Per-column partial of the two reductions: double, or float-float in the float path (8 bytes
+// either way, so one buffer serves both precisions).
+template <typename R>
+struct PartT {
+    typedef double type;
+};
+template <>
+struct PartT<float> {
+    typedef ff type;
+};
+
+// Per-thread accumulation of |r_hat|^2 and k Im(conj(u_hat) r_hat) over the modes of one column.
+template <typename R>
+struct ColAcc;
+template <>
+struct ColAcc<double> {
+    double J = 0.0, L = 0.0;
+    KS_HD void add(cpx<double> u, cpx<double> r, int k) {
+        J += r.x * r.x + r.y * r.y;
+        L += (double)k * (u.x * r.y - u.y * r.x);
+    }
+    KS_HD double part_J(double wj) const { return wj * J; }
+    KS_HD double part_L(double wj) const { return wj * L; }
+};
+template <>
+struct ColAcc<float> {
+    ff J = {0.f, 0.f}, L = {0.f, 0.f};
+    KS_HD void add(cpx<float> u, cpx<float> r, int k) {
+        J = ff_add(J, ff_add(two_prod(r.x, r.x), two_prod(r.y, r.y)));
+        ff q = two_prod(u.y, r.x);
+        q.hi = -q.hi;
+        q.lo = -q.lo;
+        const ff d = ff_add(two_prod(u.x, r.y), q);
+        const float kf = (float)k;  // exact: |k| < 2^24
+        ff t = two_prod(kf, d.hi);
+        t.lo = fmaf(kf, d.lo, t.lo);
+        L = ff_add(L, t);
+    }
+    KS_HD ff part_J(double wj) const { return wj == 1.0 ? J : ff{2.f * J.hi, 2.f * J.lo}; }
+    KS_HD ff part_L(double wj) const { return wj == 1.0 ? L : ff{2.f * L.hi, 2.f * L.lo}; }
+};
+
+KS_HD double widen(double v) { return v; }
+KS_HD double widen(ff v) { return (double)v.hi + (double)v.lo; }
+
 struct RowItem {
     int b, n0, nr, lgnr;  // loop, first row, rows in the tile (even power of two), log2 nr
 };
@@ -116,8 +190,8 @@ struct Bufs {
     R* io;                  // grid in/out for analysis / synthesis items
     double* T;              // [2][B] period, double-buffered by step parity
     double* wT;             // [2][B] 2 pi / T, same parity as T
-    double* Jpart;          // [B][nkx] per-column partial of sum w_j |r_hat|^2
-    double* L2part;         // [B][nkx] per-column partial of sum w_j w_k Im(conj(u_hat) r_hat)
+    typename PartT<R>::type* Jpart;   // [B][nkx] per-column partial of sum w_j |r_hat|^2
+    typename PartT<R>::type* L2part;  // [B][nkx] per-column partial of sum w_j k Im(conj(u_hat) r_hat)
     int* status;            // [B]
     const int* prec;        // [B] 0 double, 1 float: the precision the loop currently runs in
     long long* steps;       // [B]
@@ -279,6 +353,101 @@ KS_HD void warp_sum_partials(const double* a, const double* c, int n, double& sa
     }
     sa = x;
     sc = y;
+#endif
+}
+
+// Block-wide reduction of the per-thread column sums (result valid in every thread).
+KS_HD void block_reduce(ColAcc<double>& a, double* red) { block_sum2(red, a.J, a.L); }
+
+KS_HD void block_reduce(ColAcc<float>& a, double* redd) {
+#ifdef KS_HOST_EMULATION
+    (void)a;
+    (void)redd;
+#else
+    float* red = reinterpret_cast<float*>(redd);
+    for (int o = 16; o > 0; o >>= 1) {
+        ff bJ, bL;
+        bJ.hi = __shfl_xor_sync(0xffffffffu, a.J.hi, o);
+        bJ.lo = __shfl_xor_sync(0xffffffffu, a.J.lo, o);
+        bL.hi = __shfl_xor_sync(0xffffffffu, a.L.hi, o);
+        bL.lo = __shfl_xor_sync(0xffffffffu, a.L.lo, o);
+        a.J = ff_add(a.J, bJ);
+        a.L = ff_add(a.L, bL);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) {
+        red[4 * w] = a.J.hi;
+        red[4 * w + 1] = a.J.lo;
+        red[4 * w + 2] = a.L.hi;
+        red[4 * w + 3] = a.L.lo;
+    }
+    __syncthreads();
+    if (w == 0) {
+        ff J = {0.f, 0.f}, L = {0.f, 0.f};
+        if (l < nw) {
+            J.hi = red[4 * l];
+            J.lo = red[4 * l + 1];
+            L.hi = red[4 * l + 2];
+            L.lo = red[4 * l + 3];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ff bJ, bL;
+            bJ.hi = __shfl_xor_sync(0xffffffffu, J.hi, o);
+            bJ.lo = __shfl_xor_sync(0xffffffffu, J.lo, o);
+            bL.hi = __shfl_xor_sync(0xffffffffu, L.hi, o);
+            bL.lo = __shfl_xor_sync(0xffffffffu, L.lo, o);
+            J = ff_add(J, bJ);
+            L = ff_add(L, bL);
+        }
+        if (l == 0) {
+            red[4 * nw] = J.hi;
+            red[4 * nw + 1] = J.lo;
+            red[4 * nw + 2] = L.hi;
+            red[4 * nw + 3] = L.lo;
+        }
+    }
+    __syncthreads();
+    a.J.hi = red[4 * nw];
+    a.J.lo = red[4 * nw + 1];
+    a.L.hi = red[4 * nw + 2];
+    a.L.lo = red[4 * nw + 3];
+    __syncthreads();
+#endif
+}
+
+// Sum of the n column partials of one loop in a fixed order (lane l takes l, l+32, ..., then a
+// shuffle tree), identical in every CTA; every lane of the calling warp gets the sums.
+KS_HD void sum_partials(const double* a, const double* c, int n, double& sa, double& sc) {
+    warp_sum_partials(a, c, n, sa, sc);
+}
+
+KS_HD void sum_partials(const ff* a, const ff* c, int n, double& sa, double& sc) {
+#ifdef KS_HOST_EMULATION
+    ff x = {0.f, 0.f}, y = {0.f, 0.f};
+    for (int i = 0; i < n; ++i) {
+        x = ff_add(x, a[i]);
+        y = ff_add(y, c[i]);
+    }
+    sa = widen(x);
+    sc = widen(y);
+#else
+    const int l = threadIdx.x & 31;
+    ff x = {0.f, 0.f}, y = {0.f, 0.f};
+    for (int i = l; i < n; i += 32) {
+        x = ff_add(x, a[i]);
+        y = ff_add(y, c[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ff bx, by;
+        bx.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+        bx.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+        by.hi = __shfl_xor_sync(0xffffffffu, y.hi, o);
+        by.lo = __shfl_xor_sync(0xffffffffu, y.lo, o);
+        x = ff_add(x, bx);
+        y = ff_add(y, by);
+    }
+    sa = widen(x);
+    sc = widen(y);
 #endif
 }
 
@@ -528,8 +697,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         const double wj = (j == 0) ? 1.0 : 2.0;  // x-conjugate pairs counted twice
 
         if constexpr (MODE == COL_RESID) {
-            R pJ = 0;
-            double pL = 0.0;
+            ColAcc<R> acc;
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
                 cpx<R> x = mk<R>(0, 0);
@@ -540,22 +708,18 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     // r_hat = (a + i bk) u_hat - p_hat                                    (a5)
                     const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
                     p.rh[bo + (k + ks)] = r;
-                    pJ += r.x * r.x + r.y * r.y;              // a6
-                    // omega_k Im(conj(u) r) / (2 pi), accumulated in double: the sum over k
-                    // cancels strongly, so float terms would lose its leading digits
-                    pL += (double)k * ((double)u.x * (double)r.y - (double)u.y * (double)r.x);
+                    acc.add(u, r, k);                         // a6: |r|^2, k Im(conj(u) r)
                     x = mk<R>(-rq * r.y, rq * r.x);           // i q_j r_hat                 (a7)
                 }
                 X[i] = x;
             }
-            double sJ = (double)pJ, sL = pL;
             KS_SYNC();
             cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
-            block_sum2(red, sJ, sL);
+            block_reduce(acc, red);
             if (KS_TID == 0) {
-                p.Jpart[(size_t)b * nkx + j] = wj * sJ;
-                p.L2part[(size_t)b * nkx + j] = wj * sL;
+                p.Jpart[(size_t)b * nkx + j] = acc.part_J(wj);
+                p.L2part[(size_t)b * nkx + j] = acc.part_L(wj);
             }
             KS_SYNC();
         } else if constexpr (MODE == COL_GRAD) {
@@ -575,7 +739,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             const double T = Tc[b];
             if (KS_TID < 32) {
                 double sJ, sL;
-                warp_sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
+                sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
                 if (KS_TID == 0) {
                     red[0] = sJ * d.L;
                     red[1] = sL * d.L * wTc[b] / T;  // (L / T^2) * 2 pi * sum

@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(256) k_persist(Dims d, Bufs<R> p, int nsteps, 
 
 // J = L sum_j Jpart, dJ/dT = 2 L^dag_2 = 2 (2 pi L / T^2) sum_j L2part, per loop.
 // only loops with prec[b] == myprec are written when mask != 0.
-__global__ void k_finalize(int B, int nkx, double L, const double* Jpart, const double* L2part,
+template <typename P>
+__global__ void k_finalize(int B, int nkx, double L, const P* Jpart, const P* L2part,
                            const double* T, const int* prec, int myprec, int mask, double* J,
                            double* dJdT, double* sqrtJ) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,8 +136,8 @@ __global__ void k_finalize(int B, int nkx, double L, const double* Jpart, const 
     if (mask && prec[b] != myprec) return;
     double sj = 0.0, sl = 0.0;
     for (int c = 0; c < nkx; ++c) {
-        sj += Jpart[(size_t)b * nkx + c];
-        sl += L2part[(size_t)b * nkx + c];
+        sj += widen(Jpart[(size_t)b * nkx + c]);
+        sl += widen(L2part[(size_t)b * nkx + c]);
     }
     const double Tb = T[b];
     const double Jb = L * sj;
@@ -402,8 +403,8 @@ Bufs<R> make_bufs(ks_loop* h, const Work& w, int pr, int check_active, double to
     p.io = io;
     p.T = w.T;
     p.wT = w.wT;
-    p.Jpart = w.Jpart;
-    p.L2part = w.L2part;
+    p.Jpart = reinterpret_cast<typename PartT<R>::type*>(w.Jpart);
+    p.L2part = reinterpret_cast<typename PartT<R>::type*>(w.L2part);
     p.status = w.status;
     p.prec = w.prec;
     p.steps = w.steps;
@@ -545,7 +546,8 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     cp.nkmax = 2 * (h->nsmax / 3) + 1;
     int nsmin = h->nsmax;
     for (int v : h->ns) nsmin = std::min(nsmin, v);
-    cp.rmax = std::max(2, h->nsmax / C);
+    cp.rmax = 0;
+    for (int v : h->ns) cp.rmax = std::max(cp.rmax, cluster_rows_per_rank(v, C));
     int rt = 2;
     while (rt * 2 <= std::min(cp.rmax, 16) && 2 * (size_t)(rt * 2) * nx * cs <= 32 * 1024) rt *= 2;
     cp.rt = rt;
@@ -566,6 +568,8 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     off += al((size_t)2 * nkx * sizeof(double));
     cp.off_red = (int)off;
     off += al((size_t)COL_RED_DOUBLES * sizeof(double));
+    cp.off_tw = (int)off;
+    off += al((size_t)NMAX * cs);
     cp.bytes = (off <= (size_t)smem_limit) ? (int)off : 0;
     return cp;
 }
@@ -581,9 +585,20 @@ int setup_cluster(ks_loop* h) {
     KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
     int target = 16;
     while (target > 1 && (long long)target * h->d.B > 2LL * sms) target >>= 1;
-    if (h->force_cluster) target = h->force_cluster;
     KS_CUDA(cudaFuncSetAttribute(k_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    for (int C = target; C >= 1; C >>= 1) {
+    // candidate sizes: for each target, the smallest size that keeps the same number of
+    // columns per rank (22 columns on 16 ranks -> 11 ranks of 2), then halve the target
+    std::vector<int> cands;
+    if (h->force_cluster) {
+        cands.push_back(h->force_cluster);
+    } else {
+        for (int t = target; t >= 1; t >>= 1) {
+            const int per = (h->d.nkx + t - 1) / t;
+            const int C = (h->d.nkx + per - 1) / per;
+            if (std::find(cands.begin(), cands.end(), C) == cands.end()) cands.push_back(C);
+        }
+    }
+    for (int C : cands) {
         for (int ug = 0; ug < 2; ++ug) {
             ClusterPlan cp = make_cluster_plan<R>(h, C, ug, limit);
             if (!cp.bytes) continue;
@@ -609,7 +624,6 @@ int setup_cluster(ks_loop* h) {
             h->cgrid[pr] = C * std::min(h->d.B, ncl);
             return KS_OK;
         }
-        if (h->force_cluster) break;
     }
     return KS_OK;
 }
@@ -723,8 +737,13 @@ int run_finalize(ks_loop* h, Work& w, const double* T, int myprec, int mask,
                  cudaStream_t s) {
     const int B = h->d.B;
     LaunchScope ls(h, s, "finalize");
-    k_finalize<<<(B + 127) / 128, 128, 0, s>>>(B, h->d.nkx, h->d.L, w.Jpart, w.L2part, T,
-                                                w.prec, myprec, mask, w.J, w.dJdT, w.sqrtJ);
+    if (myprec == P64)
+        k_finalize<double><<<(B + 127) / 128, 128, 0, s>>>(B, h->d.nkx, h->d.L, w.Jpart, w.L2part, T,
+                                                            w.prec, myprec, mask, w.J, w.dJdT, w.sqrtJ);
+    else
+        k_finalize<ff><<<(B + 127) / 128, 128, 0, s>>>(B, h->d.nkx, h->d.L, (const ff*)w.Jpart,
+                                                        (const ff*)w.L2part, T, w.prec, myprec, mask,
+                                                        w.J, w.dJdT, w.sqrtJ);
     KS_CUDA(cudaGetLastError());
     ls.done();
     return KS_OK;
@@ -1418,8 +1437,7 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         if (value < 0 || value > 2) return fail(KS_ERR_ARG, "path must be 0, 1 or 2");
         h->path = (int)value;
     } else if (k == "cluster") {
-        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
-            return fail(KS_ERR_ARG, "cluster must be 0 (auto), 1, 2, 4, 8 or 16");
+        if (value < 0 || value > 16) return fail(KS_ERR_ARG, "cluster must be 0 (auto) or 1..16");
         h->force_cluster = (int)value;
         KS_TRY(setup_cluster<double>(h));
         KS_TRY(setup_cluster<float>(h));
