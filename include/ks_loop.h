@@ -178,6 +178,36 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
 
+/* Residual of ONE double-precision loop without allocating any device memory.
+ *
+ * For callers that cannot call cudaMalloc when they need a residual: code that runs inside a
+ * memory pool or arena that already owns the device memory, plugins of applications that
+ * forbid allocation after start-up, and real-time loops where an allocation (an implicit
+ * synchronisation, and a call that can fail) is not acceptable.  The paper has no counterpart:
+ * this is a deployment variant of ks_residual.
+ *
+ * Computes what ks_residual computes for a handle with batch 1 and mode KS_FP64: the residual
+ * of [P u; T] (Eq. KS_R) on the grid and J (Eq. cost_function).  No handle is needed.
+ *   L     : domain length, > 0
+ *   nx, ns: grid size, powers of two with 8 <= nx <= 256 and 8 <= ns <= 256 (larger sizes are
+ *           rejected with KS_ERR_ARG)
+ *   u     : in,  device pointer, ns x nx doubles, layout [n][m]
+ *   T     : the period (by value)
+ *   r     : out, device pointer, ns x nx doubles, nullable
+ *   J     : out, device pointer to one double
+ *   stream: cudaStream_t; the call is stream ordered
+ * Host pointers are rejected with KS_ERR_ARG.
+ *
+ * All intermediates live in one file-scope device array of about 1.4 MB (at most 2 MB) that
+ * every GPU loading the library holds until the process exits.  The first call on a device
+ * (with that device current) looks up the array's device address and uploads the twiddle
+ * table there; make that first call before any stream capture.  Every call shares the array
+ * and overwrites what the previous call left in it, so calls that overlap on the GPU (on
+ * different streams, or from several threads) race: serialise them.  Errors are reported
+ * through ks_last_error(). */
+KS_API int ks_residual_noalloc(double L, int nx, int ns, const double* u, double T, double* r,
+                               double* J, void* stream);
+
 /* Message for the last non-zero return on the calling thread ("" if none). */
 KS_API const char* ks_last_error(void);
 

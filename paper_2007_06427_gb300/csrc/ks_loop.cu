@@ -170,6 +170,9 @@ static int fail(int code, const std::string& msg) {
     return code;
 }
 
+// lets the allocation-free entry point report through ks_last_error()
+void ks_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 #define KS_CUDA(call)                                                                      \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
