@@ -32,7 +32,7 @@ struct ClusterPlan {
     int nsmax;    // max Ns over the batch
     int nkmax;    // max 2 Ks + 1
     int rmax;     // max rows per rank
-    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red, off_tw;
+    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red, off_tw, off_rin;
     int bytes;
     int u_global;  // 1: the rank's grid rows of u live in global memory (U array), not SMEM
 };
@@ -44,15 +44,36 @@ __host__ __device__ inline int cluster_rows_per_rank(int ns, int C) {
     return r < 2 ? 2 : r;
 }
 
-// FFT of `cnt` columns stored [q][n] at `a` with `b` as scratch; the result is left in `a`.
+// FFT of `cnt` columns stored [q][n] at `a` with `b` as scratch (warp-owned transforms); the
+// result is left in `a`.
 template <typename R>
 __device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                                 const cpx<R>* tw) {
-    cpx<R>* r = fft_batch(a, b, lg, cnt, dir, tw);
+    cpx<R>* r = fft_warp(a, b, lg, cnt, dir, tw);
     if (r != a) {
         const int n = cnt << lg;
         for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = r[i];
         __syncthreads();
+    }
+}
+
+// 16-byte copy global -> shared with up to eight loads in flight per thread (bytes % 16 == 0)
+__device__ __forceinline__ void copy16_g2s(void* dst, const void* src, int bytes) {
+    const int4* s = reinterpret_cast<const int4*>(src);
+    int4* d = reinterpret_cast<int4*>(dst);
+    const int n = bytes >> 4;
+    for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
+        int4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * blockDim.x;
+            if (i < n) v[u] = s[i];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * blockDim.x;
+            if (i < n) d[i] = v[u];
+        }
     }
 }
 
@@ -68,7 +89,9 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
     const int ncl = gridDim.x / C;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nx = d.nx, lgnx = d.lgnx, kx = d.kx, nkx = d.nkx, B = d.B;
-    cpx<R>* Mloc = reinterpret_cast<cpx<R>*>(smem + cp.off_M);
+    const int rmax = cp.rmax;
+    cpx<R>* Mloc = reinterpret_cast<cpx<R>*>(smem + cp.off_M);   // owned columns: P / W
+    cpx<R>* Rin = reinterpret_cast<cpx<R>*>(smem + cp.off_rin);  // own rows: v / rho, [j][r]
     cpx<R>* uhl = reinterpret_cast<cpx<R>*>(smem + cp.off_uh);
     cpx<R>* rhl = reinterpret_cast<cpx<R>*>(smem + cp.off_rh);
     R* const Us = reinterpret_cast<R*>(smem + cp.off_U);  // rows of u kept between row phases
@@ -78,7 +101,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
     cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem + cp.off_tw);
     const R h = (R)d.hx;
 
-    for (int i = tid; i < NMAX; i += nt) tws[i] = p.tw[i];
+    copy16_g2s(tws, p.tw, (int)(NMAX * sizeof(cpx<R>)));
     __syncthreads();
 
     for (int bi = cid; bi < B; bi += ncl) {
@@ -103,15 +126,52 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
         double T = p.T[(size_t)par0 * B + b];
         double wT = p.wT[(size_t)par0 * B + b];
 
-        // ---- load the band (and the mixed columns, or prime them) --------------------
-        for (int i = tid; i < ncol * nk; i += nt) {
-            const int q = i / nk, kk = i - q * nk;
-            uhl[i] = p.uh[bo + (size_t)(rank + q * C) * nk + kk];
-        }
-        if (use_M) {
+        // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)]
+        auto push_columns = [&](const cpx<R>* X) {
             for (int i = tid; i < ncol << lg; i += nt) {
                 const int q = i >> lg, n = i & (ns - 1);
-                Mloc[i] = Mg[(size_t)(rank + q * C) * ns + n];
+                const int owner = n / rpr;
+                cpx<R>* dst = cl.map_shared_rank(Rin, owner);
+                dst[(size_t)(rank + q * C) * rmax + (n - owner * rpr)] = X[i];
+            }
+        };
+
+        // ---- load the band, and the rows' mixed values (or prime them from the band) ----
+        for (int base = tid; base < ncol * nk; base += 4 * nt) {
+            cpx<R> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + u * nt;
+                if (i < ncol * nk) {
+                    const int q = i / nk, kk = i - q * nk;
+                    v[u] = p.uh[bo + (size_t)(rank + q * C) * nk + kk];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + u * nt;
+                if (i < ncol * nk) uhl[i] = v[u];
+            }
+        }
+        if (use_M) {
+            for (int base = tid; base < nkx * nrow; base += 4 * nt) {
+                cpx<R> v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = base + u * nt;
+                    if (i < nkx * nrow) {
+                        const int j = i / nrow, r = i - j * nrow;
+                        v[u] = Mg[(size_t)j * ns + row0 + r];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = base + u * nt;
+                    if (i < nkx * nrow) {
+                        const int j = i / nrow, r = i - j * nrow;
+                        Rin[(size_t)j * rmax + r] = v[u];
+                    }
+                }
             }
             __syncthreads();
         } else {
@@ -123,6 +183,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
             }
             __syncthreads();
             col_fft_inplace(Mloc, scr, lg, ncol, +1, tws);
+            push_columns(Mloc);
         }
         cl.sync();
 
@@ -143,18 +204,12 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                 for (int i = tid; i < nr * nx; i += nt) {
                     const int J = i >> lgnr, r = i & (nr - 1);
                     cpx<R> z = mk<R>(0, 0);
-                    if (J <= kx) {
-                        const cpx<R>* src = cl.map_shared_rank(Mloc, J % C) + (size_t)(J / C) * ns;
-                        z = scale(src[n0 + r], (R)1 - p.qv[J]);
-                    } else if (J >= nx - kx) {
-                        const int j = nx - J;
-                        const cpx<R>* src = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns;
-                        z = scale(conj(src[n0 + r]), (R)1 + p.qv[j]);
-                    }
+                    if (J <= kx) z = scale(Rin[(size_t)J * rmax + t0 + r], (R)1 - p.qv[J]);
+                    else if (J >= nx - kx) z = scale(conj(Rin[(size_t)(nx - J) * rmax + t0 + r]), (R)1 + p.qv[nx - J]);
                     A[(size_t)r * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<R>* z = fft_batch(A, Bf, lgnx, nr, +1, tws);
+                cpx<R>* z = fft_warp(A, Bf, lgnx, nr, +1, tws);
                 cpx<R>* Y = (z == A) ? Bf : A;
                 const int np = nr >> 1;
                 for (int i = tid; i < np * nx; i += nt) {
@@ -166,7 +221,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, tws);
+                cpx<R>* F = fft_warp(Y, z, lgnx, np, -1, tws);
                 const int lgp = lgnr - 1;
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
@@ -213,12 +268,8 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     }
                 }
                 __syncthreads();
-                // inverse of i q r_hat: scr holds the spectra, Mloc is scratch
-                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, tws);
-                if (v != Mloc) {
-                    for (int i = tid; i < ncol << lg; i += nt) Mloc[i] = v[i];
-                    __syncthreads();
-                }
+                // inverse of i q r_hat (scr holds the spectra, Mloc is scratch), then push rho
+                push_columns(fft_warp(scr, Mloc, lg, ncol, +1, tws));
             }
             cl.sync();
 
@@ -236,27 +287,17 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                 for (int i = tid; i < np * nx; i += nt) {
                     const int J = i >> lgp, pr = i & (np - 1);
                     cpx<R> z = mk<R>(0, 0);
-                    int j = -1;
-                    bool neg = false;
                     if (J <= kx) {
-                        j = J;
+                        const cpx<R>* src = Rin + (size_t)J * rmax + t0 + 2 * pr;
+                        z = src[0] + mul_i(src[1], 1);
                     } else if (J >= nx - kx) {
-                        j = nx - J;
-                        neg = true;
-                    }
-                    if (j >= 0) {
-                        const cpx<R>* src = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
-                        cpx<R> xa = src[0], xb = src[1];
-                        if (neg) {
-                            xa = conj(xa);
-                            xb = conj(xb);
-                        }
-                        z = xa + mul_i(xb, 1);
+                        const cpx<R>* src = Rin + (size_t)(nx - J) * rmax + t0 + 2 * pr;
+                        z = conj(src[0]) + mul_i(conj(src[1]), 1);
                     }
                     A[(size_t)pr * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<R>* z = fft_batch(A, Bf, lgnx, np, +1, tws);
+                cpx<R>* z = fft_warp(A, Bf, lgnx, np, +1, tws);
                 cpx<R>* Y = (z == A) ? Bf : A;
                 for (int i = tid; i < np * nx; i += nt) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
@@ -265,7 +306,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                                  Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_batch(Y, z, lgnx, np, -1, tws);
+                cpx<R>* F = fft_warp(Y, z, lgnx, np, -1, tws);
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
                     const cpx<R> yj = F[(size_t)pr * nx + j];
@@ -331,11 +372,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                     scr[i] = x;
                 }
                 __syncthreads();
-                cpx<R>* v = fft_batch(scr, Mloc, lg, ncol, +1, tws);
-                if (v != Mloc) {
-                    for (int i = tid; i < ncol << lg; i += nt) Mloc[i] = v[i];
-                    __syncthreads();
-                }
+                push_columns(fft_warp(scr, Mloc, lg, ncol, +1, tws));
             }
             T = Tnext;
             wT = wTnext;
@@ -343,14 +380,14 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
             cl.sync();
         }
 
-        // ---- write the loop back -------------------------------------------------------
+        // ---- write the loop back: band of the owned columns, mixed values of the own rows
         for (int i = tid; i < ncol * nk; i += nt) {
             const int q = i / nk, kk = i - q * nk;
             p.uh[bo + (size_t)(rank + q * C) * nk + kk] = uhl[i];
         }
-        for (int i = tid; i < ncol << lg; i += nt) {
-            const int q = i >> lg, n = i & (ns - 1);
-            Mg[(size_t)(rank + q * C) * ns + n] = Mloc[i];
+        for (int i = tid; i < nkx * nrow; i += nt) {
+            const int j = i / nrow, r = i - j * nrow;
+            Mg[(size_t)j * ns + row0 + r] = Rin[(size_t)j * rmax + r];
         }
         if (rank == 0 && tid == 0) {
             p.T[(size_t)par0 * B + b] = T;

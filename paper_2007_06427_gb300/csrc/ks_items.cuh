@@ -285,6 +285,76 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
     return a;
 }
 
+// ------------------------------------------------------------------------------------
+// Warp-owned variant of fft_batch: transform f belongs to warp f % warps, which runs every
+// pass of it alone and synchronises with __syncwarp() between passes; one block barrier at
+// the end.  Same arithmetic in the same order as fft_batch (bit-identical results), far fewer
+// block-wide barriers.  Device code only.
+// ------------------------------------------------------------------------------------
+#ifndef KS_HOST_EMULATION
+template <typename R>
+__device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
+                                            const cpx<R>* tw) {
+    const int n = 1 << lg;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int span = 1;
+    int p = lg;
+    // this warp's transforms f = w, w + nw, ...; lanes walk (transform, butterfly) jointly
+    const int nf = (cnt > w) ? (cnt - w + nw - 1) / nw : 0;
+    if (p & 1) {
+        const int nb = n >> 1;
+        for (int i = lane; i < nf * nb; i += 32) {
+            const int f = w + (i >> (lg - 1)) * nw, j = i & (nb - 1);
+            const cpx<R>* s = a + (size_t)f * n;
+            cpx<R>* d = b + (size_t)f * n;
+            const cpx<R> v0 = s[j], v1 = s[j + nb];
+            d[2 * j] = v0 + v1;
+            d[2 * j + 1] = v0 - v1;
+        }
+        __syncwarp();
+        cpx<R>* t = a;
+        a = b;
+        b = t;
+        span = 2;
+        p -= 1;
+    }
+    while (p > 0) {
+        const int nb = n >> 2;
+        const int tu = NMAX / (span * 4);
+        for (int i = lane; i < nf * nb; i += 32) {
+            const int f = w + (i >> (lg - 2)) * nw, j = i & (nb - 1);
+            {
+                const cpx<R>* s = a + (size_t)f * n;
+                cpx<R>* d = b + (size_t)f * n;
+                cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+                const int jm = j & (span - 1);
+                if (span > 1) {
+                    const int t = jm * tu;
+                    v1 = cmul(v1, twid(tw, t, dir));
+                    v2 = cmul(v2, twid(tw, 2 * t, dir));
+                    v3 = cmul(v3, twid(tw, 3 * t, dir));
+                }
+                const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
+                const cpx<R> t3 = mul_i(v1 - v3, dir);
+                const int od = ((j - jm) << 2) + jm;
+                d[od] = t0 + t2;
+                d[od + span] = t1 + t3;
+                d[od + 2 * span] = t0 - t2;
+                d[od + 3 * span] = t1 - t3;
+            }
+        }
+        __syncwarp();
+        cpx<R>* t = a;
+        a = b;
+        b = t;
+        span <<= 2;
+        p -= 2;
+    }
+    __syncthreads();
+    return a;
+}
+#endif
+
 // Block-wide sum of two doubles per thread (warp shuffles, then one warp over the warp sums);
 // red has room for 2 * (warps + 1) doubles.  The result is valid in every thread after the call.
 KS_HD void block_sum2(double* red, double& s0, double& s1) {

@@ -573,6 +573,8 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     off += al((size_t)COL_RED_DOUBLES * sizeof(double));
     cp.off_tw = (int)off;
     off += al((size_t)NMAX * cs);
+    cp.off_rin = (int)off;
+    off += al((size_t)nkx * cp.rmax * cs);
     cp.bytes = (off <= (size_t)smem_limit) ? (int)off : 0;
     return cp;
 }
@@ -589,17 +591,14 @@ int setup_cluster(ks_loop* h) {
     int target = 16;
     while (target > 1 && (long long)target * h->d.B > 2LL * sms) target >>= 1;
     KS_CUDA(cudaFuncSetAttribute(k_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    // candidate sizes: for each target, the smallest size that keeps the same number of
-    // columns per rank (22 columns on 16 ranks -> 11 ranks of 2), then halve the target
+    // candidate sizes: powers of two from the target down.  (A size that only balances the
+    // columns, e.g. 11 ranks of 2 columns for 22, gives each rank 12 rows in two x-batches and
+    // measured slower than 16 ranks with one row batch each.)
     std::vector<int> cands;
     if (h->force_cluster) {
         cands.push_back(h->force_cluster);
     } else {
-        for (int t = target; t >= 1; t >>= 1) {
-            const int per = (h->d.nkx + t - 1) / t;
-            const int C = (h->d.nkx + per - 1) / per;
-            if (std::find(cands.begin(), cands.end(), C) == cands.end()) cands.push_back(C);
-        }
+        for (int t = target; t >= 1; t >>= 1) cands.push_back(t);
     }
     for (int C : cands) {
         for (int ug = 0; ug < 2; ++ug) {
