@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--e2e-calls", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--to-tol", action="store_true", help="also run FP64 vs mixed to sqrt(J)<tol")
+    ap.add_argument("--no-to-tol", action="store_true",
+                    help="skip the FP64 vs mixed descent to sqrt(J) < tol")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the float-path throughput line")
     ap.add_argument("--to-tol-max-steps", type=int, default=1_000_000)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--switch-tol", type=float, default=1e-5)
@@ -65,7 +67,13 @@ def fft_flops(n: int) -> float:
     return 5.0 * n * math.log2(n)
 
 
-def kernel_flops(kind: str, nx: int, nss) -> float:
+def kernel_flops(kind: str, nx: int, nss, steps_per_launch: int = 1) -> float:
+    """Algorithmic flops of one launch of `kind` over the batch.
+
+    Fused kernels (cluster-resident, grid-persistent) run whole tau-steps: their work is the
+    sum of the four phases times the steps per launch."""
+    if kind.startswith("cluster") or kind.startswith("persist"):
+        return steps_per_launch * step_flops(nx, nss)
     nkx = nx // 3 + 1
     rows = sum(nss)
     if kind.startswith("rows_nonlin"):
@@ -354,8 +362,12 @@ def ours_arm(args):
                "note": "one bench step = one ks_descend call on pinned host buffers"}
 
     to_tol = None
-    if args.to_tol:
+    if not args.no_to_tol and ws == 1:
         to_tol = run_to_tol(args, w, dev)
+
+    fp32 = None
+    if not args.no_fp32 and mode == K.KS_FP64:
+        fp32 = throughput_fp32(args, w, dev, flush, K)
 
     h.close()
     if rank == 0:
@@ -377,14 +389,57 @@ def ours_arm(args):
         }
         if to_tol:
             line["time_to_tol"] = to_tol
+        if fp32:
+            line["fp32"] = fp32
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
 
 
+def throughput_fp32(args, w, dev, flush, K):
+    """Same timed loop on an FP32 handle (the bulk phase of a mixed descent)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    u = torch.from_numpy(w.packed()).to(dev, torch.float32)
+    T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
+    h = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP32, w.scheme, w.dtau)
+    K.ks_set_state(h.handle, u, T, stream)
+    for _ in range(args.warmup):
+        K.ks_step(h.handle, 1, 0.0, stream)
+    torch.cuda.synchronize(dev)
+    K.ks_profile(h.handle, True)
+    K.ks_profile_read(h.handle, reset=True)
+    evs = []
+    for _ in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K.ks_step(h.handle, 1, 0.0, stream)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof, launches = K.ks_profile_read(h.handle, reset=True)
+    h.close()
+    dname = max(prof, key=lambda k: prof[k][0]) if prof else None
+    out = {"value": w.gridpoints * args.steps / (total_ms / 1e3), "unit": UNIT,
+           "ms_per_step": total_ms / args.steps, "dtype": "f32", "gpu_launches": launches}
+    if dname:
+        ms, cnt = prof[dname]
+        fl = kernel_flops(dname, w.nx, w.ns)
+        ach = fl / (ms / cnt / 1e3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": PEAK_TFLOPS["f32"],
+                           "unit": "TFLOP/s", "frac": ach / PEAK_TFLOPS["f32"], "traffic": None,
+                           "kernel": dname, "ms_per_launch": ms / cnt}
+    return out
+
+
 def run_to_tol(args, w, dev):
     """Plain FP64 descent vs FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol."""
+    import numpy as np
     import torch
     from paper_2007_06427_gb300 import ks_loop as K
     out = {}
@@ -401,9 +456,18 @@ def run_to_tol(args, w, dev):
         K.ks_descend(h.handle, u, T, args.to_tol_max_steps, args.tol, steps, sq, st)
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
+        hs, hq, hp = K.ks_get_history(h.handle, 0)
+        marks = {}
+        for target in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
+            idx = np.nonzero(hq < target)[0]
+            if idx.size:
+                marks[f"{target:.0e}"] = int(hs[idx[0]])
+        switch = int(hs[np.nonzero(hp == 0)[0][0]]) if (name == "mixed" and (hp == 0).any()) else None
         out[name] = {"seconds": el, "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8],
                      "status": [K.STATUS_NAMES.get(int(s), str(int(s))) for s in st.tolist()[:8]],
-                     "T": T.tolist()[:8]}
+                     "T": T.tolist()[:8], "loop0_first_step_below": marks,
+                     "loop0_switch_step": switch,
+                     "loop0_history": [[int(a), float(c)] for a, c in zip(hs[::max(1, len(hs) // 40)], hq[::max(1, len(hq) // 40)])]}
         h.close()
     return out
 

@@ -137,6 +137,13 @@ KS_API int ks_adjoint_grad(ks_loop_t h, const void* u, const double* T, void* G,
 KS_API int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, double tol,
                long long* steps, double* sqrtJ, int* status, void* stream);
 
+/* Convergence history of loop b recorded by the last ks_descend at each read-back (every
+ * `chunk` steps): up to cap entries of the step count, sqrt(J) of the last evaluated loop and
+ * the precision it was descending in (0 double, 1 float).  Outputs nullable; returns the
+ * number of entries recorded (may exceed cap) or a negative KS_ERR_* code.  sqrt(J) against
+ * tau is the convergence curve of the paper's Fig. 2. */
+KS_API int ks_get_history(ks_loop_t h, int b, long long* steps, double* sqrtJ, int* prec, int cap);
+
 /* Resident state: load [P u; T] as the handle's descent state (status reset to running,
  * step counters to zero). */
 KS_API int ks_set_state(ks_loop_t h, const void* u, const double* T, void* stream);
@@ -170,10 +177,14 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *   "stall_drop_ppm" a loop whose sqrt(J) fell by less than this many parts per million over
  *                    a window is stalled (default 1000): the float phase of a mixed descent
  *                    then switches to double, a double descent stops with KS_STALLED
- *   "chunk"          tau-steps between read-backs in ks_descend */
+ *   "chunk"          tau-steps between read-backs in ks_descend
+ *   "finish_f32_adjoint"  KS_MIXED handles: 1 (default): the finishing steps keep the state,
+ *                    the residual, J, dJ/dT and the update in double and form only the descent
+ *                    direction G (the adjoint half of a step) in float; 0: all-double finish */
 KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
 
-/* Read a knob or a derived launch parameter: "path", "cluster_f64", "cluster_f32" (cluster
+/* Read a knob or a derived launch parameter: "path", "finish_f32_adjoint", "cluster_f64",
+ * "cluster_f32", "cluster_mixed_finish" (cluster
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);

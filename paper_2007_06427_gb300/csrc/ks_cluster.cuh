@@ -32,7 +32,7 @@ struct ClusterPlan {
     int nsmax;    // max Ns over the batch
     int nkmax;    // max 2 Ks + 1
     int rmax;     // max rows per rank
-    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red, off_tw, off_rin;
+    int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red, off_tw, off_rin, off_tw_a;
     int bytes;
     int u_global;  // 1: the rank's grid rows of u live in global memory (U array), not SMEM
 };
@@ -77,10 +77,24 @@ __device__ __forceinline__ void copy16_g2s(void* dst, const void* src, int bytes
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan cp, int nsteps,
-                                                 int par0, int use_M) {
+// Tables in the precision of the adjoint half of a step (twiddles, q_j, q_j^2 - q_j^4).
+template <typename RA>
+struct AdjTables {
+    const cpx<RA>* tw;
+    const RA* qv;
+    const RA* lin;
+};
+
+// R: precision of the state, the residual half of a step (phases A, B), the reductions and the
+// update.  RA: precision of the adjoint half (the inverse transform of i q r_hat, phase A' and
+// the forward transform and G_hat assembly of phase B').  RA = R is the plain float or double
+// descent; R = double, RA = float is the finishing stage of a mixed descent, where r, J,
+// dJ/dT and the update stay in double and only the descent direction is formed in float.
+template <typename R, typename RA>
+__global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA> ta,
+                                                 ClusterPlan cp, int nsteps, int par0, int use_M) {
     typedef typename PartT<R>::type Part;
+    constexpr bool kSame = sizeof(R) == sizeof(RA);
     extern __shared__ __align__(16) unsigned char smem[];
     cgx::cluster_group cl = cgx::this_cluster();
     const int C = cp.C;
@@ -99,9 +113,16 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
     Part* part = reinterpret_cast<Part*>(smem + cp.off_part);  // [2][nkx]: J, L2 partials
     double* red = reinterpret_cast<double*>(smem + cp.off_red);
     cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem + cp.off_tw);
+    // adjoint-precision views of the same buffers (phases are separated by barriers)
+    cpx<RA>* Rin_a = reinterpret_cast<cpx<RA>*>(Rin);
+    cpx<RA>* Mloc_a = reinterpret_cast<cpx<RA>*>(Mloc);
+    cpx<RA>* scr_a = reinterpret_cast<cpx<RA>*>(scr);
+    cpx<RA>* tws_a = kSame ? reinterpret_cast<cpx<RA>*>(tws) : reinterpret_cast<cpx<RA>*>(smem + cp.off_tw_a);
     const R h = (R)d.hx;
+    const RA h_a = (RA)d.hx;
 
     copy16_g2s(tws, p.tw, (int)(NMAX * sizeof(cpx<R>)));
+    if (!kSame) copy16_g2s(tws_a, ta.tw, (int)(NMAX * sizeof(cpx<RA>)));
     __syncthreads();
 
     for (int bi = cid; bi < B; bi += ncl) {
@@ -127,11 +148,11 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
         double wT = p.wT[(size_t)par0 * B + b];
 
         // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)]
-        auto push_columns = [&](const cpx<R>* X) {
+        auto push_columns = [&](const auto* X, auto* RinT) {
             for (int i = tid; i < ncol << lg; i += nt) {
                 const int q = i >> lg, n = i & (ns - 1);
                 const int owner = n / rpr;
-                cpx<R>* dst = cl.map_shared_rank(Rin, owner);
+                auto* dst = cl.map_shared_rank(RinT, owner);
                 dst[(size_t)(rank + q * C) * rmax + (n - owner * rpr)] = X[i];
             }
         };
@@ -183,7 +204,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
             }
             __syncthreads();
             col_fft_inplace(Mloc, scr, lg, ncol, +1, tws);
-            push_columns(Mloc);
+            push_columns(Mloc, Rin);
         }
         cl.sync();
 
@@ -257,7 +278,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                             acc.add(u, r, k);
                             x = mk<R>(-rq * r.y, rq * r.x);
                         }
-                        scr[(q << lg) + n] = x;
+                        scr_a[(q << lg) + n] = mk<RA>((RA)x.x, (RA)x.y);
                     }
                     block_reduce(acc, red);
                     if (tid < C) {
@@ -269,7 +290,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                 }
                 __syncthreads();
                 // inverse of i q r_hat (scr holds the spectra, Mloc is scratch), then push rho
-                push_columns(fft_warp(scr, Mloc, lg, ncol, +1, tws));
+                push_columns(fft_warp(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a);
             }
             cl.sync();
 
@@ -282,39 +303,39 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
                 }
                 const int np = nr >> 1;
                 const int n0 = row0 + t0;
-                cpx<R>* A = scr;
-                cpx<R>* Bf = scr + (size_t)nr * nx;
+                cpx<RA>* A = scr_a;
+                cpx<RA>* Bf = scr_a + (size_t)nr * nx;
                 for (int i = tid; i < np * nx; i += nt) {
                     const int J = i >> lgp, pr = i & (np - 1);
-                    cpx<R> z = mk<R>(0, 0);
+                    cpx<RA> z = mk<RA>(0, 0);
                     if (J <= kx) {
-                        const cpx<R>* src = Rin + (size_t)J * rmax + t0 + 2 * pr;
+                        const cpx<RA>* src = Rin_a + (size_t)J * rmax + t0 + 2 * pr;
                         z = src[0] + mul_i(src[1], 1);
                     } else if (J >= nx - kx) {
-                        const cpx<R>* src = Rin + (size_t)(nx - J) * rmax + t0 + 2 * pr;
+                        const cpx<RA>* src = Rin_a + (size_t)(nx - J) * rmax + t0 + 2 * pr;
                         z = conj(src[0]) + mul_i(conj(src[1]), 1);
                     }
                     A[(size_t)pr * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<R>* z = fft_warp(A, Bf, lgnx, np, +1, tws);
-                cpx<R>* Y = (z == A) ? Bf : A;
+                cpx<RA>* z = fft_warp(A, Bf, lgnx, np, +1, tws_a);
+                cpx<RA>* Y = (z == A) ? Bf : A;
                 for (int i = tid; i < np * nx; i += nt) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
-                    const cpx<R> rx = z[i];
-                    Y[i] = mk<R>(Ul[(size_t)(t0 + 2 * pr) * nx + m] * rx.x,
-                                 Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
+                    const cpx<RA> rx = z[i];
+                    Y[i] = mk<RA>((RA)Ul[(size_t)(t0 + 2 * pr) * nx + m] * rx.x,
+                                  (RA)Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_warp(Y, z, lgnx, np, -1, tws);
+                cpx<RA>* F = fft_warp(Y, z, lgnx, np, -1, tws_a);
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
-                    const cpx<R> yj = F[(size_t)pr * nx + j];
-                    const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
-                    const cpx<R> sm = yj + ym, df = yj - ym;
-                    cpx<R>* dst = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
-                    dst[0] = scale(sm, h);
-                    dst[1] = mk<R>(df.y * h, -df.x * h);
+                    const cpx<RA> yj = F[(size_t)pr * nx + j];
+                    const cpx<RA> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
+                    const cpx<RA> sm = yj + ym, df = yj - ym;
+                    cpx<RA>* dst = cl.map_shared_rank(Mloc_a, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
+                    dst[0] = scale(sm, h_a);
+                    dst[1] = mk<RA>(df.y * h_a, -df.x * h_a);
                 }
                 __syncthreads();
                 t0 += nr;
@@ -344,35 +365,39 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, ClusterPlan 
             else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
             if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
             if (ncol > 0) {
-                col_fft_inplace(Mloc, scr, lg, ncol, -1, tws);
+                col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;
+                const RA wTa = (RA)wT;
+                const RA ins_a = (RA)ins;
                 for (int i = tid; i < ncol << lg; i += nt) {
                     const int q = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
+                    const cpx<RA> wh = scale(Mloc_a[i], ins_a);
                     cpx<R> x = mk<R>(0, 0);
                     if (k >= -ks && k <= ks) {
                         const int j = rank + q * C;
-                        const R a_lin = p.lin[j];
-                        const cpx<R> wh = scale(Mloc[i], ins);
-                        const cpx<R> r = rhl[q * nk + k + ks];
-                        const R bk = (R)k * wTr;
-                        const cpx<R> G = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                        const RA a_lin = ta.lin[j];
+                        const cpx<R> rr = rhl[q * nk + k + ks];
+                        const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
+                        const RA bk = (RA)k * wTa;
+                        // G_hat = (a + i omega/T) r_hat + F[P(u r_x)], in the adjoint precision
+                        const cpx<RA> G = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
                         R f = dt;
                         if (d.scheme == 1) {
                             const R kk2 = (R)k * (R)k;
                             f = dt / ((R)1 + dt * (kk2 * wT2 + p.cq[j]));
                         }
                         cpx<R> u = uhl[q * nk + k + ks];
-                        u = u - scale(G, f);
+                        u = u - scale(mk<R>((R)G.x, (R)G.y), f);
                         uhl[q * nk + k + ks] = u;
                         x = u;
                     }
                     scr[i] = x;
                 }
                 __syncthreads();
-                push_columns(fft_warp(scr, Mloc, lg, ncol, +1, tws));
+                push_columns(fft_warp(scr, Mloc, lg, ncol, +1, tws), Rin);
             }
             T = Tnext;
             wT = wTnext;

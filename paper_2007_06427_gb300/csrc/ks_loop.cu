@@ -256,9 +256,10 @@ struct ks_loop {
     // cooperative kernel; 2 = four launches per tau-step
     int path = 0;
     int force_cluster = 0;          // 0: choose the cluster size; else use this one
-    ClusterPlan cplan[2] = {};      // per precision; C = 0 when the cluster path is unavailable
+    ClusterPlan cplan[3] = {};      // double, float, double + float adjoint; bytes = 0: unavailable
     int cthreads = 128;
-    int cgrid[2] = {0, 0};
+    int cgrid[3] = {0, 0, 0};
+    int finish_f32_adjoint = 1;     // mixed descents: finishing steps form the adjoint in float
     // persistent kernel
     bool persistent = true;
     int pgrid[2] = {0, 0};
@@ -279,6 +280,10 @@ struct ks_loop {
     struct Rec { int kind; cudaEvent_t a, b; };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
+    // convergence history recorded by ks_descend at every read-back: (steps, sqrtJ, prec)
+    std::vector<std::vector<long long>> hist_steps;
+    std::vector<std::vector<double>> hist_sqrtJ;
+    std::vector<std::vector<int>> hist_prec;
     // host mirrors
     std::vector<int> h_status, h_prec;
     std::vector<double> h_sqrtJ;
@@ -538,7 +543,7 @@ int setup_persistent(ks_loop* h) {
 }
 
 // Shared-memory plan of the cluster kernel for cluster size C (bytes = 0 if it cannot fit).
-template <typename R>
+template <typename R, typename RA>
 ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_limit) {
     ClusterPlan cp{};
     const size_t cs = sizeof(cpx<R>), rs = sizeof(R);
@@ -575,22 +580,25 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     off += al((size_t)NMAX * cs);
     cp.off_rin = (int)off;
     off += al((size_t)nkx * cp.rmax * cs);
+    cp.off_tw_a = (int)off;
+    if (sizeof(RA) != sizeof(R)) off += al((size_t)NMAX * sizeof(cpx<RA>));
     cp.bytes = (off <= (size_t)smem_limit) ? (int)off : 0;
     return cp;
 }
 
 // pick the cluster size: enough CTAs to cover the GPU (about two per SM), at most 16, and a
 // plan that fits shared memory (grid rows of u in global memory if needed)
-template <typename R>
+// plan slots: 0 double, 1 float, 2 double state with a float adjoint (mixed finishing)
+template <typename R, typename RA>
 int setup_cluster(ks_loop* h) {
-    const int pr = std::is_same<R, double>::value ? P64 : P32;
+    const int pr = std::is_same<R, double>::value ? (std::is_same<RA, double>::value ? 0 : 2) : 1;
     h->cplan[pr] = ClusterPlan{};
     int limit = 0, sms = 0;
     KS_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
     KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
     int target = 16;
     while (target > 1 && (long long)target * h->d.B > 2LL * sms) target >>= 1;
-    KS_CUDA(cudaFuncSetAttribute(k_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     // candidate sizes: powers of two from the target down.  (A size that only balances the
     // columns, e.g. 11 ranks of 2 columns for 22, gives each rank 12 rows in two x-batches and
     // measured slower than 16 ranks with one row batch each.)
@@ -602,9 +610,9 @@ int setup_cluster(ks_loop* h) {
     }
     for (int C : cands) {
         for (int ug = 0; ug < 2; ++ug) {
-            ClusterPlan cp = make_cluster_plan<R>(h, C, ug, limit);
+            ClusterPlan cp = make_cluster_plan<R, RA>(h, C, ug, limit);
             if (!cp.bytes) continue;
-            KS_CUDA(cudaFuncSetAttribute(k_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
+            KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);
             cfg.blockDim = dim3(h->cthreads);
@@ -617,7 +625,7 @@ int setup_cluster(ks_loop* h) {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int ncl = 0;
-            if (cudaOccupancyMaxActiveClusters(&ncl, k_cluster<R>, &cfg) != cudaSuccess) {
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_cluster<R, RA>, &cfg) != cudaSuccess) {
                 cudaGetLastError();
                 ncl = 0;
             }
@@ -631,13 +639,16 @@ int setup_cluster(ks_loop* h) {
 }
 
 // nsteps tau-steps of the live loops of precision pr, one cluster per loop
-template <typename R>
+template <typename R, typename RA>
 int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, double switch_tol,
                 cudaStream_t s) {
     Bufs<R> p = make_bufs<R>(h, w, pr, 1, tol, switch_tol, (R*)nullptr);
-    const ClusterPlan& cp = h->cplan[pr];
+    const int slot = std::is_same<R, RA>::value ? pr : 2;
+    const int pa = std::is_same<RA, double>::value ? P64 : P32;
+    AdjTables<RA> ta{(const cpx<RA>*)h->d_tw[pa], (const RA*)h->d_qv[pa], (const RA*)h->d_lin[pa]};
+    const ClusterPlan& cp = h->cplan[slot];
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->cgrid[pr]);
+    cfg.gridDim = dim3(h->cgrid[slot]);
     cfg.blockDim = dim3(h->cthreads);
     cfg.dynamicSmemBytes = cp.bytes;
     cfg.stream = s;
@@ -648,8 +659,8 @@ int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    LaunchScope ls(h, s, std::string("cluster") + prec_suffix(pr));
-    KS_CUDA(cudaLaunchKernelEx(&cfg, k_cluster<R>, h->d, p, cp, (int)nsteps, w.par,
+    LaunchScope ls(h, s, std::string("cluster") + prec_suffix(pr) + (slot == 2 ? "_adj_f32" : ""));
+    KS_CUDA(cudaLaunchKernelEx(&cfg, k_cluster<R, RA>, h->d, p, ta, cp, (int)nsteps, w.par,
                                w.mix_valid[pr] ? 1 : 0));
     ls.done();
     w.mix_valid[pr] = true;
@@ -997,7 +1008,9 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     }
     if ((rc = set_smem_attrs<double>(h)) || (rc = set_smem_attrs<float>(h))) return cleanup(rc);
     if ((rc = setup_persistent<double>(h)) || (rc = setup_persistent<float>(h))) return cleanup(rc);
-    if ((rc = setup_cluster<double>(h)) || (rc = setup_cluster<float>(h))) return cleanup(rc);
+    if ((rc = setup_cluster<double, double>(h)) || (rc = setup_cluster<float, float>(h)) ||
+        (h->mode == KS_MIXED && (rc = setup_cluster<double, float>(h))))
+        return cleanup(rc);
     h->h_status.assign(B, 0);
     h->h_prec.assign(B, 0);
     h->h_sqrtJ.assign(B, 0.0);
@@ -1117,6 +1130,9 @@ int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
     h->h_steps.assign(B, 0);
     w.mix_valid[P64] = w.mix_valid[P32] = false;
     h->state_set = true;
+    h->hist_steps.assign(B, {});
+    h->hist_sqrtJ.assign(B, {});
+    h->hist_prec.assign(B, {});
     return KS_OK;
 }
 
@@ -1139,8 +1155,13 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s) {
     if ((!live[P32] || clus[P32]) && (!live[P64] || clus[P64])) {
         for (long long done = 0; done < n;) {
             const long long c = std::min(kMaxPerLaunch, n - done);
-            if (live[P32]) KS_TRY(run_cluster<float>(h, w, P32, c, tol, swt, s));
-            if (live[P64]) KS_TRY(run_cluster<double>(h, w, P64, c, tol, 0.0, s));
+            if (live[P32]) KS_TRY((run_cluster<float, float>(h, w, P32, c, tol, swt, s)));
+            if (live[P64]) {
+                if (h->mode == KS_MIXED && h->finish_f32_adjoint && h->cplan[2].bytes > 0)
+                    KS_TRY((run_cluster<double, float>(h, w, P64, c, tol, 0.0, s)));
+                else
+                    KS_TRY((run_cluster<double, double>(h, w, P64, c, tol, 0.0, s)));
+            }
             if (c & 1) w.par ^= 1;
             done += c;
         }
@@ -1333,6 +1354,12 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
         KS_TRY(steps_impl(h, c, tl, s));
         done += c;
         KS_TRY(readback(h, s));
+        for (int b = 0; b < B; ++b) {
+            if (!h->hist_steps[b].empty() && h->hist_steps[b].back() == h->h_steps[b]) continue;
+            h->hist_steps[b].push_back(h->h_steps[b]);
+            h->hist_sqrtJ[b].push_back(h->h_sqrtJ[b]);
+            h->hist_prec[b].push_back(h->h_prec[b]);
+        }
         std::vector<int> sel(B, 0);
         bool any_switch = false, any_live = false, status_dirty = false;
         for (int b = 0; b < B; ++b) {
@@ -1441,10 +1468,13 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
     } else if (k == "cluster") {
         if (value < 0 || value > 16) return fail(KS_ERR_ARG, "cluster must be 0 (auto) or 1..16");
         h->force_cluster = (int)value;
-        KS_TRY(setup_cluster<double>(h));
-        KS_TRY(setup_cluster<float>(h));
+        KS_TRY((setup_cluster<double, double>(h)));
+        KS_TRY((setup_cluster<float, float>(h)));
+        if (h->mode == KS_MIXED) KS_TRY((setup_cluster<double, float>(h)));
         if (value && (h->cplan[0].C != value && h->cplan[1].C != value))
             return fail(KS_ERR_ARG, "requested cluster size does not fit this batch");
+    } else if (k == "finish_f32_adjoint") {
+        h->finish_f32_adjoint = value != 0;
     } else if (k == "stall_window") {
         if (value < 1) return fail(KS_ERR_ARG, "stall_window must be >= 1");
         h->stall_window = value;
@@ -1471,8 +1501,25 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "cluster_smem_f64") *value = h->cplan[0].bytes;
     else if (k == "cluster_smem_f32") *value = h->cplan[1].bytes;
     else if (k == "rows_per_tile") *value = h->rows_per_tile;
+    else if (k == "finish_f32_adjoint") *value = h->finish_f32_adjoint;
+    else if (k == "cluster_mixed_finish") *value = h->cplan[2].bytes ? h->cplan[2].C : 0;
     else if (k == "stall_window") *value = h->stall_window;
     else if (k == "chunk") *value = h->chunk;
     else return fail(KS_ERR_ARG, "unknown option " + k);
     return KS_OK;
+}
+
+extern "C" int ks_get_history(ks_loop_t h, int b, long long* steps, double* sqrtJ, int* prec,
+                              int cap) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (b < 0 || b >= h->d.B) return fail(KS_ERR_ARG, "loop index out of range");
+    if (b >= (int)h->hist_steps.size()) return 0;
+    const int n = (int)h->hist_steps[b].size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (steps) steps[i] = h->hist_steps[b][i];
+        if (sqrtJ) sqrtJ[i] = h->hist_sqrtJ[b][i];
+        if (prec) prec[i] = h->hist_prec[b][i];
+    }
+    return n;
 }

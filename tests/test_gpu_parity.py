@@ -228,9 +228,11 @@ def test_persistent_kernel_equals_phase_launches(mode):
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
 
-def test_mixed_descent_converges_and_switches():
-    """FP32 bulk, then FP64 finish: a small-amplitude loop descends to sqrt(J) < 1e-10 (the
-    constant equilibria attract it); the result is in the same class as a plain FP64 descent's."""
+@pytest.mark.parametrize("f32_adjoint", [1, 0])
+def test_mixed_descent_converges_and_switches(f32_adjoint):
+    """FP32 bulk, then FP64 finish (with the adjoint half of each finishing step in float, or
+    all in double): a small-amplitude loop descends to sqrt(J) < 1e-10 (the constant
+    equilibria attract it); the result is in the same class as a plain FP64 descent's."""
     L, nx, nss = 22.0, 32, [32, 64]
     us, Ts = make(nx, nss, L, T_range=(30.0, 50.0))
     us = [1e-2 * a for a in us]
@@ -242,10 +244,16 @@ def test_mixed_descent_converges_and_switches():
         st = torch.zeros(2, dtype=torch.int32, device="cuda")
         with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15, tol=1e-10, switch_tol=1e-6,
                       chunk=2000) as h:
+            if mode == K.KS_MIXED:
+                K.ks_set_option(h.handle, "finish_f32_adjoint", f32_adjoint)
             K.ks_descend(h.handle, u, T, 400000, 1e-10, steps, sq, st)
-        res[mode] = (u.cpu().numpy(), steps.tolist(), sq.tolist(), st.tolist())
+            if mode == K.KS_MIXED:
+                hs, hq, hp = K.ks_get_history(h.handle, 0)
+                assert hp[0] == 1 and hp[-1] == 0      # float bulk, then double finish
+                assert np.all(np.diff(hs) > 0)
+        res[mode] = (u.cpu().numpy(), steps.tolist(), sq.tolist(), st.tolist(), T.cpu().numpy())
     for mode in (K.KS_FP64, K.KS_MIXED):
-        u, steps, sq, st = res[mode]
+        u, steps, sq, st, _ = res[mode]
         assert st == [K.KS_CONVERGED] * 2, (mode, st, sq, steps)
         assert max(sq) < 1e-10
         # u = const is an equilibrium for every constant (Sec. 4.1): the mean may drift, the
