@@ -89,6 +89,29 @@ def kernel_flops(kind: str, nx: int, nss, steps_per_launch: int = 1) -> float:
     return 0.0
 
 
+def csrc_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2007_06427_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch from the committed ncu capture, if the CUDA sources still match."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("source_sha") != csrc_hash():
+        return None
+    e = t.get("kernels", {}).get(f"{workload}/{kernel}")
+    return None if e is None else e.get("bytes_per_launch")
+
+
 def step_flops(nx, nss) -> float:
     return sum(kernel_flops(k, nx, nss) for k in ("rows_nonlin", "cols_resid", "rows_adj",
                                                    "cols_update"))
@@ -321,7 +344,7 @@ def ours_arm(args):
         ach = fl / (ms / cnt / 1e3) / 1e12 if ms > 0 else 0.0
         pk = PEAK_TFLOPS["f32" if dname.endswith("f32") else "f64"]
         roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": None, "kernel": dname,
+                "frac": ach / pk, "traffic": measured_traffic(w.name, dname), "kernel": dname,
                 "flops_per_launch": fl, "ms_per_launch": ms / cnt,
                 "share": ms / max(sum(v[0] for v in prof.values()), 1e-30),
                 "peak_source": ("nominal GB300 FP64 rate (1.25 TFLOP/s)" if not dname.endswith("f32")
@@ -432,7 +455,8 @@ def throughput_fp32(args, w, dev, flush, K):
         fl = kernel_flops(dname, w.nx, w.ns)
         ach = fl / (ms / cnt / 1e3) / 1e12
         out["roofline"] = {"bound": "alu", "achieved": ach, "peak": PEAK_TFLOPS["f32"],
-                           "unit": "TFLOP/s", "frac": ach / PEAK_TFLOPS["f32"], "traffic": None,
+                           "unit": "TFLOP/s", "frac": ach / PEAK_TFLOPS["f32"],
+                           "traffic": measured_traffic(w.name, dname),
                            "kernel": dname, "ms_per_launch": ms / cnt}
     return out
 
