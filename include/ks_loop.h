@@ -97,7 +97,7 @@ typedef struct {
     double switch_tol;   /* KS_MIXED: switch to double once sqrt(J) <= switch_tol */
     long long max_steps; /* default step cap of ks_descend (used when its max_steps < 0) */
     int chunk;           /* tau-steps between convergence read-backs in ks_descend (> 0) */
-    int autotune;        /* 0: default launch shapes; 1: time the candidates once at create */
+    int autotune;        /* 0: default launch shapes; 1: ks_autotune at create */
 } ks_config;
 
 /* Create a handle: validates cfg, allocates the device workspace for the batch (band states,
@@ -178,6 +178,9 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *                    a window is stalled (default 1000): the float phase of a mixed descent
  *                    then switches to double, a double descent stops with KS_STALLED
  *   "chunk"          tau-steps between read-backs in ks_descend
+ *   "test_barrier_timeout" test hook: 1 makes every grid barrier of the path-1 kernel wait
+ *                    for one arrival that never comes, so each wait runs out (about a second)
+ *                    and the next read-back returns KS_ERR_TIMEOUT; 0 (default) restores it
  *   "finish_f32_adjoint"  KS_MIXED handles: 1 (default): the finishing steps keep the state,
  *                    the residual, J, dJ/dT and the update in double and form only the descent
  *                    direction G (the adjoint half of a step) in float; 0: all-double finish */
@@ -218,6 +221,15 @@ KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
  * through ks_last_error(). */
 KS_API int ks_residual_noalloc(double L, int nx, int ns, const double* u, double T, double* r,
                                double* J, void* stream);
+
+/* Time the launch candidates of this batch (cluster-resident kernel for each cluster size that
+ * fits, with 128 and 256 threads per CTA; grid-persistent kernel; four launches per step) on a
+ * synthetic band-limited state and keep the fastest for the precision the descent spends its
+ * bulk in.  If the environment variable KS_AUTOTUNE_CACHE names a file, choices are read from
+ * and appended to it, keyed by Nx, the Ns list, the batch size, the mode and the scheme.
+ * Clears the resident state (call ks_set_state afterwards).  All candidates give the same
+ * results bit for bit; only the time differs. */
+KS_API int ks_autotune(ks_loop_t h);
 
 /* Message for the last non-zero return on the calling thread ("" if none). */
 KS_API const char* ks_last_error(void);

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -58,16 +59,24 @@ __global__ void k_prep_wT(const double* T, double* wT, int B) {
 
 // ---- grid-wide barrier with a bounded wait -------------------------------------------------
 // Sense-free generation barrier: each CTA reads the generation, arrives on the counter; the
-// last arrival resets the counter and bumps the generation.  Waiters give up after
-// KS_SPIN_LIMIT polls (about a second), set the error word and leave; every CTA then returns
-// at its next barrier, so an inconsistent launch ends instead of hanging.
+// last arrival resets the counter and bumps the generation.  Waiters give up after about a
+// second (global timer), set the error word and leave; every CTA then returns at its next
+// barrier, so an inconsistent launch ends instead of hanging.
 struct GridBar {
     unsigned int* count;
     unsigned int* gen;
     int* err;
+    unsigned int extra;  // arrivals expected beyond the grid: 0, or 1 to test the timeout path
 };
 
-#define KS_SPIN_LIMIT (1u << 23)
+#define KS_SPIN_LIMIT (1u << 26)
+#define KS_WAIT_NS 1000000000ull
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
     unsigned int v;
@@ -83,14 +92,17 @@ __device__ __forceinline__ bool grid_sync(const GridBar& g) {
         __threadfence();
         const unsigned int a = atomicAdd(g.count, 1u);
         int good = 1;
-        if (a == gridDim.x - 1) {
+        if (a == gridDim.x - 1 + g.extra) {
             atomicExch(g.count, 0u);
             __threadfence();
             atomicAdd(g.gen, 1u);
         } else {
+            // bounded wait: give up after KS_WAIT_NS of the GPU's global timer (or, as a
+            // second guard, KS_SPIN_LIMIT polls)
+            const unsigned long long t0 = globaltimer_ns();
             unsigned int it = 0;
             while (ld_acquire_gpu(g.gen) == my) {
-                if (++it > KS_SPIN_LIMIT) {
+                if (++it > KS_SPIN_LIMIT || ((it & 63) == 0 && globaltimer_ns() - t0 > KS_WAIT_NS)) {
                     atomicExch(g.err, 1);
                     good = 0;
                     break;
@@ -260,6 +272,7 @@ struct ks_loop {
     int cthreads = 128;
     int cgrid[3] = {0, 0, 0};
     int finish_f32_adjoint = 1;     // mixed descents: finishing steps form the adjoint in float
+    int test_barrier_extra = 0;     // test hook: the grid barrier waits for arrivals that never come
     // persistent kernel
     bool persistent = true;
     int pgrid[2] = {0, 0};
@@ -677,7 +690,7 @@ int run_persist(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     int par0 = w.par;
     int nrow = (int)h->rows.size();
     int ncol = h->d.B * h->d.nkx;
-    GridBar bar{h->d_bar, h->d_bar + 1, h->d_err};
+    GridBar bar{h->d_bar, h->d_bar + 1, h->d_err, (unsigned int)h->test_barrier_extra};
     void* args[] = {&d, &p, &ns_i, &par0, &nrow, &ncol, &bar};
     LaunchScope ls(h, s, std::string("persist") + prec_suffix(pr));
     KS_CUDA(cudaLaunchCooperativeKernel((const void*)k_persist<R>, dim3(h->pgrid[pr]), dim3(128),
@@ -836,6 +849,8 @@ int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 extern "C" const char* ks_last_error(void) { return g_err.c_str(); }
 extern "C" const char* ks_version(void) { return KS_VERSION_STRING; }
 extern "C" unsigned long long ks_config_sizeof(void) { return sizeof(ks_config); }
+
+int ks_autotune_impl(ks_loop* h);
 
 extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     g_err.clear();
@@ -1015,6 +1030,7 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     h->h_prec.assign(B, 0);
     h->h_sqrtJ.assign(B, 0.0);
     h->h_steps.assign(B, 0);
+    if (h->autotune && (rc = ks_autotune_impl(h))) return cleanup(rc);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(fail(KS_ERR_CUDA, cudaGetErrorString(e)));
     *out = h;
@@ -1473,6 +1489,8 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         if (h->mode == KS_MIXED) KS_TRY((setup_cluster<double, float>(h)));
         if (value && (h->cplan[0].C != value && h->cplan[1].C != value))
             return fail(KS_ERR_ARG, "requested cluster size does not fit this batch");
+    } else if (k == "test_barrier_timeout") {
+        h->test_barrier_extra = value ? 1 : 0;
     } else if (k == "finish_f32_adjoint") {
         h->finish_f32_adjoint = value != 0;
     } else if (k == "stall_window") {
@@ -1502,6 +1520,7 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "cluster_smem_f32") *value = h->cplan[1].bytes;
     else if (k == "rows_per_tile") *value = h->rows_per_tile;
     else if (k == "finish_f32_adjoint") *value = h->finish_f32_adjoint;
+    else if (k == "cluster_threads") *value = h->cthreads;
     else if (k == "cluster_mixed_finish") *value = h->cplan[2].bytes ? h->cplan[2].C : 0;
     else if (k == "stall_window") *value = h->stall_window;
     else if (k == "chunk") *value = h->chunk;
@@ -1522,4 +1541,150 @@ extern "C" int ks_get_history(ks_loop_t h, int b, long long* steps, double* sqrt
         if (prec) prec[i] = h->hist_prec[b][i];
     }
     return n;
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuner: time the launch candidates of this batch on a synthetic band-limited state and
+// keep the fastest.  Candidates: the cluster-resident kernel for every cluster size whose
+// shared-memory plan fits, with 128 or 256 threads per CTA; the grid-persistent kernel; four
+// launches per step.  The tuned precision is the one a descent spends its bulk in (float for
+// KS_FP32 and KS_MIXED handles, double for KS_FP64).  Choices are cached in the text file named
+// by the environment variable KS_AUTOTUNE_CACHE, if set, keyed by the batch shape and mode.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct TuneChoice {
+    int path, cluster, threads;
+};
+
+std::string tune_key(const ks_loop* h) {
+    unsigned long long hs = 1469598103934665603ull;  // FNV-1a over the Ns list
+    for (int v : h->ns) {
+        hs ^= (unsigned long long)v;
+        hs *= 1099511628211ull;
+    }
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "nx=%d B=%d ns=%016llx mode=%d scheme=%d", h->d.nx, h->d.B, hs,
+                  h->mode, h->d.scheme);
+    return buf;
+}
+
+bool cache_lookup(const std::string& key, TuneChoice& c) {
+    const char* path = std::getenv("KS_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[256];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string ln(line);
+        const size_t bar = ln.find('|');
+        if (bar == std::string::npos || ln.substr(0, bar) != key) continue;
+        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d", &c.path, &c.cluster, &c.threads) == 3)
+            found = true;
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string& key, const TuneChoice& c) {
+    const char* path = std::getenv("KS_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s|%d %d %d\n", key.c_str(), c.path, c.cluster, c.threads);
+    std::fclose(f);
+}
+
+int apply_choice(ks_loop* h, const TuneChoice& c) {
+    h->path = c.path;
+    h->force_cluster = c.cluster;
+    h->cthreads = c.threads;
+    KS_TRY((setup_cluster<double, double>(h)));
+    KS_TRY((setup_cluster<float, float>(h)));
+    if (h->mode == KS_MIXED) KS_TRY((setup_cluster<double, float>(h)));
+    return KS_OK;
+}
+
+}  // namespace
+
+int ks_autotune_impl(ks_loop* h) {
+    const std::string key = tune_key(h);
+    TuneChoice best{0, 0, 128};
+    if (cache_lookup(key, best)) return apply_choice(h, best);
+    const int pr = (h->mode == KS_FP64) ? P64 : P32;
+    // synthetic state: a few band modes of amplitude ~0.5, T = 40, on the grid (double)
+    const int nx = h->d.nx;
+    std::vector<double> u((size_t)h->ngrid);
+    for (int b = 0; b < h->d.B; ++b) {
+        const int ns = h->ns[b];
+        for (int n = 0; n < ns; ++n)
+            for (int m = 0; m < nx; ++m) {
+                const double x = 6.283185307179586 * m / nx, t = 6.283185307179586 * n / ns;
+                u[(size_t)h->goff[b] + (size_t)n * nx + m] =
+                    0.5 * std::sin(x + t) + 0.3 * std::cos(2 * x - t) + 0.1 * std::sin(3 * x + 2 * t);
+            }
+    }
+    std::vector<double> T(h->d.B, 40.0);
+    std::vector<float> uf;
+    const void* usrc = u.data();
+    if (h->mode == KS_FP32) {
+        uf.assign(u.begin(), u.end());
+        usrc = uf.data();
+    }
+    double* dT = nullptr;
+    void* du = nullptr;
+    KS_TRY(dev_alloc(h, (void**)&dT, h->d.B * sizeof(double)));
+    KS_TRY(dev_alloc(h, &du, (size_t)h->ngrid * elem_size(h->mode == KS_FP32 ? P32 : P64)));
+    KS_CUDA(cudaMemcpy(dT, T.data(), h->d.B * sizeof(double), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpy(du, usrc, (size_t)h->ngrid * elem_size(h->mode == KS_FP32 ? P32 : P64),
+                       cudaMemcpyHostToDevice));
+    std::vector<TuneChoice> cands;
+    for (int C : {16, 8, 4, 2, 1})
+        for (int th : {128, 256}) cands.push_back(TuneChoice{0, C, th});
+    cands.push_back(TuneChoice{1, 0, 128});
+    cands.push_back(TuneChoice{2, 0, 128});
+    cudaEvent_t e0, e1;
+    KS_CUDA(cudaEventCreate(&e0));
+    KS_CUDA(cudaEventCreate(&e1));
+    const int S = std::max(2, (int)std::min<long long>(40, 4000000LL / std::max<long long>(1, h->ngrid)));
+    float best_ms = 1e30f;
+    for (const TuneChoice& c : cands) {
+        if (apply_choice(h, c) != KS_OK) continue;
+        if (c.path == 0) {
+            const int slot = pr == P64 ? 0 : 1;
+            if (!h->cplan[slot].bytes || h->cplan[slot].C != c.cluster) continue;
+        }
+        if (c.path == 1 && !h->pgrid[pr]) continue;
+        if (set_state_full(h, du, dT, 0) != KS_OK) continue;
+        if (steps_impl(h, 2, 0.0, 0) != KS_OK) continue;
+        KS_CUDA(cudaEventRecord(e0, 0));
+        for (int rep = 0; rep < 3; ++rep)
+            if (steps_impl(h, S, 0.0, 0) != KS_OK) break;
+        KS_CUDA(cudaEventRecord(e1, 0));
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->state_set = false;
+    h->launches = 0;
+    cache_store(key, best);
+    return apply_choice(h, best);
+}
+
+extern "C" int ks_autotune(ks_loop_t h) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    KS_TRY(ks_autotune_impl(h));
+    KS_CUDA(cudaDeviceSynchronize());
+    return KS_OK;
 }

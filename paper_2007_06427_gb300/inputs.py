@@ -118,8 +118,14 @@ def workload(name: str, batch: Optional[int] = None) -> Workload:
         b = 8 if batch is None else batch
         return make_loops(name, 256, 100.0, range(b), ns=1024, T0=120.0, decay=(8.0, 8.0),
                           scheme=1, dtau=0.15, meta={"switch_tol": 1e-5, "tol": 1e-10})
+    if name == "paper_L39_64x64":
+        # the paper's own numerical setting (Sec. 4.4): L = 39, 64 x 64 modes, dtau = 0.15,
+        # T0 = 40, here on a seeded spectral loop in place of the authors' recurrence guess
+        b = 1 if batch is None else batch
+        return make_loops(name, 64, 39.0, range(b), ns=64, T0=40.0, scheme=1, dtau=0.15,
+                          meta={"tol": 1e-12})
     raise KeyError(name)
 
 
 WORKLOADS = ("single_32x32_explicit", "single_64x128_imex", "batch16_64x64",
-             "ragged256_64xNs", "large8_256x1024")
+             "ragged256_64xNs", "large8_256x1024", "paper_L39_64x64")

@@ -1,0 +1,43 @@
+"""The autotuner picks a launch shape by timing; every candidate computes the same thing, so a
+tuned handle reproduces an untuned one bit for bit.  The on-disk cache is written once and
+reused."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2007_06427_gb300 import ks_loop as K
+from paper_2007_06427_gb300.inputs import spectral_loop
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32, K.KS_MIXED])
+def test_tuned_handle_reproduces_default(mode, tmp_path, monkeypatch):
+    monkeypatch.setenv("KS_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    L, nx, nss = 22.0, 64, [64, 128, 32]
+    us, Ts = [], []
+    for i, n in enumerate(nss):
+        u, T, _ = spectral_loop(i, nx, L, ns=n, T_range=(20.0, 80.0))
+        us.append(u)
+        Ts.append(T)
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    outs = []
+    for tune in (0, 1):
+        u = torch.tensor(np.concatenate([a.ravel() for a in us]), device="cuda").to(dt)
+        T = torch.tensor(Ts, dtype=torch.float64, device="cuda")
+        with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15, autotune=tune, chunk=6) as h:
+            if tune:
+                assert K.ks_get_option(h.handle, "path") in (0, 1, 2)
+                assert K.ks_get_option(h.handle, "cluster_threads") in (128, 256)
+            K.ks_descend(h.handle, u, T, 15, 0.0)
+        outs.append((u.cpu(), T.cpu()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    lines = open(tmp_path / "tune.txt").read().strip().splitlines()
+    assert len(lines) == 1 and "|" in lines[0]
+    # a second tuned handle of the same shape reads the cache instead of timing again
+    with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15, autotune=1) as h:
+        pass
+    assert len(open(tmp_path / "tune.txt").read().strip().splitlines()) == 1
