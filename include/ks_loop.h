@@ -144,6 +144,21 @@ KS_API int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, doub
  * tau is the convergence curve of the paper's Fig. 2. */
 KS_API int ks_get_history(ks_loop_t h, int b, long long* steps, double* sqrtJ, int* prec, int cap);
 
+/* Band-level access to the resident state, for bitwise checkpoints.  The band of loop b is
+ * (Kx+1) x (2 Ks_b + 1) complex coefficients u_hat_jk of Eq. 2D_Fourier, j = 0..Kx,
+ * k = -Ks_b..Ks_b, stored [j][k + Ks_b] as interleaved (re, im) doubles; loops follow one
+ * another in batch order.  ks_band_size gives the number of complex values (or -1).
+ * ks_get_band: band (double, 2 * size), T, the precision each loop descends in (0 double,
+ * 1 float) and the step counters (outputs nullable except band).  ks_set_band: installs a
+ * band, T, optional precisions (NULL: the mode's start) and optional step counters; every loop
+ * restarts as running.  Float loops are stored widened to double and narrowed back exactly,
+ * so get followed by set continues the descent bit for bit. */
+KS_API long long ks_band_size(ks_loop_t h);
+KS_API int ks_get_band(ks_loop_t h, double* band, double* T, int* prec, long long* steps,
+                       void* stream);
+KS_API int ks_set_band(ks_loop_t h, const double* band, const double* T, const int* prec,
+                       const long long* steps, void* stream);
+
 /* Resident state: load [P u; T] as the handle's descent state (status reset to running,
  * step counters to zero). */
 KS_API int ks_set_state(ks_loop_t h, const void* u, const double* T, void* stream);

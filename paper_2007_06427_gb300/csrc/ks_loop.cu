@@ -1688,3 +1688,92 @@ extern "C" int ks_autotune(ks_loop_t h) {
     KS_CUDA(cudaDeviceSynchronize());
     return KS_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+// Band-level state I/O (bitwise checkpoints): the band of every loop as interleaved complex
+// doubles, loops in batch order, each [j][k + Ks] with j = 0..Kx, k = -Ks..Ks.
+// ------------------------------------------------------------------------------------------
+namespace {
+__global__ void k_band_d2f_sel(const cpx<double>* src, cpx<float>* dst, const long long* boff,
+                               const int* prec, int B, int nkx, const int* ks) {
+    const int b = blockIdx.y;
+    if (b >= B || prec[b] != 1) return;
+    const long long n = (long long)nkx * (2 * ks[b] + 1);
+    const long long o = boff[b];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[o + i] = mk<float>((float)src[o + i].x, (float)src[o + i].y);
+}
+}  // namespace
+
+extern "C" long long ks_band_size(ks_loop_t h) { return h ? h->nband : -1; }
+
+extern "C" int ks_get_band(ks_loop_t h, double* band, double* T, int* prec, long long* steps,
+                           void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!h->state_set) return fail(KS_ERR_STATE, "ks_get_band before ks_set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    KS_TRY(readback(h, s));
+    Work& w = h->st;
+    Work& a = h->api;
+    const int B = h->d.B;
+    if (h->need[P32]) {
+        dim3 g(8, B);
+        k_band_merge<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (const cpx<double>*)w.uh[P64],
+                                       (cpx<double>*)a.uh[P64], h->d_boff, w.prec, B, h->d.nkx, h->d_ks);
+        KS_CUDA(cudaGetLastError());
+    } else {
+        KS_CUDA(cudaMemcpyAsync(a.uh[P64], w.uh[P64], (size_t)h->nband * sizeof(cpx<double>),
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    KS_TRY(copy_out(band, a.uh[P64], (size_t)h->nband * sizeof(cpx<double>), s));
+    KS_TRY(copy_out(T, w.T + (size_t)w.par * B, B * sizeof(double), s));
+    KS_TRY(copy_out(steps, w.steps, B * sizeof(long long), s));
+    if (prec) KS_CUDA(cudaMemcpyAsync(prec, h->h_prec.data(), B * sizeof(int), cudaMemcpyDefault, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+extern "C" int ks_set_band(ks_loop_t h, const double* band, const double* T, const int* prec,
+                           const long long* steps, void* stream) {
+    g_err.clear();
+    KS_TRY(check_handle(h));
+    if (!band || !T) return fail(KS_ERR_ARG, "band and T are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    Work& w = h->st;
+    const int B = h->d.B;
+    std::vector<int> pv(B, start_prec(h));
+    if (prec) {
+        KS_CUDA(cudaMemcpy(pv.data(), prec, B * sizeof(int), cudaMemcpyDefault));
+        for (int b = 0; b < B; ++b) {
+            if (pv[b] != P64 && pv[b] != P32) return fail(KS_ERR_ARG, "precision must be 0 or 1");
+            if (!h->need[pv[b]]) return fail(KS_ERR_ARG, "precision not available in this mode");
+        }
+    }
+    KS_CUDA(cudaMemcpyAsync(w.uh[P64], band, (size_t)h->nband * sizeof(cpx<double>), cudaMemcpyDefault, s));
+    KS_CUDA(cudaMemcpyAsync(w.T, T, B * sizeof(double), cudaMemcpyDefault, s));
+    w.par = 0;
+    k_prep_wT<<<(B + 127) / 128, 128, 0, s>>>(w.T, w.wT, B);
+    KS_CUDA(cudaGetLastError());
+    h->h_prec = pv;
+    KS_CUDA(cudaMemcpyAsync(w.prec, h->h_prec.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (h->need[P32]) {
+        dim3 g(8, B);
+        k_band_d2f_sel<<<g, 256, 0, s>>>((const cpx<double>*)w.uh[P64], (cpx<float>*)w.uh[P32], h->d_boff,
+                                         w.prec, B, h->d.nkx, h->d_ks);
+        KS_CUDA(cudaGetLastError());
+    }
+    KS_CUDA(cudaMemsetAsync(w.status, 0, B * sizeof(int), s));
+    KS_CUDA(cudaMemsetAsync(w.sqrtJ, 0, B * sizeof(double), s));
+    if (steps) KS_CUDA(cudaMemcpyAsync(w.steps, steps, B * sizeof(long long), cudaMemcpyDefault, s));
+    else KS_CUDA(cudaMemsetAsync(w.steps, 0, B * sizeof(long long), s));
+    h->h_status.assign(B, KS_RUNNING);
+    w.mix_valid[P64] = w.mix_valid[P32] = false;
+    h->state_set = true;
+    h->hist_steps.assign(B, {});
+    h->hist_sqrtJ.assign(B, {});
+    h->hist_prec.assign(B, {});
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "running", 1: "converged", 2: "step_cap", 3: "stalled", 4: "d
 _EXPORTS = ("ks_loop_create", "ks_destroy", "ks_residual", "ks_adjoint_grad", "ks_descend",
             "ks_set_state", "ks_step", "ks_get_state", "ks_last_error", "ks_version",
             "ks_config_sizeof", "ks_profile", "ks_profile_read", "ks_set_option", "ks_get_option",
-            "ks_residual_noalloc", "ks_get_history", "ks_autotune")
+            "ks_residual_noalloc", "ks_get_history", "ks_autotune", "ks_band_size",
+            "ks_get_band", "ks_set_band")
 
 
 class KsError(RuntimeError):
@@ -77,11 +78,15 @@ def load_library(path: str = LIB_PATH):
     lib.ks_residual_noalloc.argtypes = [dp, i32, i32, vp, dp, vp, vp, vp]
     lib.ks_get_history.argtypes = [vp, i32, vp, vp, vp, i32]
     lib.ks_autotune.argtypes = [vp]
+    lib.ks_band_size.argtypes = [vp]
+    lib.ks_band_size.restype = i64
+    lib.ks_get_band.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.ks_set_band.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ks_profile_read.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     for f in ("ks_loop_create", "ks_destroy", "ks_residual", "ks_adjoint_grad", "ks_descend",
               "ks_set_state", "ks_step", "ks_get_state", "ks_profile", "ks_profile_read",
               "ks_set_option", "ks_get_option", "ks_residual_noalloc", "ks_get_history",
-              "ks_autotune"):
+              "ks_autotune", "ks_get_band", "ks_set_band"):
         getattr(lib, f).restype = i32
     lib.ks_last_error.restype = ctypes.c_char_p
     lib.ks_version.restype = ctypes.c_char_p
@@ -194,6 +199,20 @@ def ks_residual_noalloc(L: float, nx: int, ns: int, u, T: float, r=None, J=None,
     """Residual of one double loop with no device allocation (device buffers only)."""
     _check(load_library().ks_residual_noalloc(float(L), int(nx), int(ns), _ptr(u), float(T),
                                               _ptr(r), _ptr(J), _stream(stream)))
+
+
+def ks_band_size(h) -> int:
+    return int(load_library().ks_band_size(h))
+
+
+def ks_get_band(h, band, T=None, prec=None, steps=None, stream=None) -> None:
+    _check(load_library().ks_get_band(h, _ptr(band), _ptr(T), _ptr(prec), _ptr(steps),
+                                      _stream(stream)))
+
+
+def ks_set_band(h, band, T, prec=None, steps=None, stream=None) -> None:
+    _check(load_library().ks_set_band(h, _ptr(band), _ptr(T), _ptr(prec), _ptr(steps),
+                                      _stream(stream)))
 
 
 def ks_autotune(h) -> None:
