@@ -56,8 +56,10 @@ typedef struct ks_loop* ks_loop_t;
 enum {
     KS_FP64 = 0,   /* every step in double */
     KS_FP32 = 1,   /* every step in float; reductions finished in double; T in double */
-    KS_MIXED = 2   /* ks_descend: float steps until sqrt(J) <= switch_tol or the float descent
-                      stalls, then double steps to the end; other calls compute in double */
+    KS_MIXED = 2   /* ks_descend: float steps while sqrt(J), evaluated in double at every
+                      read-back, exceeds switch_tol and keeps falling; then double steps to the
+                      end (the adjoint half of each in float unless "finish_f32_adjoint" is 0);
+                      other calls compute in double */
 };
 
 /* tau-integration scheme (Sec. 4.2) */
@@ -188,7 +190,7 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *   "persistent"     1 (default): each ks_step / descent chunk runs as one cooperative launch
  *                    whose CTAs step through the four phases with grid-wide barriers; 0: four
  *                    launches per tau-step.
- *   "stall_window"   tau-steps over which ks_descend measures progress (default 20000)
+ *   "stall_window"   tau-steps over which ks_descend measures progress (default 40000)
  *   "stall_drop_ppm" a loop whose sqrt(J) fell by less than this many parts per million over
  *                    a window is stalled (default 1000): the float phase of a mixed descent
  *                    then switches to double, a double descent stops with KS_STALLED

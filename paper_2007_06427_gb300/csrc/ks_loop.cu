@@ -244,7 +244,7 @@ struct ks_loop {
     long long max_steps = 1000000;
     int chunk = 1000;
     int autotune = 0;
-    long long stall_window = 20000;
+    long long stall_window = 40000;
     double stall_drop = 1e-3;
     std::vector<int> ns, lgns, ksv;
     std::vector<long long> boff, moff, goff;
@@ -1153,7 +1153,7 @@ int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
 }
 
 // run n steps of the resident state on the precisions that have live loops
-int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s) {
+int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_switch = true) {
     Work& w = h->st;
     bool live[2] = {false, false};
     for (int b = 0; b < h->d.B; ++b)
@@ -1165,7 +1165,7 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s) {
             else KS_TRY(run_prime<float>(h, w, pr, s));
         }
     }
-    const double swt = (h->mode == KS_MIXED) ? h->switch_tol : 0.0;
+    const double swt = (h->mode == KS_MIXED && device_switch) ? h->switch_tol : 0.0;
     const long long kMaxPerLaunch = 1 << 14;
     const bool clus[2] = {h->path == 0 && h->cplan[P64].bytes > 0, h->path == 0 && h->cplan[P32].bytes > 0};
     if ((!live[P32] || clus[P32]) && (!live[P64] || clus[P64])) {
@@ -1262,6 +1262,29 @@ int final_eval(ks_loop* h, cudaStream_t s) {
         else KS_TRY(run_residual<float>(h, w, pr, s));
         KS_TRY(run_finalize(h, w, Tc, pr, 1, s));
     }
+    return KS_OK;
+}
+
+// sqrt(J) of the resident state of every loop evaluated in double (the band of float loops
+// widened first): the residual evaluation of a mixed descent stays in double.  Uses the API
+// workspace; the resident state is not touched.
+int monitor_f64(ks_loop* h, cudaStream_t s, std::vector<double>& out) {
+    Work& w = h->st;
+    Work& a = h->api;
+    const int B = h->d.B;
+    dim3 g(8, B);
+    k_band_merge<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (const cpx<double>*)w.uh[P64],
+                                   (cpx<double>*)a.uh[P64], h->d_boff, w.prec, B, h->d.nkx, h->d_ks);
+    KS_CUDA(cudaGetLastError());
+    KS_CUDA(cudaMemcpyAsync(a.T, w.T + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    a.par = 0;
+    k_prep_wT<<<(B + 127) / 128, 128, 0, s>>>(a.T, a.wT, B);
+    KS_CUDA(cudaGetLastError());
+    KS_TRY(run_residual<double>(h, a, P64, s));
+    KS_TRY(run_finalize(h, a, a.T, P64, 0, s));
+    out.resize(B);
+    KS_CUDA(cudaMemcpyAsync(out.data(), a.sqrtJ, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
     return KS_OK;
 }
 
@@ -1364,16 +1387,25 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
     // stall detection: sqrt(J) at the start of the current window
     std::vector<double> win_val(B, -1.0);
     std::vector<long long> win_step(B, 0);
+    std::vector<double> mon;
+    // mixed descents: the float kernels do not switch on their own; the switch is decided here
+    // from sqrt(J) evaluated in double, which keeps falling after the float value has reached
+    // its noise floor
+    const bool monitor = (h->mode == KS_MIXED);
     long long done = 0;
     while (done < cap) {
         const long long c = std::min<long long>(h->chunk, cap - done);
-        KS_TRY(steps_impl(h, c, tl, s));
+        KS_TRY(steps_impl(h, c, tl, s, !monitor));
         done += c;
         KS_TRY(readback(h, s));
+        if (monitor) KS_TRY(monitor_f64(h, s, mon));
+        std::vector<double> val(B);
+        for (int b = 0; b < B; ++b)
+            val[b] = (monitor && h->h_prec[b] == P32) ? mon[b] : h->h_sqrtJ[b];
         for (int b = 0; b < B; ++b) {
             if (!h->hist_steps[b].empty() && h->hist_steps[b].back() == h->h_steps[b]) continue;
             h->hist_steps[b].push_back(h->h_steps[b]);
-            h->hist_sqrtJ[b].push_back(h->h_sqrtJ[b]);
+            h->hist_sqrtJ[b].push_back(val[b]);
             h->hist_prec[b].push_back(h->h_prec[b]);
         }
         std::vector<int> sel(B, 0);
@@ -1386,8 +1418,25 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
                 continue;
             }
             if (stb != KS_RUNNING) continue;
+            const double v = val[b];
+            if (monitor && h->h_prec[b] == P32) {
+                if (!(v == v) || v > 1e150) {
+                    stb = KS_DIVERGED;
+                    status_dirty = true;
+                    continue;
+                }
+                if (v < tl) {
+                    stb = KS_CONVERGED;  // the float loop already meets tol in double
+                    status_dirty = true;
+                    continue;
+                }
+                if (h->switch_tol > 0.0 && v <= h->switch_tol) {
+                    sel[b] = 1;
+                    any_switch = true;
+                    continue;
+                }
+            }
             // no-progress test over a window of stall_window steps
-            const double v = h->h_sqrtJ[b];
             if (win_val[b] < 0.0) {
                 win_val[b] = v;
                 win_step[b] = h->h_steps[b];
@@ -1417,9 +1466,14 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
         if (status_dirty) KS_TRY(set_status(h, s));
         if (!any_live) break;
     }
-    // final residual at the resident state, step-cap status for the loops still running
+    // final residual at the resident state (in double for every loop of a mixed descent),
+    // step-cap status for the loops still running
     KS_TRY(final_eval(h, s));
     KS_TRY(readback(h, s));
+    if (monitor) {
+        KS_TRY(monitor_f64(h, s, mon));
+        KS_CUDA(cudaMemcpyAsync(h->st.sqrtJ, mon.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     for (int b = 0; b < B; ++b)
         if (h->h_status[b] == KS_RUNNING || h->h_status[b] == ST_SWITCH) h->h_status[b] = KS_STEP_CAP;
     KS_TRY(set_status(h, s));
