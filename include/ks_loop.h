@@ -187,9 +187,25 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
                            long long* total_launches, int reset);
 
 /* Tuning knobs of a handle (KS_ERR_ARG for an unknown key or a bad value):
- *   "persistent"     1 (default): each ks_step / descent chunk runs as one cooperative launch
- *                    whose CTAs step through the four phases with grid-wide barriers; 0: four
- *                    launches per tau-step.
+ *   "path"           launch shape of ks_step / descent chunks: 0 (default) cluster-resident
+ *                    kernel (one thread-block cluster per loop, state in shared memory for the
+ *                    whole chunk, falls back to 1 where the loop does not fit); 1 one
+ *                    cooperative launch per chunk with grid-wide barriers between the four
+ *                    phases of a step; 2 four launches per tau-step.  All three give bit-identical
+ *                    results.
+ *   "persistent"     1: path 1, 0: path 2 (older spelling of "path")
+ *   "cluster"        0 (default): cluster size chosen per precision; 1..16: force this size
+ *                    (KS_ERR_ARG when no plan of that size fits the batch)
+ *   "symmetry"       1: restrict the descent to loops invariant under Xi: (x, s) -> (-x, s),
+ *                    u -> -u (the centre-symmetric subspace, Sec. 3).  Every later analysis of a
+ *                    grid field (ks_residual, ks_adjoint_grad, ks_set_state, ks_descend) projects
+ *                    it onto that subspace, ks_adjoint_grad returns the projected G, and every
+ *                    update is taken along the projected G, so the band state stays exactly
+ *                    invariant (u_hat[j][-k] = -conj(u_hat[j][k]) bit for bit, zero j = 0
+ *                    column).  0 (default): no projection; the flow still preserves the symmetry
+ *                    of an invariant loop up to rounding.  A state already resident keeps its
+ *                    non-invariant part (set the state again after changing the knob);
+ *                    ks_set_band stores the band as given.
  *   "stall_window"   tau-steps over which ks_descend measures progress (default 40000)
  *   "stall_drop_ppm" a loop whose sqrt(J) fell by less than this many parts per million over
  *                    a window is stalled (default 1000): the float phase of a mixed descent
@@ -206,7 +222,7 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
 /* Read a knob or a derived launch parameter: "path", "finish_f32_adjoint", "cluster_f64",
  * "cluster_f32", "cluster_mixed_finish" (cluster
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
- * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk". */
+ * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk", "symmetry". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
 
 /* Residual of ONE double-precision loop without allocating any device memory.

@@ -38,6 +38,12 @@ Readings where the paper is silent (each also listed in the design notes):
 * IMEX: Lambda_jk uses T at the start of the step; u and T are both advanced from the same
   state l^n.
 * Names: ``G`` is +L^dag_1 r (the ascent direction); ``dJdT`` is dJ/dT = 2 L^dag_2.
+* Centre-symmetric subspace (Sec. 3, Eq. KS_loop_sym; Sec. 5): with ``xi=True`` the loop is
+  restricted to the fields invariant under Xi: (x, s) -> (-x, s), u -> -u.  The input is
+  projected onto that subspace with the band, and the descent direction L^dag_1 r is
+  projected at every step (the flow preserves the symmetry of an invariant loop, so the
+  projection only removes rounding; it also makes the returned G the gradient of J within
+  the subspace).
 
 The grid layout is u[n, m] (n: s-sample, m: x-sample).  Spectral arrays are indexed by
 signed modes in the paper's ranges, k = -N/2 .. N/2-1 on axis 0 and j = -M/2 .. M/2-1 on
@@ -105,6 +111,18 @@ class Grid:
         """P: zero every mode outside |j| <= floor(M/3), |k| <= floor(N/3)."""
         return np.where(self.mask, uh, 0.0)
 
+    def xi(self, uh: np.ndarray) -> np.ndarray:
+        """Spectral image of Xi u (x, s) = -u(-x, s) (Eq. KS_loop_sym): uh_jk -> -uh_{-j,k}.
+
+        On the signed range j = -M/2 .. M/2-1 the mode -j sits at index (M - i) mod M of the
+        mode at index i (the Nyquist mode maps to itself)."""
+        neg = np.mod(self.Nx - np.arange(self.Nx), self.Nx)
+        return -uh[:, neg]
+
+    def xi_project(self, uh: np.ndarray) -> np.ndarray:
+        """Orthogonal projection onto the Xi-invariant loops, (u + Xi u) / 2."""
+        return 0.5 * (uh + self.xi(uh))
+
     def real_grid(self, uh: np.ndarray) -> np.ndarray:
         return self.to_grid(uh).real
 
@@ -130,10 +148,11 @@ def grid(Nx: int, Ns: int, L: float) -> Grid:
 # Residual, cost and adjoint (Sec. 2, Sec. 4.1, App. B)
 # ---------------------------------------------------------------------------------------
 
-def band_state(u: np.ndarray, L: float) -> np.ndarray:
-    """Project grid values onto the 2/3 band: uh = P F[u]."""
+def band_state(u: np.ndarray, L: float, xi: bool = False) -> np.ndarray:
+    """Project grid values onto the 2/3 band: uh = P F[u] (and onto the Xi subspace if xi)."""
     g = grid(u.shape[1], u.shape[0], L)
-    return g.project(g.to_spectral(np.asarray(u, dtype=np.float64)))
+    uh = g.project(g.to_spectral(np.asarray(u, dtype=np.float64)))
+    return g.xi_project(uh) if xi else uh
 
 
 def residual_hat(uh: np.ndarray, T: float, g: Grid):
@@ -190,22 +209,26 @@ def adjoint_u_hat(uh: np.ndarray, rh: np.ndarray, T: float, g: Grid, u=None) -> 
     return (1.0 / T) * rs_h + nl - rxx_h - rxxxx_h
 
 
-def residual(u: np.ndarray, T: float, L: float) -> dict:
+def residual(u: np.ndarray, T: float, L: float, xi: bool = False) -> dict:
     """Residual of the loop [P u; T] on the grid, with J and dJ/dT (Eq. KS_R, cost_function)."""
     g = grid(u.shape[1], u.shape[0], L)
-    uh = band_state(u, L)
+    uh = band_state(u, L, xi)
     rh, _, _ = residual_hat(uh, T, g)
     J = cost(rh, g)
     L2 = adjoint_T(uh, rh, T, g)
     return {"uh": uh, "rh": rh, "r": g.real_grid(rh), "J": J, "L2": L2, "dJdT": 2.0 * L2}
 
 
-def adjoint_grad(u: np.ndarray, T: float, L: float) -> dict:
-    """G = +L^dag_1 r on the grid and dJ/dT = 2 L^dag_2, at the loop [P u; T]."""
+def adjoint_grad(u: np.ndarray, T: float, L: float, xi: bool = False) -> dict:
+    """G = +L^dag_1 r on the grid and dJ/dT = 2 L^dag_2, at the loop [P u; T].
+
+    With xi, u is first projected onto the Xi subspace and G is the projected L^dag_1 r."""
     g = grid(u.shape[1], u.shape[0], L)
-    uh = band_state(u, L)
+    uh = band_state(u, L, xi)
     rh, ug, _ = residual_hat(uh, T, g)
     Gh = adjoint_u_hat(uh, rh, T, g, u=ug)
+    if xi:
+        Gh = g.xi_project(Gh)
     L2 = adjoint_T(uh, rh, T, g)
     return {"uh": uh, "rh": rh, "Gh": Gh, "G": g.real_grid(Gh), "J": cost(rh, g),
             "L2": L2, "dJdT": 2.0 * L2}
@@ -221,17 +244,20 @@ def linear_symbol(T: float, g: Grid) -> np.ndarray:
     return -(W / T) ** 2 - Q ** 8 + 2.0 * Q ** 6 - Q ** 4
 
 
-def step_hat(uh: np.ndarray, T: float, g: Grid, dtau: float, scheme: int):
+def step_hat(uh: np.ndarray, T: float, g: Grid, dtau: float, scheme: int, xi: bool = False):
     """One tau-step of Eq. KS_G from the band state (uh, T).
 
     Returns (uh_next, T_next, J, L2) where J and L2 are evaluated at the input state.
     IMEX (Sec. 4.2): (uh' - uh)/dtau = Lambda uh' + G_NL with G_NL the field flow minus
-    its linear part, G_NL = -L^dag_1 r - Lambda uh; explicit Euler for T.
+    its linear part, G_NL = -L^dag_1 r - Lambda uh; explicit Euler for T.  With xi the field
+    flow is the Xi-projected one (Lambda is even in j, so it commutes with the projection).
     """
     rh, u, _ = residual_hat(uh, T, g)
     J = cost(rh, g)
     L2 = adjoint_T(uh, rh, T, g)
     Gh = adjoint_u_hat(uh, rh, T, g, u=u)
+    if xi:
+        Gh = g.xi_project(Gh)
     flow = -Gh                      # du/dtau = -L^dag_1 (Eq. KS_G)
     if scheme == IMEX:
         lam = linear_symbol(T, g)
@@ -246,15 +272,16 @@ def step_hat(uh: np.ndarray, T: float, g: Grid, dtau: float, scheme: int):
 
 
 def descend(u: np.ndarray, T: float, L: float, dtau: float, scheme: int, nsteps: int,
-            tol: float = 0.0, record: bool = False) -> dict:
+            tol: float = 0.0, record: bool = False, xi: bool = False) -> dict:
     """Advance the loop [P u; T] by up to ``nsteps`` tau-steps.
 
     Stops before a step whose starting state already has sqrt(J) < tol (the convergence
     test of Sec. 4.3).  Returns the final grid field, T, the step count, sqrt(J) of the final
-    state and, optionally, the sqrt(J) history (one value per evaluated state).
+    state and, optionally, the sqrt(J) history (one value per evaluated state).  With xi the
+    descent runs in the Xi-invariant subspace (see ``step_hat``).
     """
     g = grid(u.shape[1], u.shape[0], L)
-    uh = band_state(u, L)
+    uh = band_state(u, L, xi)
     hist = []
     steps = 0
     while True:
@@ -265,7 +292,7 @@ def descend(u: np.ndarray, T: float, L: float, dtau: float, scheme: int, nsteps:
             hist.append(sq)
         if (tol > 0.0 and sq < tol) or steps >= nsteps:
             break
-        uh, T, _, _ = step_hat(uh, T, g, dtau, scheme)
+        uh, T, _, _ = step_hat(uh, T, g, dtau, scheme, xi)
         steps += 1
     out = {"u": g.real_grid(uh), "uh": uh, "T": T, "steps": steps, "sqrtJ": sq}
     if record:
@@ -329,13 +356,13 @@ def flow_expanded(u: np.ndarray, T: float, L: float) -> np.ndarray:
 # Batched helpers (a batch is a list of independent loops)
 # ---------------------------------------------------------------------------------------
 
-def residual_batch(us, Ts, L):
-    return [residual(u, T, L) for u, T in zip(us, Ts)]
+def residual_batch(us, Ts, L, xi=False):
+    return [residual(u, T, L, xi) for u, T in zip(us, Ts)]
 
 
-def adjoint_grad_batch(us, Ts, L):
-    return [adjoint_grad(u, T, L) for u, T in zip(us, Ts)]
+def adjoint_grad_batch(us, Ts, L, xi=False):
+    return [adjoint_grad(u, T, L, xi) for u, T in zip(us, Ts)]
 
 
-def descend_batch(us, Ts, L, dtau, scheme, nsteps, tol=0.0):
-    return [descend(u, T, L, dtau, scheme, nsteps, tol) for u, T in zip(us, Ts)]
+def descend_batch(us, Ts, L, dtau, scheme, nsteps, tol=0.0, xi=False):
+    return [descend(u, T, L, dtau, scheme, nsteps, tol, xi=xi) for u, T in zip(us, Ts)]

@@ -371,33 +371,53 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                 const R wT2 = wTr * wTr;
                 const RA wTa = (RA)wT;
                 const RA ins_a = (RA)ins;
+                // G_hat = (a + i omega/T) r_hat + F[P(u r_x)], in the adjoint precision
+                auto g_hat = [&](int i, int q, int k) {
+                    const cpx<RA> wh = scale(Mloc_a[i], ins_a);
+                    const RA a_lin = ta.lin[rank + q * C];
+                    const cpx<R> rr = rhl[q * nk + k + ks];
+                    const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
+                    const RA bk = (RA)k * wTa;
+                    const cpx<RA> G = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    return mk<R>((R)G.x, (R)G.y);
+                };
+                if (p.xi) {
+                    // Xi subspace: G_hat of every k into scr first; the update takes the
+                    // projected pair (j, k), (j, -k) from there and writes the new u_hat to Mloc
+                    for (int i = tid; i < ncol << lg; i += nt) {
+                        const int q = i >> lg, n = i & (ns - 1);
+                        const int k = (n < (ns >> 1)) ? n : n - ns;
+                        if (k >= -ks && k <= ks) scr[i] = g_hat(i, q, k);
+                    }
+                    __syncthreads();
+                }
+                cpx<R>* Y = p.xi ? Mloc : scr;
                 for (int i = tid; i < ncol << lg; i += nt) {
                     const int q = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
-                    const cpx<RA> wh = scale(Mloc_a[i], ins_a);
                     cpx<R> x = mk<R>(0, 0);
                     if (k >= -ks && k <= ks) {
                         const int j = rank + q * C;
-                        const RA a_lin = ta.lin[j];
-                        const cpx<R> rr = rhl[q * nk + k + ks];
-                        const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
-                        const RA bk = (RA)k * wTa;
-                        // G_hat = (a + i omega/T) r_hat + F[P(u r_x)], in the adjoint precision
-                        const cpx<RA> G = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                        cpx<R> G;
+                        if (p.xi)
+                            G = (j == 0) ? mk<R>(0, 0)
+                                         : xi_pair(scr[i], scr[(q << lg) + ((ns - n) & (ns - 1))]);
+                        else
+                            G = g_hat(i, q, k);
                         R f = dt;
                         if (d.scheme == 1) {
                             const R kk2 = (R)k * (R)k;
                             f = dt / ((R)1 + dt * (kk2 * wT2 + p.cq[j]));
                         }
                         cpx<R> u = uhl[q * nk + k + ks];
-                        u = u - scale(mk<R>((R)G.x, (R)G.y), f);
+                        u = u - scale(G, f);
                         uhl[q * nk + k + ks] = u;
                         x = u;
                     }
-                    scr[i] = x;
+                    Y[i] = x;
                 }
                 __syncthreads();
-                push_columns(fft_warp(scr, Mloc, lg, ncol, +1, tws), Rin);
+                push_columns(p.xi ? fft_warp(Mloc, scr, lg, ncol, +1, tws) : fft_warp(scr, Mloc, lg, ncol, +1, tws), Rin);
             }
             T = Tnext;
             wT = wTnext;

@@ -208,7 +208,19 @@ struct Bufs {
     double tol;             // freeze a loop once sqrt(J) < tol
     double switch_tol;      // float phase of a mixed descent: freeze as ST_SWITCH once sqrt(J) <= switch_tol
     int check_active;       // 1: skip loops that are not running in this precision
+    int xi;                 // 1: descent restricted to the Xi-invariant (centre-symmetric) subspace
 };
+
+// Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 3, the
+// symmetry of Eq. KS_G).  An invariant loop has u_hat_{j,-k} = -conj(u_hat_{j,k}) in the
+// half spectrum, and a zero j = 0 column.  With a the value at (j, k) and m the value at
+// (j, -k), the projected value at (j, k) is (a - conj(m)) / 2.  Evaluated at (j, -k) with the
+// two arguments exchanged, the result is exactly -conj of it (IEEE subtraction is antisymmetric
+// and addition commutative), so a projected band satisfies the relation bit for bit.
+template <typename R>
+KS_HD cpx<R> xi_pair(cpx<R> a, cpx<R> m) {
+    return mk<R>((R)0.5 * (a.x - m.x), (R)0.5 * (a.y + m.y));
+}
 
 // ------------------------------------------------------------------------------------
 // Batched Stockham FFT in shared memory.
@@ -755,7 +767,9 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         if constexpr (MODE == COL_ANALYZE) {
             for (int kk = KS_TID; kk < nk; kk += KS_NT) {
                 const int k = kk - ks;
-                p.uh[bo + kk] = scale(F[k & (ns - 1)], ins);
+                cpx<R> v = scale(F[k & (ns - 1)], ins);
+                if (p.xi) v = (j == 0) ? mk<R>(0, 0) : xi_pair(v, scale(F[(-k) & (ns - 1)], ins));
+                p.uh[bo + kk] = v;
             }
             KS_SYNC();
             return;
@@ -799,10 +813,21 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     const cpx<R> wh = scale(F[i], ins);
                     const cpx<R> r = p.rh[bo + (k + ks)];
                     const R bk = (R)k * w_over_T;             // +omega_k / T
-                    p.gh[bo + (k + ks)] = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    const cpx<R> G = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    if (p.xi) X[i] = G;
+                    else p.gh[bo + (k + ks)] = G;
                 }
             }
             KS_SYNC();
+            if (p.xi) {
+                // gradient within the Xi subspace: the projected G_hat
+                for (int i = KS_TID; i < ns; i += KS_NT) {
+                    const int k = (i < (ns >> 1)) ? i : i - ns;
+                    if (k >= -ks && k <= ks)
+                        p.gh[bo + (k + ks)] = (j == 0) ? mk<R>(0, 0) : xi_pair(X[i], X[(ns - i) & (ns - 1)]);
+                }
+                KS_SYNC();
+            }
         } else if constexpr (MODE == COL_UPDATE) {
             // J and L^dag_2 of this loop from the column partials: warp 0 sums them in a fixed
             // order (identical in every CTA of the loop, so all CTAs take the same decision)
@@ -834,15 +859,36 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             const R dt = (R)d.dtau;
             const R cqj = p.cq[j];
             const R wT2 = w_over_T * w_over_T;
+            if (p.xi) {
+                // Xi subspace: G_hat of every k into X first; the update below takes the
+                // projected pair (j, k), (j, -k) from there
+                for (int i = KS_TID; i < ns; i += KS_NT) {
+                    const int k = (i < (ns >> 1)) ? i : i - ns;
+                    if (k >= -ks && k <= ks) {
+                        const cpx<R> wh = scale(F[i], ins);
+                        const cpx<R> r = p.rh[bo + (k + ks)];
+                        const R bk = (R)k * w_over_T;
+                        X[i] = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    }
+                }
+                KS_SYNC();
+            }
+            // the new u_hat goes to X, or to F (free once G_hat is formed) in the Xi subspace
+            cpx<R>* Y = p.xi ? F : X;
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
                 cpx<R> x = mk<R>(0, 0);
                 if (k >= -ks && k <= ks) {
-                    const cpx<R> wh = scale(F[i], ins);
-                    const cpx<R> r = p.rh[bo + (k + ks)];
-                    const R bk = (R)k * w_over_T;
-                    // G_hat = (a + i omega/T) r_hat + F[P(u r_x)]                          (a9)
-                    const cpx<R> G = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    cpx<R> G;
+                    if (p.xi) {
+                        G = (j == 0) ? mk<R>(0, 0) : xi_pair(X[i], X[(ns - i) & (ns - 1)]);
+                    } else {
+                        const cpx<R> wh = scale(F[i], ins);
+                        const cpx<R> r = p.rh[bo + (k + ks)];
+                        const R bk = (R)k * w_over_T;
+                        // G_hat = (a + i omega/T) r_hat + F[P(u r_x)]                      (a9)
+                        G = mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                    }
                     R f = dt;
                     if (d.scheme == 1) {
                         // IMEX: dtau / (1 - dtau Lambda), Lambda = -(omega/T)^2 - q^4 (q^2-1)^2  (a10)
@@ -854,10 +900,10 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     p.uh[bo + (k + ks)] = u;
                     x = u;
                 }
-                X[i] = x;
+                Y[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
+            cpx<R>* v = fft_batch(Y, p.xi ? X : F, lg, 1, +1, p.tw);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             if (j == 0 && KS_TID == 0) {
                 const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)

@@ -272,6 +272,7 @@ struct ks_loop {
     int cthreads = 128;
     int cgrid[3] = {0, 0, 0};
     int finish_f32_adjoint = 1;     // mixed descents: finishing steps form the adjoint in float
+    int xi = 0;                     // 1: loads, gradients and updates projected onto the Xi subspace
     int test_barrier_extra = 0;     // test hook: the grid barrier waits for arrivals that never come
     // persistent kernel
     bool persistent = true;
@@ -442,6 +443,7 @@ Bufs<R> make_bufs(ks_loop* h, const Work& w, int pr, int check_active, double to
     p.tol = tol;
     p.switch_tol = switch_tol;
     p.check_active = check_active;
+    p.xi = h->xi;
     return p;
 }
 
@@ -1547,6 +1549,9 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         h->test_barrier_extra = value ? 1 : 0;
     } else if (k == "finish_f32_adjoint") {
         h->finish_f32_adjoint = value != 0;
+    } else if (k == "symmetry") {
+        if (value < 0 || value > 1) return fail(KS_ERR_ARG, "symmetry must be 0 (none) or 1 (Xi)");
+        h->xi = (int)value;
     } else if (k == "stall_window") {
         if (value < 1) return fail(KS_ERR_ARG, "stall_window must be >= 1");
         h->stall_window = value;
@@ -1578,6 +1583,7 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "cluster_mixed_finish") *value = h->cplan[2].bytes ? h->cplan[2].C : 0;
     else if (k == "stall_window") *value = h->stall_window;
     else if (k == "chunk") *value = h->chunk;
+    else if (k == "symmetry") *value = h->xi;
     else return fail(KS_ERR_ARG, "unknown option " + k);
     return KS_OK;
 }

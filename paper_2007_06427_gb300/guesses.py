@@ -13,6 +13,12 @@ loop closes smoothly.  This module provides both halves:
 * ``recurrence_loops``: the recurrence search, segment extraction, temporal low-pass onto the
   descent's band and resampling to Ns points in s.
 
+The paper takes its initial loops from a chaotic run within the subspace of centre-symmetric
+fields, u(-x) = -u(x) (Sec. 5); ``symmetric=True`` keeps the run there (an odd real field
+has purely imaginary Fourier coefficients, and the KSE preserves that, so the projection after
+each step only removes rounding).  Every later step of the extraction is linear and acts the
+same at x and -x, so the loops it returns are centre-symmetric as well.
+
 Host-side preprocessing (NumPy); the loops it returns are inputs for the GPU descent.
 """
 from __future__ import annotations
@@ -23,8 +29,12 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 
-def ks_dns(L: float, nx: int, dt: float, nsteps: int, u0: np.ndarray, save_every: int = 1):
-    """Integrate the KSE; returns (t [nsave], u [nsave, nx]) sampled every save_every steps."""
+def ks_dns(L: float, nx: int, dt: float, nsteps: int, u0: np.ndarray, save_every: int = 1,
+           symmetric: bool = False):
+    """Integrate the KSE; returns (t [nsave], u [nsave, nx]) sampled every save_every steps.
+
+    symmetric: stay in the centre-symmetric subspace (the real parts of the coefficients are
+    zeroed initially and after every step)."""
     k = np.fft.rfftfreq(nx, d=1.0 / nx)                 # 0 .. nx/2
     q = 2.0 * np.pi * k / L
     lin = q ** 2 - q ** 4                               # symbol of -u_xx - u_xxxx
@@ -45,7 +55,10 @@ def ks_dns(L: float, nx: int, dt: float, nsteps: int, u0: np.ndarray, save_every
         u = np.fft.irfft(vh, n=nx)
         return g * np.where(keep, np.fft.rfft(u * u), 0.0)
 
-    vh = np.where(keep, np.fft.rfft(np.asarray(u0, dtype=np.float64)), 0.0)
+    def sym(vh):
+        return 1j * vh.imag if symmetric else vh
+
+    vh = sym(np.where(keep, np.fft.rfft(np.asarray(u0, dtype=np.float64)), 0.0))
     ts, us = [0.0], [np.fft.irfft(vh, n=nx)]
     for n in range(1, nsteps + 1):
         Nv = N(vh)
@@ -55,7 +68,7 @@ def ks_dns(L: float, nx: int, dt: float, nsteps: int, u0: np.ndarray, save_every
         Nb = N(b)
         c = E2 * a + Q * (2.0 * Nb - Nv)
         Nc = N(c)
-        vh = E * vh + Nv * f1 + 2.0 * (Na + Nb) * f2 + Nc * f3
+        vh = sym(E * vh + Nv * f1 + 2.0 * (Na + Nb) * f2 + Nc * f3)
         if n % save_every == 0:
             ts.append(n * dt)
             us.append(np.fft.irfft(vh, n=nx))
@@ -126,12 +139,13 @@ def recurrence_loops(ts: np.ndarray, us: np.ndarray, L: float, ns: int,
 
 
 def chaotic_run(L: float, nx: int, t_end: float, dt: float = 0.25, seed: int = 0,
-                save_dt: float = 0.5, amplitude: float = 0.1):
-    """A chaotic KS trajectory from a small seeded perturbation (transient included)."""
+                save_dt: float = 0.5, amplitude: float = 0.1, symmetric: bool = False):
+    """A chaotic KS trajectory from a small seeded perturbation (transient included); with
+    symmetric, in the centre-symmetric subspace."""
     rng = np.random.default_rng(seed)
     x = L * np.arange(nx) / nx
     u0 = amplitude * (np.cos(2 * np.pi * x / L) * rng.standard_normal()
                       + np.sin(4 * np.pi * x / L) * rng.standard_normal()
                       + 0.3 * rng.standard_normal(nx))
     save_every = max(1, int(round(save_dt / dt)))
-    return ks_dns(L, nx, dt, int(round(t_end / dt)), u0, save_every)
+    return ks_dns(L, nx, dt, int(round(t_end / dt)), u0, save_every, symmetric=symmetric)

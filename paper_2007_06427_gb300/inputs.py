@@ -15,6 +15,10 @@ Recipe (per loop b, generator ``numpy.random.default_rng(seed_b)``, draws in thi
 5. u(x_m, s_n) = sum_jk c_jk exp(2 pi i (m j / N_x + n k / N_s)), then u is scaled so that its
    grid rms is 1.
 
+Centre-symmetric loops (``symmetric=True``, the subspace the paper's orbits lie in, Sec. 5):
+same draws, then c_jk <- (c_jk - conj(c_{j,-k})) / 2 before step 5, which makes u odd in x,
+u(-x, s) = -u(x, s).
+
 The loops are band limited by construction, so the 2/3-rule projection leaves them unchanged
 up to rounding.  The paper draws its initial loops from recurrences of a chaotic KS run
 (Sec. 4.3); these seeded spectral loops stand in for that data, which is not available.
@@ -55,7 +59,7 @@ class Workload:
 def spectral_loop(seed: int, nx: int, L: float, ns: Optional[int] = None,
                   ns_choices: Optional[Sequence[int]] = None, T0: Optional[float] = None,
                   T_range: Optional[Tuple[float, float]] = None, decay=(2.0, 2.0),
-                  rms: float = 1.0):
+                  rms: float = 1.0, symmetric: bool = False):
     """One seeded loop (u grid [Ns, Nx] float64, T0, Ns) following the module recipe."""
     rng = np.random.default_rng(seed)
     if ns_choices is not None:
@@ -74,6 +78,8 @@ def spectral_loop(seed: int, nx: int, L: float, ns: Optional[int] = None,
     amp = np.exp(-j / decay[0])[:, None] * np.exp(-np.abs(k) / decay[1])[None, :]
     c = (re + 1j * im) * amp
     c[0, :] = 0.0
+    if symmetric:
+        c = 0.5 * (c - np.conj(c[:, ::-1]))       # column k = -Ks..Ks reversed is -k
     # real synthesis: u = 2 Re sum_{j>=1} sum_k c_jk e^{2 pi i (m j / Nx + n k / Ns)}
     m = np.arange(nx)
     n = np.arange(ns)
@@ -87,18 +93,19 @@ def spectral_loop(seed: int, nx: int, L: float, ns: Optional[int] = None,
 
 
 def make_loops(name: str, nx: int, L: float, seeds: Sequence[int], *, ns=None, ns_choices=None,
-               T0=None, T_range=None, decay=(2.0, 2.0), scheme=1, dtau=0.15, meta=None):
+               T0=None, T_range=None, decay=(2.0, 2.0), scheme=1, dtau=0.15, meta=None,
+               symmetric=False):
     us, Ts, nss = [], [], []
     for sd in seeds:
         u, T, n = spectral_loop(sd, nx, L, ns=ns, ns_choices=ns_choices, T0=T0,
-                                T_range=T_range, decay=decay)
+                                T_range=T_range, decay=decay, symmetric=symmetric)
         us.append(u)
         Ts.append(T)
         nss.append(n)
     return Workload(name, float(L), int(nx), nss, Ts, us, scheme, float(dtau), dict(meta or {}))
 
 
-# The five workloads: sizes, periods and init decay rates of the descent benchmarks.
+# The named workloads: sizes, periods and init decay rates of the descent benchmarks.
 def workload(name: str, batch: Optional[int] = None) -> Workload:
     if name == "single_32x32_explicit":
         return make_loops(name, 32, 22.0, [0], ns=32, T0=40.0, scheme=0, dtau=1e-4,
@@ -124,8 +131,14 @@ def workload(name: str, batch: Optional[int] = None) -> Workload:
         b = 1 if batch is None else batch
         return make_loops(name, 64, 39.0, range(b), ns=64, T0=40.0, scheme=1, dtau=0.15,
                           meta={"tol": 1e-12})
+    if name == "paper_L39_xi_64x64":
+        # the same setting restricted to centre-symmetric loops, as the paper's initial loops
+        # and converged orbits are (Sec. 5); descended with the "symmetry" knob set to 1
+        b = 1 if batch is None else batch
+        return make_loops(name, 64, 39.0, range(b), ns=64, T0=40.0, scheme=1, dtau=0.15,
+                          meta={"tol": 1e-12, "symmetry": 1}, symmetric=True)
     raise KeyError(name)
 
 
 WORKLOADS = ("single_32x32_explicit", "single_64x128_imex", "batch16_64x64",
-             "ragged256_64xNs", "large8_256x1024", "paper_L39_64x64")
+             "ragged256_64xNs", "large8_256x1024", "paper_L39_64x64", "paper_L39_xi_64x64")

@@ -69,3 +69,23 @@ def test_batch16_64x64_fp32_gradient():
         off += n * w.nx
         assert np.linalg.norm(got - exact) <= 1e-5 * np.linalg.norm(exact)
         assert abs(T.grad[b].item() - (b + 1) * ref["dJdT"]) <= 1e-5 * abs((b + 1) * ref["dJdT"])
+
+
+def test_gradcheck_in_centre_symmetric_subspace():
+    """With the "symmetry" knob the cost is J(P_Xi P u) and its gradient the projected G:
+    full Jacobian check on a tiny ragged batch from non-invariant inputs."""
+    L, nx, nss = 22.0, 8, [8, 16]
+    us, Ts = [], []
+    for i, n in enumerate(nss):
+        u, T, _ = spectral_loop(i + 3, nx, L, ns=n, T_range=(20.0, 80.0))
+        us.append(u)
+        Ts.append(T)
+    u = torch.tensor(np.concatenate([a.ravel() for a in us]), device="cuda", requires_grad=True)
+    T = torch.tensor(Ts, dtype=torch.float64, device="cuda", requires_grad=True)
+    with K.KSLoop(L, nx, nss, K.KS_FP64) as h:
+        K.ks_set_option(h.handle, "symmetry", 1)
+        assert torch.autograd.gradcheck(lambda a, b: cost(a, b, h), (u, T), eps=1e-6,
+                                        atol=1e-6, rtol=1e-5)
+        J = cost(u, T, h)
+    for b in range(len(nss)):
+        assert abs(J[b].item() - ko.residual(us[b], Ts[b], L, xi=True)["J"]) <= 1e-12 * J[b].item()

@@ -26,3 +26,32 @@ def test_descent_from_recurrence_guess():
         hs, hq, _ = K.ks_get_history(h.handle, 0)
     assert np.all(np.diff(hq) <= 0)
     assert sq.item() < 0.05 * np.sqrt(J0.item())
+
+
+def test_descent_from_centre_symmetric_guess_at_L39():
+    """The paper's setting (Sec. 4.4-5): L = 39, 64 x 64, dtau = 0.15, a recurrence loop of a
+    centre-symmetric chaotic run, descended with the "symmetry" knob: J falls monotonically
+    and the band stays exactly invariant."""
+    L, nx, ns = 39.0, 64, 64
+    ts, us = chaotic_run(L, nx, 1500.0, seed=2, symmetric=True)
+    g = recurrence_loops(ts, us, L, ns, T_range=(10.0, 120.0), tol=0.01, t_min=200.0,
+                         max_loops=1)[0]
+    u = torch.tensor(g.u.ravel(), device="cuda")
+    T = torch.tensor([g.T], dtype=torch.float64, device="cuda")
+    with K.KSLoop(L, nx, [ns], K.KS_FP64, K.KS_IMEX, 0.15, chunk=1000) as h:
+        K.ks_set_option(h.handle, "symmetry", 1)
+        J0 = torch.empty(1, dtype=torch.float64, device="cuda")
+        K.ks_residual(h.handle, u, T, None, J0)
+        sq = torch.zeros(1, dtype=torch.float64, device="cuda")
+        K.ks_descend(h.handle, u, T, 20000, 1e-10, None, sq, None)
+        hs, hq, _ = K.ks_get_history(h.handle, 0)
+        nb = K.ks_band_size(h.handle)
+        band = torch.zeros(2 * nb, dtype=torch.float64, device="cuda")
+        K.ks_get_band(h.handle, band)
+    assert np.all(np.diff(hq) <= 0)
+    assert sq.item() < 0.2 * np.sqrt(J0.item())
+    a = band.cpu().numpy().reshape(nx // 3 + 1, 2 * (ns // 3) + 1, 2)
+    assert not a[0].any()
+    assert np.array_equal(a[1:, :, 0], -a[1:, ::-1, 0]) and np.array_equal(a[1:, :, 1], a[1:, ::-1, 1])
+    v = u.cpu().numpy().reshape(ns, nx)
+    assert np.abs(v + np.roll(v[:, ::-1], 1, axis=1)).max() < 1e-12 * np.abs(v).max()

@@ -49,3 +49,27 @@ def test_recurrence_loops_are_band_limited_near_solutions():
         r = rnd * math.sqrt(np.mean(lp.u ** 2))
         J_rnd = ko.residual(r, lp.T, L)["J"]
         assert J / e < 0.2 and J < 0.1 * J_rnd
+
+
+def _reflect(u):
+    """u(-x) on the grid x_m = m L / Nx (last axis)."""
+    return np.roll(u[..., ::-1], 1, axis=-1)
+
+
+def test_symmetric_run_and_loops_stay_centre_symmetric():
+    """In the centre-symmetric subspace (Sec. 5) the run stays odd in x and chaotic, and the
+    extracted loops are odd in x as well (L = 39, the paper's domain)."""
+    L, nx, ns = 39.0, 64, 64
+    ts, us = chaotic_run(L, nx, 1500.0, seed=2, symmetric=True)
+    assert np.abs(us + _reflect(us)).max() < 1e-13 * np.abs(us).max()
+    nrm = norm_series(us, L)
+    tail = nrm[-400:]
+    assert np.isfinite(nrm).all() and tail.mean() > 1.0 and np.ptp(tail) > 0.05 * tail.mean()
+    loops = recurrence_loops(ts, us, L, ns, T_range=(10.0, 120.0), tol=0.01, t_min=200.0,
+                             max_loops=2)
+    assert len(loops) >= 1
+    for lp in loops:
+        assert np.abs(lp.u + _reflect(lp.u)).max() < 1e-12 * np.abs(lp.u).max()
+        # the oracle's Xi projection leaves it unchanged
+        np.testing.assert_allclose(ko.band_state(lp.u, L, xi=True), ko.band_state(lp.u, L),
+                                   rtol=0, atol=1e-13 * np.abs(lp.u).max())

@@ -194,6 +194,72 @@ def test_center_symmetry_preserved():
     assert np.abs(G - _xi(G)).max() < 1e-11 * np.abs(G).max()
 
 
+def test_xi_projection_matches_grid_reflection():
+    """The spectral Xi projection equals the transform of (u(x, s) - u(-x, s)) / 2 formed on
+    the grid (Eq. KS_loop_sym), for an arbitrary field (all modes, Nyquist included)."""
+    rng = np.random.default_rng(21)
+    for Nx, Ns in [(8, 8), (16, 32), (32, 16)]:
+        g = ko.grid(Nx, Ns, 22.0)
+        u = rng.standard_normal((Ns, Nx))
+        spec = g.xi_project(g.to_spectral(u))
+        grid_side = g.to_spectral(0.5 * (u + _xi(u)))
+        np.testing.assert_allclose(spec, grid_side, rtol=0, atol=1e-15)
+
+
+def test_xi_projection_closed_forms():
+    """sin(q x) f(s) is Xi-invariant, cos(q x) f(s) is projected out; the projector is
+    idempotent and self-adjoint (an orthogonal projection)."""
+    Nx, Ns, L = 32, 32, 22.0
+    g = ko.grid(Nx, Ns, L)
+    x = L * np.arange(Nx)[None, :] / Nx
+    s = np.arange(Ns)[:, None] / Ns
+    f = np.cos(2 * math.pi * s) + 0.3 * np.sin(4 * math.pi * s + 0.2)
+    odd = np.sin(2 * math.pi * 3 * x / L) * f
+    even = np.cos(2 * math.pi * 2 * x / L) * f + 0.7
+    np.testing.assert_allclose(ko.band_state(odd, L, xi=True), ko.band_state(odd, L), atol=1e-15)
+    assert np.abs(ko.band_state(even, L, xi=True)).max() < 1e-15
+    np.testing.assert_allclose(ko.band_state(odd + even, L, xi=True), ko.band_state(odd, L),
+                               atol=1e-15)
+    rng = np.random.default_rng(3)
+    a = g.to_spectral(rng.standard_normal((Ns, Nx)))
+    b = g.to_spectral(rng.standard_normal((Ns, Nx)))
+    np.testing.assert_allclose(g.xi_project(g.xi_project(a)), g.xi_project(a), atol=1e-16)
+    lhs = np.vdot(g.xi_project(a), b)
+    rhs = np.vdot(a, g.xi_project(b))
+    assert abs(lhs - rhs) < 1e-15
+
+
+def test_xi_descent_equals_plain_descent_on_invariant_loop():
+    """On a Xi-invariant loop the projected descent follows the unprojected one (the flow
+    preserves the symmetry, Sec. 3): they differ by rounding only."""
+    u, T, _ = spectral_loop(4, 32, 22.0, ns=32, T0=40.0, symmetric=True)
+    a = ko.descend(u, T, 22.0, 0.15, ko.IMEX, 8)
+    b = ko.descend(u, T, 22.0, 0.15, ko.IMEX, 8, xi=True)
+    assert np.abs(a["u"] - b["u"]).max() < 1e-13 * np.abs(a["u"]).max()
+    assert b["T"] == pytest.approx(a["T"], rel=1e-14)
+    assert np.abs(b["u"] - _xi(b["u"])).max() < 1e-14 * np.abs(b["u"]).max()
+
+
+@pytest.mark.parametrize("Nx,Ns", [(8, 8), (16, 16)])
+def test_xi_gradient_matches_finite_differences(Nx, Ns):
+    """With xi, J(u) := J(P_Xi P u) and the returned G is its gradient: centred differences
+    along arbitrary (not invariant) directions from a non-invariant u match
+    (2L/(Nx Ns)) sum_grid G v."""
+    rng = np.random.default_rng(17)
+    L, T, h = 22.0, 33.0, 1e-6
+    u = _band_random(rng, Nx, Ns, L)
+    adj = ko.adjoint_grad(u, T, L, xi=True)
+    assert np.abs(adj["G"] - _xi(adj["G"])).max() < 1e-13 * np.abs(adj["G"]).max()
+    for _ in range(3):
+        v = rng.standard_normal((Ns, Nx))
+        fd = (ko.residual(u + h * v, T, L, xi=True)["J"]
+              - ko.residual(u - h * v, T, L, xi=True)["J"]) / (2 * h)
+        an = 2 * L / (Nx * Ns) * float(np.sum(adj["G"] * v))
+        assert fd == pytest.approx(an, rel=2e-7, abs=1e-9)
+    fdT = (ko.residual(u, T + h, L, xi=True)["J"] - ko.residual(u, T - h, L, xi=True)["J"]) / (2 * h)
+    assert fdT == pytest.approx(adj["dJdT"], rel=2e-7, abs=1e-9)
+
+
 def test_monotone_decrease_explicit():
     """J decreases at every one of 2000 explicit steps (Eq. J_variation), 32 x 32, L = 22."""
     u, T, _ = spectral_loop(0, 32, 22.0, ns=32, T0=40.0)
