@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                     Y[i] = x;
                 }
                 __syncthreads();
-                push_columns(p.xi ? fft_warp(Mloc, scr, lg, ncol, +1, tws) : fft_warp(scr, Mloc, lg, ncol, +1, tws), Rin);
+                push_columns(fft_warp(Y, p.xi ? scr : Mloc, lg, ncol, +1, tws), Rin);
             }
             T = Tnext;
             wT = wTnext;

@@ -302,11 +302,17 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
 // pass of it alone and synchronises with __syncwarp() between passes; one block barrier at
 // the end.  Same arithmetic in the same order as fft_batch (bit-identical results), far fewer
 // block-wide barriers.  Device code only.
+//
+// Double: an FP64 warp instruction costs the same issue time with idle lanes, and a 64-point
+// radix-4 pass has only 16 butterflies per transform, so the double transform runs as
+// fft_batch itself (butterflies of all transforms spread over full warps).  A float transform
+// is latency-bound and keeps one transform per warp.  (Unrolling the float passes for fixed
+// lengths saved little inside the step and cost instruction-cache misses after a launch.)
 // ------------------------------------------------------------------------------------
 #ifndef KS_HOST_EMULATION
 template <typename R>
-__device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
-                                            const cpx<R>* tw) {
+__device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
+                                                const cpx<R>* tw) {
     const int n = 1 << lg;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int span = 1;
@@ -335,25 +341,23 @@ __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cn
         const int tu = NMAX / (span * 4);
         for (int i = lane; i < nf * nb; i += 32) {
             const int f = w + (i >> (lg - 2)) * nw, j = i & (nb - 1);
-            {
-                const cpx<R>* s = a + (size_t)f * n;
-                cpx<R>* d = b + (size_t)f * n;
-                cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
-                const int jm = j & (span - 1);
-                if (span > 1) {
-                    const int t = jm * tu;
-                    v1 = cmul(v1, twid(tw, t, dir));
-                    v2 = cmul(v2, twid(tw, 2 * t, dir));
-                    v3 = cmul(v3, twid(tw, 3 * t, dir));
-                }
-                const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
-                const cpx<R> t3 = mul_i(v1 - v3, dir);
-                const int od = ((j - jm) << 2) + jm;
-                d[od] = t0 + t2;
-                d[od + span] = t1 + t3;
-                d[od + 2 * span] = t0 - t2;
-                d[od + 3 * span] = t1 - t3;
+            const cpx<R>* s = a + (size_t)f * n;
+            cpx<R>* d = b + (size_t)f * n;
+            cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+            const int jm = j & (span - 1);
+            if (span > 1) {
+                const int t = jm * tu;
+                v1 = cmul(v1, twid(tw, t, dir));
+                v2 = cmul(v2, twid(tw, 2 * t, dir));
+                v3 = cmul(v3, twid(tw, 3 * t, dir));
             }
+            const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
+            const cpx<R> t3 = mul_i(v1 - v3, dir);
+            const int od = ((j - jm) << 2) + jm;
+            d[od] = t0 + t2;
+            d[od + span] = t1 + t3;
+            d[od + 2 * span] = t0 - t2;
+            d[od + 3 * span] = t1 - t3;
         }
         __syncwarp();
         cpx<R>* t = a;
@@ -364,6 +368,13 @@ __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cn
     }
     __syncthreads();
     return a;
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
+                                            const cpx<R>* tw) {
+    if constexpr (sizeof(R) == 8) return fft_batch(a, b, lg, cnt, dir, tw);
+    else return fft_warp_any(a, b, lg, cnt, dir, tw);
 }
 #endif
 
