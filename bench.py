@@ -1,6 +1,7 @@
 #!/usr/bin/env python
-"""Benchmark of the KS loop tau-descent on GB300: tau-step gridpoints/s (and, with --to-tol,
-wall time to sqrt(J) < 1e-10 for plain FP64 against FP32-bulk + FP64-finish).
+"""Benchmark of the KS loop tau-descent on GB300: tau-step gridpoints/s and (unless --no-to-tol)
+wall time to sqrt(J) < 1e-10 for plain FP64 against FP32-bulk + FP64-finish, plus the FP64
+descent with the extrapolation of App. C.
 
 One bench step is one tau-step of the whole hot path (residual, reductions, adjoint, update)
 over the workload's batch, on the resident state in HBM.  The L2 cache is flushed (a 256 MiB
@@ -39,7 +40,7 @@ PEAK_TFLOPS = {"f64": 1.25, "f32": 152 * 128 * 2 * 2.070e9 / 1e12}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -137,7 +138,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -465,11 +466,15 @@ def throughput_fp32(args, w, dev, flush, K):
 
 
 def run_to_tol(args, w, dev):
-    """Plain FP64 descent vs FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol."""
+    """Plain FP64 descent vs FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol;
+    then the FP64 descent with the extrapolation of App. C (loop 0), for the step count."""
     import numpy as np
     import torch
     from paper_2007_06427_gb300 import ks_loop as K
+    from paper_2007_06427_gb300.accel import descend_extrapolated
     out = {}
+    clk = ClockSampler(dev.index if dev.index is not None else 0)
+    clk.start()
     for name, mode in (("fp64", K.KS_FP64), ("mixed", K.KS_MIXED)):
         h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, tol=args.tol,
                      switch_tol=args.switch_tol, max_steps=args.to_tol_max_steps, chunk=2000)
@@ -496,6 +501,22 @@ def run_to_tol(args, w, dev):
                      "loop0_switch_step": switch,
                      "loop0_history": [[int(a), float(c)] for a, c in zip(hs[::max(1, len(hs) // 40)], hq[::max(1, len(hq) // 40)])]}
         h.close()
+    if w.batch == 1:
+        h = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP64, w.scheme, w.dtau)
+        u = torch.from_numpy(w.packed()).to(dev, torch.float64)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = descend_extrapolated(h, u, float(w.T0[0]), tol=args.tol,
+                                 max_steps=args.to_tol_max_steps, chunk=1000)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        out["fp64_extrapolated"] = {
+            "seconds": el, "steps": [r.steps], "sqrtJ": [r.sqrtJ],
+            "status": [K.STATUS_NAMES.get(int(r.status), str(int(r.status)))], "T": [r.T],
+            "extrapolations": r.extrapolations, "rejected": r.rejected,
+            "note": "App. C: from sqrt(J) = 1e-3, geometric extrapolation each time sqrt(J) halves"}
+        h.close()
+    out["clocks"] = clk.stop()
     return out
 
 

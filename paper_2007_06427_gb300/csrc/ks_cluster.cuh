@@ -57,6 +57,19 @@ __device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, in
     }
 }
 
+// Two adjacent complex values to (possibly remote) shared memory: one 16-byte store for float
+// (the address is 16-byte aligned at every call site: even element index, aligned base), two
+// for double.  Halves the DSMEM store transactions of the float exchange.
+template <typename X>
+__device__ __forceinline__ void store_pair(cpx<X>* dst, cpx<X> a, cpx<X> b) {
+    if constexpr (sizeof(X) == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        dst[0] = a;
+        dst[1] = b;
+    }
+}
+
 // 16-byte copy global -> shared with up to eight loads in flight per thread (bytes % 16 == 0)
 __device__ __forceinline__ void copy16_g2s(void* dst, const void* src, int bytes) {
     const int4* s = reinterpret_cast<const int4*>(src);
@@ -121,39 +134,44 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
     const R h = (R)d.hx;
     const RA h_a = (RA)d.hx;
 
+    // no barrier after the table copies: the twiddles are first read after the barrier that
+    // closes the state load below, so the copies overlap the per-loop loads
     copy16_g2s(tws, p.tw, (int)(NMAX * sizeof(cpx<R>)));
     if (!kSame) copy16_g2s(tws_a, ta.tw, (int)(NMAX * sizeof(cpx<RA>)));
-    __syncthreads();
 
     for (int bi = cid; bi < B; bi += ncl) {
         const int b = p.colorder[bi];
-        // every rank reads the same global words: the skip is uniform across the cluster
-        if (p.prec[b] != p.myprec || p.status[b] != ST_RUNNING) {
-            if (rank == 0 && tid == 0 && p.status[b] != ST_RUNNING) {
-                p.T[(size_t)(par0 ^ 1) * B + b] = p.T[(size_t)par0 * B + b];
-                p.wT[(size_t)(par0 ^ 1) * B + b] = p.wT[(size_t)par0 * B + b];
+        // the skip test and the per-loop scalars in one round of loads; every rank reads the
+        // same global words, so the skip is uniform across the cluster
+        const int prec_b = p.prec[b], status_b = p.status[b];
+        const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b], nk = 2 * ks + 1;
+        const R ins = p.insv[b];
+        const size_t bo = (size_t)p.boff[b];
+        const long long moff_b = p.moff[b], goff_b = p.goff[b];
+        double T = p.T[(size_t)par0 * B + b];
+        double wT = p.wT[(size_t)par0 * B + b];
+        if (prec_b != p.myprec || status_b != ST_RUNNING) {
+            if (rank == 0 && tid == 0 && status_b != ST_RUNNING) {
+                p.T[(size_t)(par0 ^ 1) * B + b] = T;
+                p.wT[(size_t)(par0 ^ 1) * B + b] = wT;
             }
             continue;
         }
-        const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b], nk = 2 * ks + 1;
         const int ncol = (rank < nkx) ? (nkx - rank + C - 1) / C : 0;
         const int rpr = cluster_rows_per_rank(ns, C);
         const int row0 = rank * rpr;
         const int nrow = (row0 < ns) ? min(rpr, ns - row0) : 0;
-        const R ins = p.insv[b];
-        const size_t bo = (size_t)p.boff[b];
-        cpx<R>* Mg = p.M + p.moff[b];
-        R* Ul = cp.u_global ? p.U + p.goff[b] + (size_t)row0 * nx : Us;
-        double T = p.T[(size_t)par0 * B + b];
-        double wT = p.wT[(size_t)par0 * B + b];
+        cpx<R>* Mg = p.M + moff_b;
+        R* Ul = cp.u_global ? p.U + goff_b + (size_t)row0 * nx : Us;
 
-        // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)]
+        // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)],
+        // two rows per store (rows per rank and rmax are even, so a pair has one owner)
         auto push_columns = [&](const auto* X, auto* RinT) {
-            for (int i = tid; i < ncol << lg; i += nt) {
-                const int q = i >> lg, n = i & (ns - 1);
+            for (int i = tid; i < (ncol << lg) >> 1; i += nt) {
+                const int q = (2 * i) >> lg, n = (2 * i) & (ns - 1);
                 const int owner = n / rpr;
                 auto* dst = cl.map_shared_rank(RinT, owner);
-                dst[(size_t)(rank + q * C) * rmax + (n - owner * rpr)] = X[i];
+                store_pair(dst + (size_t)(rank + q * C) * rmax + (n - owner * rpr), X[2 * i], X[2 * i + 1]);
             }
         };
 
@@ -250,8 +268,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                     const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<R> sm = yj + ym, df = yj - ym;
                     cpx<R>* dst = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
-                    dst[0] = scale(sm, h);
-                    dst[1] = mk<R>(df.y * h, -df.x * h);
+                    store_pair(dst, scale(sm, h), mk<R>(df.y * h, -df.x * h));
                 }
                 __syncthreads();
                 t0 += nr;
@@ -262,30 +279,47 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
             if (ncol > 0) {
                 col_fft_inplace(Mloc, scr, lg, ncol, -1, tws);
                 const R wTr = (R)wT;
-                for (int q = 0; q < ncol; ++q) {
-                    const int j = rank + q * C;
-                    const R a_lin = p.lin[j], rq = p.qv[j];
-                    ColAcc<R> acc;
-                    for (int n = tid; n < ns; n += nt) {
-                        const int k = (n < (ns >> 1)) ? n : n - ns;
-                        cpx<R> x = mk<R>(0, 0);
-                        if (k >= -ks && k <= ks) {
-                            const cpx<R> ph = scale(Mloc[(q << lg) + n], ins);
-                            const cpx<R> u = uhl[q * nk + k + ks];
-                            const R bk = -(R)k * wTr;
-                            const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
-                            rhl[q * nk + k + ks] = r;
-                            acc.add(u, r, k);
-                            x = mk<R>(-rq * r.y, rq * r.x);
+                // columns in pairs: one block reduction for two columns' partials.  Element n
+                // of a column is accumulated by thread n mod COL_ACC_LANES, as in the item
+                // kernels, so the partials do not depend on the block size.
+                for (int q0 = 0; q0 < ncol; q0 += 2) {
+                    const bool two = q0 + 1 < ncol;
+                    ColAcc<R> acc[2];
+                    if (tid < COL_ACC_LANES) {
+                        for (int n = tid; n < ns; n += COL_ACC_LANES) {
+                            const int k = (n < (ns >> 1)) ? n : n - ns;
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                if (t == 1 && !two) break;
+                                const int q = q0 + t;
+                                const int j = rank + q * C;
+                                cpx<R> x = mk<R>(0, 0);
+                                if (k >= -ks && k <= ks) {
+                                    const R a_lin = p.lin[j], rq = p.qv[j];
+                                    const cpx<R> ph = scale(Mloc[(q << lg) + n], ins);
+                                    const cpx<R> u = uhl[q * nk + k + ks];
+                                    const R bk = -(R)k * wTr;
+                                    const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
+                                    rhl[q * nk + k + ks] = r;
+                                    acc[t].add(u, r, k);
+                                    x = mk<R>(-rq * r.y, rq * r.x);
+                                }
+                                scr_a[(q << lg) + n] = mk<RA>((RA)x.x, (RA)x.y);
+                            }
                         }
-                        scr_a[(q << lg) + n] = mk<RA>((RA)x.x, (RA)x.y);
                     }
-                    block_reduce(acc, red);
+                    if (two) block_reduce2(acc[0], acc[1], red);
+                    else block_reduce(acc[0], red);
                     if (tid < C) {
-                        const double wj = (j == 0) ? 1.0 : 2.0;
                         Part* dstp = cl.map_shared_rank(part, tid);
-                        dstp[j] = acc.part_J(wj);
-                        dstp[nkx + j] = acc.part_L(wj);
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            if (t == 1 && !two) break;
+                            const int j = rank + (q0 + t) * C;
+                            const double wj = (j == 0) ? 1.0 : 2.0;
+                            dstp[j] = acc[t].part_J(wj);
+                            dstp[nkx + j] = acc[t].part_L(wj);
+                        }
                     }
                 }
                 __syncthreads();
@@ -334,8 +368,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                     const cpx<RA> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<RA> sm = yj + ym, df = yj - ym;
                     cpx<RA>* dst = cl.map_shared_rank(Mloc_a, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
-                    dst[0] = scale(sm, h_a);
-                    dst[1] = mk<RA>(df.y * h_a, -df.x * h_a);
+                    store_pair(dst, scale(sm, h_a), mk<RA>(df.y * h_a, -df.x * h_a));
                 }
                 __syncthreads();
                 t0 += nr;
@@ -349,7 +382,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                 sum_partials(part, part + nkx, nkx, sJ, sL);
                 if (tid == 0) {
                     const double J = sJ * d.L;
-                    const double L2 = sL * d.L * wT / T;  // (L / T^2) 2 pi sum
+                    const double L2 = sL * d.L * (wT * wT) * kInv2Pi;  // (L / T^2) 2 pi sum
                     const double Tn = T - d.dtau * L2;    // explicit Euler for T (Sec. 4.2)
                     red[0] = J;
                     red[1] = Tn;

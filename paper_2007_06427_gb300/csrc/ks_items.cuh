@@ -508,6 +508,98 @@ KS_HD void block_reduce(ColAcc<float>& a, double* redd) {
 #endif
 }
 
+// Two columns' accumulators reduced together: the same shuffle tree and warp-sum order as
+// block_reduce for each of them (bit-identical partials), one set of block barriers for both.
+// red has room for 4 * (warps + 1) doubles.
+KS_HD void block_reduce2(ColAcc<double>& a, ColAcc<double>& b, double* red) {
+#ifdef KS_HOST_EMULATION
+    block_reduce(a, red);
+    block_reduce(b, red);
+#else
+    double v[4] = {a.J, a.L, b.J, b.L};
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) red[4 * w + t] = v[t];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[t] = (l < nw) ? red[4 * l + t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        if (l == 0)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) red[4 * nw + t] = v[t];
+    }
+    __syncthreads();
+    a.J = red[4 * nw];
+    a.L = red[4 * nw + 1];
+    b.J = red[4 * nw + 2];
+    b.L = red[4 * nw + 3];
+    __syncthreads();
+#endif
+}
+
+KS_HD void block_reduce2(ColAcc<float>& a, ColAcc<float>& b, double* redd) {
+#ifdef KS_HOST_EMULATION
+    (void)a;
+    (void)b;
+    (void)redd;
+#else
+    float* red = reinterpret_cast<float*>(redd);
+    ff v[4] = {a.J, a.L, b.J, b.L};
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            ff y;
+            y.hi = __shfl_xor_sync(0xffffffffu, v[t].hi, o);
+            y.lo = __shfl_xor_sync(0xffffffffu, v[t].lo, o);
+            v[t] = ff_add(v[t], y);
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            red[8 * w + 2 * t] = v[t].hi;
+            red[8 * w + 2 * t + 1] = v[t].lo;
+        }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            v[t].hi = (l < nw) ? red[8 * l + 2 * t] : 0.f;
+            v[t].lo = (l < nw) ? red[8 * l + 2 * t + 1] : 0.f;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                ff y;
+                y.hi = __shfl_xor_sync(0xffffffffu, v[t].hi, o);
+                y.lo = __shfl_xor_sync(0xffffffffu, v[t].lo, o);
+                v[t] = ff_add(v[t], y);
+            }
+        }
+        if (l == 0)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                red[8 * nw + 2 * t] = v[t].hi;
+                red[8 * nw + 2 * t + 1] = v[t].lo;
+            }
+    }
+    __syncthreads();
+    a.J = ff{red[8 * nw], red[8 * nw + 1]};
+    a.L = ff{red[8 * nw + 2], red[8 * nw + 3]};
+    b.J = ff{red[8 * nw + 4], red[8 * nw + 5]};
+    b.L = ff{red[8 * nw + 6], red[8 * nw + 7]};
+    __syncthreads();
+#endif
+}
+
 // Sum of the n column partials of one loop in a fixed order (lane l takes l, l+32, ..., then a
 // shuffle tree), identical in every CTA; every lane of the calling warp gets the sums.
 KS_HD void sum_partials(const double* a, const double* c, int n, double& sa, double& sc) {
@@ -723,7 +815,16 @@ enum ColMode {
 };
 
 // Shared-memory bytes a column item needs beyond its two transform buffers.
-constexpr int COL_RED_DOUBLES = 2 * (256 / 32 + 1) + 4;
+constexpr int COL_RED_DOUBLES = 4 * (256 / 32 + 1) + 4;
+
+// 1 / (2 pi), for L^dag_2 = (L / T^2) 2 pi S = L (2 pi / T)^2 S / (2 pi) from the stored 2 pi / T
+constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
+
+// Threads that accumulate one column's J and L^dag_2 partial: element n of a column goes to
+// accumulator n mod COL_ACC_LANES in every launch form, whatever the block size, so the partial
+// (and everything downstream of it) is the same bits in the item kernels (128 threads) and in a
+// cluster kernel of 128 or 256 threads.
+constexpr int COL_ACC_LANES = 128;
 
 template <typename R, int MODE>
 KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem, int par) {
@@ -848,7 +949,8 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
                 if (KS_TID == 0) {
                     red[0] = sJ * d.L;
-                    red[1] = sL * d.L * wTc[b] / T;  // (L / T^2) * 2 pi * sum
+                    // (L / T^2) * 2 pi * sum, with 2 pi / T^2 = (2 pi / T)^2 / (2 pi): no division
+                    red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
                 }
             }
             KS_SYNC();

@@ -548,7 +548,7 @@ int setup_persistent(ks_loop* h) {
     const size_t sm = std::max(h->lrow[pr].smem, h->lcol[pr].smem);
     KS_CUDA(cudaFuncSetAttribute(k_persist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0, sms = 0, coop = 0;
-    KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R>, 128, sm));
+    KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R>, COL_ACC_LANES, sm));
     KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
     KS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
     const int items = std::max((int)h->rows.size(), h->d.B * h->d.nkx);
@@ -695,7 +695,7 @@ int run_persist(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     GridBar bar{h->d_bar, h->d_bar + 1, h->d_err, (unsigned int)h->test_barrier_extra};
     void* args[] = {&d, &p, &ns_i, &par0, &nrow, &ncol, &bar};
     LaunchScope ls(h, s, std::string("persist") + prec_suffix(pr));
-    KS_CUDA(cudaLaunchCooperativeKernel((const void*)k_persist<R>, dim3(h->pgrid[pr]), dim3(128),
+    KS_CUDA(cudaLaunchCooperativeKernel((const void*)k_persist<R>, dim3(h->pgrid[pr]), dim3(COL_ACC_LANES),
                                         args, h->psmem[pr], s));
     ls.done();
     return KS_OK;
@@ -1019,7 +1019,7 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
         lr.smem = 2 * (size_t)h->rows_per_tile * h->d.nx * cs;
         lr.grid = 152 * 16;
         Launch& lc = h->lcol[pr];
-        lc.threads = 128;
+        lc.threads = COL_ACC_LANES;  // the column partials' accumulation width (ks_items.cuh)
         lc.smem = 2 * (size_t)h->nsmax * cs + COL_RED_DOUBLES * sizeof(double);
         lc.grid = 152 * 16;
     }
