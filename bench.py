@@ -471,7 +471,7 @@ def run_to_tol(args, w, dev):
     import numpy as np
     import torch
     from paper_2007_06427_gb300 import ks_loop as K
-    from paper_2007_06427_gb300.accel import descend_extrapolated
+    from paper_2007_06427_gb300.accel import descend_extrapolated, descend_extrapolated_mixed
     out = {}
     clk = ClockSampler(dev.index if dev.index is not None else 0)
     clk.start()
@@ -516,6 +516,24 @@ def run_to_tol(args, w, dev):
             "extrapolations": r.extrapolations, "rejected": r.rejected,
             "note": "App. C: from sqrt(J) = 1e-3, geometric extrapolation each time sqrt(J) halves"}
         h.close()
+        h32 = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP32, w.scheme, w.dtau)
+        h64 = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP64, w.scheme, w.dtau)
+        u = torch.from_numpy(w.packed()).to(dev, torch.float64)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = descend_extrapolated_mixed(h32, h64, u, float(w.T0[0]), tol=args.tol,
+                                       max_steps=args.to_tol_max_steps, chunk=1000)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        out["mixed_extrapolated"] = {
+            "seconds": el, "steps": [r.steps], "sqrtJ": [r.sqrtJ],
+            "status": [K.STATUS_NAMES.get(int(r.status), str(int(r.status)))], "T": [r.T],
+            "extrapolations": r.extrapolations, "rejected": r.rejected,
+            "switch_step": r.switch_step,
+            "note": "float bulk and double finish, both with the App. C extrapolation; "
+                    "sqrt(J) of the float state evaluated in double"}
+        h32.close()
+        h64.close()
     out["clocks"] = clk.stop()
     return out
 

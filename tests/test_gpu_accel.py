@@ -28,3 +28,26 @@ def test_extrapolation_converges_with_fewer_steps():
     for r in (plain, acc):
         a = r.u.cpu().numpy().reshape(ns, nx)
         assert np.abs(a - a.mean()).max() < 1e-6
+
+
+def test_mixed_extrapolation_converges():
+    """Float bulk and double finish, both extrapolated: converges below 1e-10 to the same class
+    of fixed point, with at least one kept extrapolation and a switch to double."""
+    from paper_2007_06427_gb300.accel import descend_extrapolated_mixed
+    L, nx, ns = 22.0, 32, 32
+    u0, T0, _ = spectral_loop(2, nx, L, ns=ns, T_range=(30.0, 50.0))
+    u0 = 1e-2 * u0
+    u = torch.tensor(u0.ravel(), device="cuda")
+    with K.KSLoop(L, nx, [ns], K.KS_FP32, K.KS_IMEX, 0.15) as h32, \
+            K.KSLoop(L, nx, [ns], K.KS_FP64, K.KS_IMEX, 0.15) as h64:
+        r = descend_extrapolated_mixed(h32, h64, u, T0, tol=1e-10, chunk=200)
+        plain = descend_extrapolated(h64, u, T0, tol=1e-10, start=0.0, chunk=200)
+    assert r.status == K.KS_CONVERGED and r.sqrtJ < 1e-10
+    assert r.switch_step is not None and r.extrapolations >= 1
+    assert r.steps < plain.steps
+    a = r.u.cpu().numpy().reshape(ns, nx)
+    assert np.abs(a - a.mean()).max() < 1e-6
+    # in the double phase the recorded sqrt(J) never increases from one kept state to the next
+    after = [s for st, s, ev in r.history if st >= r.switch_step and ev != "rejected"]
+    assert len(after) >= 2
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(after, after[1:]))
