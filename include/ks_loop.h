@@ -58,8 +58,10 @@ enum {
     KS_FP32 = 1,   /* every step in float; reductions finished in double; T in double */
     KS_MIXED = 2   /* ks_descend: float steps while sqrt(J), evaluated in double at every
                       read-back, exceeds switch_tol and keeps falling; then double steps to the
-                      end (the adjoint half of each in float unless "finish_f32_adjoint" is 0);
-                      other calls compute in double */
+                      end (the adjoint half of each in float unless "finish_f32_adjoint" is 0).
+                      A loop whose float rounding alone more than doubles sqrt(J) (one that
+                      starts below the float floor) takes double steps from the start.
+                      Other calls compute in double */
 };
 
 /* tau-integration scheme (Sec. 4.2) */

@@ -1270,13 +1270,20 @@ int final_eval(ks_loop* h, cudaStream_t s) {
 // sqrt(J) of the resident state of every loop evaluated in double (the band of float loops
 // widened first): the residual evaluation of a mixed descent stays in double.  Uses the API
 // workspace; the resident state is not touched.
-int monitor_f64(ks_loop* h, cudaStream_t s, std::vector<double>& out) {
+// double_band: evaluate the double band of every loop instead (the projected input right after
+// ks_set_state of a mixed handle, before any float step)
+int monitor_f64(ks_loop* h, cudaStream_t s, std::vector<double>& out, bool double_band = false) {
     Work& w = h->st;
     Work& a = h->api;
     const int B = h->d.B;
     dim3 g(8, B);
+    const int* sel_prec = w.prec;
+    if (double_band) {
+        KS_CUDA(cudaMemsetAsync(w.sel, 0, B * sizeof(int), s));  // precision 0 (double) for all
+        sel_prec = w.sel;
+    }
     k_band_merge<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (const cpx<double>*)w.uh[P64],
-                                   (cpx<double>*)a.uh[P64], h->d_boff, w.prec, B, h->d.nkx, h->d_ks);
+                                   (cpx<double>*)a.uh[P64], h->d_boff, sel_prec, B, h->d.nkx, h->d_ks);
     KS_CUDA(cudaGetLastError());
     KS_CUDA(cudaMemcpyAsync(a.T, w.T + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
     a.par = 0;
@@ -1394,6 +1401,24 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
     // from sqrt(J) evaluated in double, which keeps falling after the float value has reached
     // its noise floor
     const bool monitor = (h->mode == KS_MIXED);
+    if (monitor) {
+        // a loop whose float rounding alone already doubles sqrt(J) (it starts below the float
+        // floor, e.g. a nearly converged loop) descends in double from the start
+        std::vector<double> jf, jd;
+        KS_TRY(monitor_f64(h, s, jf));
+        KS_TRY(monitor_f64(h, s, jd, true));
+        bool any = false;
+        for (int b = 0; b < B; ++b)
+            if (jf[b] > 2.0 * jd[b]) {
+                h->h_prec[b] = P64;
+                any = true;
+            }
+        if (any) {
+            KS_CUDA(cudaMemcpyAsync(h->st.prec, h->h_prec.data(), B * sizeof(int),
+                                    cudaMemcpyHostToDevice, s));
+            h->st.mix_valid[P64] = false;
+        }
+    }
     long long done = 0;
     while (done < cap) {
         const long long c = std::min<long long>(h->chunk, cap - done);

@@ -293,3 +293,25 @@ def test_cluster_kernel_equals_phase_launches(mode, nx, nss, C):
         outs.append((u.cpu(), T.cpu(), steps.cpu(), sq.cpu()))
     for a, b in zip(outs[0], outs[1]):
         assert torch.equal(a, b)
+
+
+def test_mixed_descent_starts_below_float_floor_in_double():
+    """A loop already far below the float floor (a nontrivial KS equilibrium reached by a
+    centre-symmetric run at L = 22, repeated over s): a mixed descent must not first raise its
+    sqrt(J) to the float floor; it descends in double from the first chunk."""
+    from paper_2007_06427_gb300.guesses import chaotic_run
+    L, nx, ns = 22.0, 32, 32
+    _, us = chaotic_run(L, nx, 1500.0, seed=0, symmetric=True)
+    loop = np.repeat(us[-1][None, :], ns, axis=0)
+    u = torch.tensor(loop.ravel(), device="cuda")
+    T = torch.tensor([11.0], dtype=torch.float64, device="cuda")
+    J0 = torch.empty(1, dtype=torch.float64, device="cuda")
+    sq = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with K.KSLoop(L, nx, [ns], K.KS_MIXED, K.KS_IMEX, 0.15, chunk=2000) as h:
+        K.ks_residual(h.handle, u, T, None, J0)
+        K.ks_descend(h.handle, u, T, 20000, 1e-11, None, sq, None)
+        hs, hq, hp = K.ks_get_history(h.handle, 0)
+    assert np.sqrt(np.mean(loop ** 2)) > 0.5                 # nontrivial state
+    assert np.sqrt(J0.item()) < 1e-6
+    assert hp[0] == 0                                       # double from the first chunk
+    assert sq.item() <= np.sqrt(J0.item())

@@ -73,3 +73,18 @@ def test_symmetric_run_and_loops_stay_centre_symmetric():
         # the oracle's Xi projection leaves it unchanged
         np.testing.assert_allclose(ko.band_state(lp.u, L, xi=True), ko.band_state(lp.u, L),
                                    rtol=0, atol=1e-13 * np.abs(lp.u).max())
+
+
+def test_orbit_classification_closed_forms():
+    """u = 0 is trivial, u = a sin(q x) is steady, u = a sin(q x + 2 pi s) has
+    ||u_s|| / ||u|| = 2 pi (omega = 2 pi for the first temporal mode)."""
+    from paper_2007_06427_gb300.orbits import classify
+    L, nx, ns = 39.0, 32, 32
+    x = L * np.arange(nx)[None, :] / nx
+    s = np.arange(ns)[:, None] / ns
+    q = 2 * math.pi * 2 / L
+    assert classify(np.zeros((ns, nx)), L)[0] == "trivial"
+    kind, norm, ratio = classify(0.7 * np.sin(q * x) + 0 * s, L)
+    assert kind == "steady" and ratio < 1e-14 and norm == pytest.approx(0.7 * math.sqrt(L / 2))
+    kind, norm, ratio = classify(0.7 * np.sin(q * x + 2 * math.pi * s), L)
+    assert kind == "periodic" and ratio == pytest.approx(2 * math.pi, rel=1e-12)
