@@ -209,10 +209,11 @@ print(json.dumps({{"steps": steps, "seconds": el, "gridpoint_steps": gp}}))
 """
 
 
-def run_cpu_oracle(workload_name: str, budget_s: float = 0.0, max_steps: int = 0):
+def run_cpu_oracle(workload_name: str, budget_s: float = 0.0, max_steps: int = 0,
+                   threads: int = 1):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
+        env[v] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
     code = CPU_SNIPPET.format(root=ROOT, wl=workload_name, mode="fp64", budget=budget_s,
                               max_steps=max_steps)
@@ -282,6 +283,11 @@ def ours_arm(args):
                    "kind": "oracle",
                    "sample": f"{r['steps']} oracle tau-steps of {args.workload} "
                              f"({r['seconds']:.1f} s, NumPy FP64 dense DFTs, 1 BLAS thread)"}
+            nc = os.cpu_count() or 1
+            if nc > 1:
+                ra = run_cpu_oracle(args.workload, args.cpu_seconds / 2, 0, threads=nc)
+                cpu["all_cores"] = {"value": ra["gridpoint_steps"] / ra["seconds"], "cores": nc,
+                                    "sample": f"{ra['steps']} oracle tau-steps, {nc} BLAS threads"}
         except Exception as e:  # keep the GPU line even if the host leg fails
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {str(e)[-200:]}"}
@@ -415,6 +421,12 @@ def ours_arm(args):
             "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()},
         }
         if to_tol:
+            if cpu and cpu.get("value"):
+                # the oracle at the measured per-step rate for the same step counts (FP64 runs)
+                for key in ("fp64", "fp64_extrapolated"):
+                    if key in to_tol:
+                        n = sum(to_tol[key]["steps"]) if w.batch == 1 else to_tol[key]["steps"][0]
+                        to_tol[key]["cpu_oracle_seconds_extrapolated"] = n * w.gridpoints / cpu["value"]
             line["time_to_tol"] = to_tol
         if fp32:
             line["fp32"] = fp32
