@@ -1,0 +1,80 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration the benchmark times
+(one ks_step call per tau-step on the resident state, default launch path), checked on sampled
+loops the oracle can follow one by one: FP64 at 1e-12 relative, FP32 at 1e-5 (the oracle is
+given the float-rounded input, as in the other parity tests)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ks_oracle as ko
+from paper_2007_06427_gb300 import ks_loop as K
+from paper_2007_06427_gb300.inputs import workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {K.KS_FP64: 1e-12, K.KS_FP32: 1e-5}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_steps(w, mode, nsteps):
+    """nsteps single-step calls on the resident state; returns (u per loop, T, path used)."""
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    us = [a.astype(np.float32).astype(np.float64) for a in w.u] if mode == K.KS_FP32 else w.u
+    u = torch.from_numpy(np.concatenate([a.ravel() for a in us])).to("cuda", dt)
+    T = torch.tensor(w.T0, dtype=torch.float64, device="cuda")
+    with K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau) as h:
+        K.ks_set_state(h.handle, u, T)
+        K.ks_profile(h.handle, True)
+        for _ in range(nsteps):
+            K.ks_step(h.handle, 1, 0.0)
+        K.ks_get_state(h.handle, u, T)
+        torch.cuda.synchronize()
+        prof, _ = K.ks_profile_read(h.handle)
+    flat = u.double().cpu().numpy()
+    out, o = [], 0
+    for n in w.ns:
+        out.append(flat[o:o + n * w.nx].reshape(n, w.nx))
+        o += n * w.nx
+    return us, out, T.cpu().numpy(), set(prof)
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+def test_bench_workload_single_64x128(mode):
+    w = workload("single_64x128_imex")
+    us, out, T, kinds = run_steps(w, mode, 3)
+    assert any(k.startswith("cluster") for k in kinds), kinds      # the benchmark's launch form
+    d = ko.descend(us[0], w.T0[0], w.L, w.dtau, w.scheme, 3)
+    assert rel(out[0], d["u"]) < TOL[mode]
+    assert abs(T[0] - d["T"]) < TOL[mode] * d["T"]
+
+
+def test_ragged256_sampled_fp64():
+    w = workload("ragged256_64xNs")
+    us, out, T, kinds = run_steps(w, K.KS_FP64, 2)
+    for b in (0, 1, 97, 255):
+        d = ko.descend(us[b], w.T0[b], w.L, w.dtau, w.scheme, 2)
+        assert rel(out[b], d["u"]) < 1e-12, b
+        assert abs(T[b] - d["T"]) < 1e-12 * d["T"]
+
+
+def test_batch16_sampled_fp32():
+    w = workload("batch16_64x64")
+    us, out, T, kinds = run_steps(w, K.KS_FP32, 3)
+    assert any(k.startswith("cluster") for k in kinds), kinds
+    for b in (0, 7, 15):
+        d = ko.descend(us[b], w.T0[b], w.L, w.dtau, w.scheme, 3)
+        assert rel(out[b], d["u"]) < 1e-5, b
+
+
+def test_large8_256x1024_sampled_fp32():
+    """The large-domain workload (8 loops of 256 x 1024, L = 100): one step of the whole batch,
+    loop 3 followed by the oracle."""
+    w = workload("large8_256x1024")
+    us, out, T, kinds = run_steps(w, K.KS_FP32, 1)
+    d = ko.descend(us[3], w.T0[3], w.L, w.dtau, w.scheme, 1)
+    assert rel(out[3], d["u"]) < 1e-5
+    assert abs(T[3] - d["T"]) < 1e-5 * d["T"]
