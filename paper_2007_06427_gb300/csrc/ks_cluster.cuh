@@ -33,6 +33,7 @@ struct ClusterPlan {
     int nkmax;    // max 2 Ks + 1
     int rmax;     // max rows per rank
     int off_M, off_uh, off_rh, off_U, off_scr, off_part, off_red, off_tw, off_rin, off_tw_a;
+    int off_tab;  // per-x-mode tables q_j, q_j^2 - q_j^4, q_j^4 (q_j^2 - 1)^2 (and the second in RA)
     int bytes;
     int u_global;  // 1: the rank's grid rows of u live in global memory (U array), not SMEM
 };
@@ -133,6 +134,17 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
     cpx<RA>* tws_a = kSame ? reinterpret_cast<cpx<RA>*>(tws) : reinterpret_cast<cpx<RA>*>(smem + cp.off_tw_a);
     const R h = (R)d.hx;
     const RA h_a = (RA)d.hx;
+    // the per-x-mode tables, read in every phase, live in shared memory
+    R* const s_qv = reinterpret_cast<R*>(smem + cp.off_tab);
+    R* const s_lin = s_qv + nkx;
+    R* const s_cq = s_lin + nkx;
+    RA* const s_lina = reinterpret_cast<RA*>(s_cq + nkx);
+    for (int i = tid; i < nkx; i += nt) {
+        s_qv[i] = p.qv[i];
+        s_lin[i] = p.lin[i];
+        s_cq[i] = p.cq[i];
+        s_lina[i] = ta.lin[i];
+    }
 
     // no barrier after the table copies: the twiddles are first read after the barrier that
     // closes the state load below, so the copies overlap the per-loop loads
@@ -243,8 +255,8 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                 for (int i = tid; i < nr * nx; i += nt) {
                     const int J = i >> lgnr, r = i & (nr - 1);
                     cpx<R> z = mk<R>(0, 0);
-                    if (J <= kx) z = scale(Rin[(size_t)J * rmax + t0 + r], (R)1 - p.qv[J]);
-                    else if (J >= nx - kx) z = scale(conj(Rin[(size_t)(nx - J) * rmax + t0 + r]), (R)1 + p.qv[nx - J]);
+                    if (J <= kx) z = scale(Rin[(size_t)J * rmax + t0 + r], (R)1 - s_qv[J]);
+                    else if (J >= nx - kx) z = scale(conj(Rin[(size_t)(nx - J) * rmax + t0 + r]), (R)1 + s_qv[nx - J]);
                     A[(size_t)r * nx + J] = z;
                 }
                 __syncthreads();
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                                 const int j = rank + q * C;
                                 cpx<R> x = mk<R>(0, 0);
                                 if (k >= -ks && k <= ks) {
-                                    const R a_lin = p.lin[j], rq = p.qv[j];
+                                    const R a_lin = s_lin[j], rq = s_qv[j];
                                     const cpx<R> ph = scale(Mloc[(q << lg) + n], ins);
                                     const cpx<R> u = uhl[q * nk + k + ks];
                                     const R bk = -(R)k * wTr;
@@ -384,18 +396,22 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                     const double J = sJ * d.L;
                     const double L2 = sL * d.L * (wT * wT) * kInv2Pi;  // (L / T^2) 2 pi sum
                     const double Tn = T - d.dtau * L2;    // explicit Euler for T (Sec. 4.2)
+                    // the freeze decision is taken here once, so the other threads compare ints
+                    int sv = ST_RUNNING;
+                    if (!(J == J) || J > 1e300 || !(T > 0.0)) sv = ST_DIVERGED;
+                    else if (J < p.tol * p.tol) sv = ST_CONVERGED;
+                    else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) sv = ST_SWITCH;
                     red[0] = J;
                     red[1] = Tn;
                     red[2] = 2.0 * 3.14159265358979323846 / Tn;
+                    reinterpret_cast<int*>(red + 3)[0] = sv;
                 }
             }
             __syncthreads();
             const double J = red[0], Tnext = red[1], wTnext = red[2];
+            st = reinterpret_cast<const int*>(red + 3)[0];
             __syncthreads();
             Jlast = J;
-            if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
-            else if (J < p.tol * p.tol) st = ST_CONVERGED;
-            else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
             if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
             if (ncol > 0) {
                 col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                 // G_hat = (a + i omega/T) r_hat + F[P(u r_x)], in the adjoint precision
                 auto g_hat = [&](int i, int q, int k) {
                     const cpx<RA> wh = scale(Mloc_a[i], ins_a);
-                    const RA a_lin = ta.lin[rank + q * C];
+                    const RA a_lin = s_lina[rank + q * C];
                     const cpx<R> rr = rhl[q * nk + k + ks];
                     const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
                     const RA bk = (RA)k * wTa;
@@ -440,7 +456,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                         R f = dt;
                         if (d.scheme == 1) {
                             const R kk2 = (R)k * (R)k;
-                            f = dt / ((R)1 + dt * (kk2 * wT2 + p.cq[j]));
+                            f = dt / ((R)1 + dt * (kk2 * wT2 + s_cq[j]));
                         }
                         cpx<R> u = uhl[q * nk + k + ks];
                         u = u - scale(G, f);

@@ -378,6 +378,16 @@ __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cn
 }
 #endif
 
+// First xor distance of the reduction over the per-warp sums held by lanes 0..nw-1 of warp 0
+// (the other lanes hold zeros).  At a distance >= nw a lane below nw only meets lanes whose
+// values came from lanes >= nw, all zero, so starting below nw gives those lanes the same bits
+// in fewer shuffle rounds.
+KS_HD int warp0_start(int nw) {
+    int o = 16;
+    while (o > 1 && o >= nw) o >>= 1;
+    return o;
+}
+
 // Block-wide sum of two doubles per thread (warp shuffles, then one warp over the warp sums);
 // red has room for 2 * (warps + 1) doubles.  The result is valid in every thread after the call.
 KS_HD void block_sum2(double* red, double& s0, double& s1) {
@@ -397,7 +407,7 @@ KS_HD void block_sum2(double* red, double& s0, double& s1) {
     if (w == 0) {
         s0 = (l < nw) ? red[2 * l] : 0.0;
         s1 = (l < nw) ? red[2 * l + 1] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = warp0_start(nw); o > 0; o >>= 1) {
             s0 += __shfl_xor_sync(0xffffffffu, s0, o);
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         }
@@ -483,7 +493,7 @@ KS_HD void block_reduce(ColAcc<float>& a, double* redd) {
             L.hi = red[4 * l + 2];
             L.lo = red[4 * l + 3];
         }
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = warp0_start(nw); o > 0; o >>= 1) {
             ff bJ, bL;
             bJ.hi = __shfl_xor_sync(0xffffffffu, J.hi, o);
             bJ.lo = __shfl_xor_sync(0xffffffffu, J.lo, o);
@@ -528,7 +538,7 @@ KS_HD void block_reduce2(ColAcc<double>& a, ColAcc<double>& b, double* red) {
     if (w == 0) {
 #pragma unroll
         for (int t = 0; t < 4; ++t) v[t] = (l < nw) ? red[4 * l + t] : 0.0;
-        for (int o = 16; o > 0; o >>= 1)
+        for (int o = warp0_start(nw); o > 0; o >>= 1)
 #pragma unroll
             for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
         if (l == 0)
@@ -575,7 +585,7 @@ KS_HD void block_reduce2(ColAcc<float>& a, ColAcc<float>& b, double* redd) {
             v[t].hi = (l < nw) ? red[8 * l + 2 * t] : 0.f;
             v[t].lo = (l < nw) ? red[8 * l + 2 * t + 1] : 0.f;
         }
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = warp0_start(nw); o > 0; o >>= 1) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 ff y;

@@ -597,6 +597,8 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     off += al((size_t)nkx * cp.rmax * cs);
     cp.off_tw_a = (int)off;
     if (sizeof(RA) != sizeof(R)) off += al((size_t)NMAX * sizeof(cpx<RA>));
+    cp.off_tab = (int)off;
+    off += al((size_t)nkx * (3 * rs + sizeof(RA)));
     cp.bytes = (off <= (size_t)smem_limit) ? (int)off : 0;
     return cp;
 }
