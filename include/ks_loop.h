@@ -199,7 +199,7 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *   "cluster"        0 (default): cluster size chosen per precision; 1..16: force this size
  *                    (KS_ERR_ARG when no plan of that size fits the batch)
  *   "symmetry"       1: restrict the descent to loops invariant under Xi: (x, s) -> (-x, s),
- *                    u -> -u (the centre-symmetric subspace, Sec. 3).  Every later analysis of a
+ *                    u -> -u (the centre-symmetric subspace, Sec. 4.1).  Every later analysis of a
  *                    grid field (ks_residual, ks_adjoint_grad, ks_set_state, ks_descend) projects
  *                    it onto that subspace, ks_adjoint_grad returns the projected G, and every
  *                    update is taken along the projected G, so the band state stays exactly

@@ -38,7 +38,7 @@ Readings where the paper is silent (each also listed in the design notes):
 * IMEX: Lambda_jk uses T at the start of the step; u and T are both advanced from the same
   state l^n.
 * Names: ``G`` is +L^dag_1 r (the ascent direction); ``dJdT`` is dJ/dT = 2 L^dag_2.
-* Centre-symmetric subspace (Sec. 3, Eq. KS_loop_sym; Sec. 5): with ``xi=True`` the loop is
+* Centre-symmetric subspace (Sec. 4.1, Eq. KS_loop_sym; Sec. 4.4): with ``xi=True`` the loop is
   restricted to the fields invariant under Xi: (x, s) -> (-x, s), u -> -u.  The input is
   projected onto that subspace with the band, and the descent direction L^dag_1 r is
   projected at every step (the flow preserves the symmetry of an invariant loop, so the

@@ -211,7 +211,7 @@ struct Bufs {
     int xi;                 // 1: descent restricted to the Xi-invariant (centre-symmetric) subspace
 };
 
-// Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 3, the
+// Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 4.1, the
 // symmetry of Eq. KS_G).  An invariant loop has u_hat_{j,-k} = -conj(u_hat_{j,k}) in the
 // half spectrum, and a zero j = 0 column.  With a the value at (j, k) and m the value at
 // (j, -k), the projected value at (j, k) is (a - conj(m)) / 2.  Evaluated at (j, -k) with the

@@ -14,7 +14,7 @@ loop closes smoothly.  This module provides both halves:
   descent's band and resampling to Ns points in s.
 
 The paper takes its initial loops from a chaotic run within the subspace of centre-symmetric
-fields, u(-x) = -u(x) (Sec. 5); ``symmetric=True`` keeps the run there (an odd real field
+fields, u(-x) = -u(x) (Sec. 4.4); ``symmetric=True`` keeps the run there (an odd real field
 has purely imaginary Fourier coefficients, and the KSE preserves that, so the projection after
 each step only removes rounding).  Every later step of the extraction is linear and acts the
 same at x and -x, so the loops it returns are centre-symmetric as well.

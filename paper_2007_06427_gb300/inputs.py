@@ -15,7 +15,7 @@ Recipe (per loop b, generator ``numpy.random.default_rng(seed_b)``, draws in thi
 5. u(x_m, s_n) = sum_jk c_jk exp(2 pi i (m j / N_x + n k / N_s)), then u is scaled so that its
    grid rms is 1.
 
-Centre-symmetric loops (``symmetric=True``, the subspace the paper's orbits lie in, Sec. 5):
+Centre-symmetric loops (``symmetric=True``, the subspace the paper's orbits lie in, Sec. 4.4):
 same draws, then c_jk <- (c_jk - conj(c_{j,-k})) / 2 before step 5, which makes u odd in x,
 u(-x, s) = -u(x, s).
 
@@ -133,7 +133,7 @@ def workload(name: str, batch: Optional[int] = None) -> Workload:
                           meta={"tol": 1e-12})
     if name == "paper_L39_xi_64x64":
         # the same setting restricted to centre-symmetric loops, as the paper's initial loops
-        # and converged orbits are (Sec. 5); descended with the "symmetry" knob set to 1
+        # and converged orbits are (Sec. 4.4); descended with the "symmetry" knob set to 1
         b = 1 if batch is None else batch
         return make_loops(name, 64, 39.0, range(b), ns=64, T0=40.0, scheme=1, dtau=0.15,
                           meta={"tol": 1e-12, "symmetry": 1}, symmetric=True)

@@ -1,6 +1,6 @@
 """Periodic-orbit search at the paper's setting: chaotic run -> recurrence loops -> tau-descent.
 
-The pipeline of Sec. 4.3-5: a chaotic KS run in the centre-symmetric subspace, initial loops from
+The pipeline of Sec. 4.3-4.4: a chaotic KS run in the centre-symmetric subspace, initial loops from
 its close recurrences (``guesses.recurrence_loops``), and the descent of all of them together as
 one batch on the GPU (mixed precision: float bulk, double finish) with the ``symmetry`` knob set,
 so every loop stays in the subspace as the paper's do.  Each converged loop is classified by

@@ -1,12 +1,12 @@
 """GPU: the descent restricted to the centre-symmetric subspace (the "symmetry" knob).
 
 A loop is Xi-invariant when u(-x, s) = -u(x, s) (Eq. KS_loop_sym); the paper's initial loops and
-orbits all are (Sec. 5).  With the knob set, every analysis of a grid field and every descent
+orbits all are (Sec. 4.4).  With the knob set, every analysis of a grid field and every descent
 direction is projected onto that subspace.  Checked here against the oracle's xi=True
 evaluation (FP64 1e-12, FP32 1e-5 relative), bit-exact invariance of the band state
 (u_hat[j][-k] = -conj(u_hat[j][k]), zero j = 0 column) on all three launch paths and in mixed
 precision, bit-identical results across the paths, and that without the knob the flow keeps an
-invariant loop invariant up to rounding (Sec. 3).
+invariant loop invariant up to rounding (Sec. 4.1).
 """
 import numpy as np
 import pytest
@@ -203,7 +203,7 @@ def test_mixed_descent_stays_invariant(f32_adjoint):
 
 
 def test_flow_preserves_symmetry_without_projection():
-    """Without the knob an invariant loop stays invariant up to rounding (Sec. 3): after 300
+    """Without the knob an invariant loop stays invariant up to rounding (Sec. 4.1): after 300
     IMEX steps the non-invariant part of the band is at the rounding level."""
     L, nx, nss = 22.0, 64, [64]
     us, Ts = make(nx, nss, L)

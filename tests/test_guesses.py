@@ -57,7 +57,7 @@ def _reflect(u):
 
 
 def test_symmetric_run_and_loops_stay_centre_symmetric():
-    """In the centre-symmetric subspace (Sec. 5) the run stays odd in x and chaotic, and the
+    """In the centre-symmetric subspace (Sec. 4.4) the run stays odd in x and chaotic, and the
     extracted loops are odd in x as well (L = 39, the paper's domain)."""
     L, nx, ns = 39.0, 64, 64
     ts, us = chaotic_run(L, nx, 1500.0, seed=2, symmetric=True)

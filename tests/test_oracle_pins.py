@@ -4,7 +4,7 @@ Every check here is fixed by the paper's equations or by mathematics derived by 
 closed forms for a single Fourier mode (Eq. KS_R, Eq. cost_function, Eq. KS_L_dagger),
 equilibria with zero residual (Sec. 4.1), Parseval, the adjoint identity that defines
 L^dag (Eq. adjoint_definition, App. B), centred finite differences of J, the expanded flow of
-Eq. KS_G_1, the shift and centre symmetries (Sec. 3, Eq. KS_loop_sym), monotone decrease of J
+Eq. KS_G_1, the shift symmetries (Sec. 3) and the centre symmetry (Sec. 4.1, Eq. KS_loop_sym), monotone decrease of J
 (Eq. J_variation) and the linear decay factors of the Euler schemes (Sec. 4.2).
 """
 import math
@@ -231,7 +231,7 @@ def test_xi_projection_closed_forms():
 
 def test_xi_descent_equals_plain_descent_on_invariant_loop():
     """On a Xi-invariant loop the projected descent follows the unprojected one (the flow
-    preserves the symmetry, Sec. 3): they differ by rounding only."""
+    preserves the symmetry, Sec. 4.1): they differ by rounding only."""
     u, T, _ = spectral_loop(4, 32, 22.0, ns=32, T0=40.0, symmetric=True)
     a = ko.descend(u, T, 22.0, 0.15, ko.IMEX, 8)
     b = ko.descend(u, T, 22.0, 0.15, ko.IMEX, 8, xi=True)
