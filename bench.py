@@ -502,11 +502,10 @@ def throughput_fp32(args, w, dev, flush, K):
 
 def run_to_tol(args, w, dev):
     """Plain FP64 descent vs FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol;
-    then the FP64 descent with the extrapolation of App. C (loop 0), for the step count."""
+    then both again with the extrapolation of App. C inside ks_descend."""
     import numpy as np
     import torch
     from paper_2007_06427_gb300 import ks_loop as K
-    from paper_2007_06427_gb300.accel import descend_extrapolated, descend_extrapolated_mixed
     out = {}
     clk = ClockSampler(dev.index if dev.index is not None else 0)
     clk.start()
@@ -536,39 +535,35 @@ def run_to_tol(args, w, dev):
                      "loop0_switch_step": switch,
                      "loop0_history": [[int(a), float(c)] for a, c in zip(hs[::max(1, len(hs) // 40)], hq[::max(1, len(hq) // 40)])]}
         h.close()
-    if w.batch == 1:
-        h = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP64, w.scheme, w.dtau)
+    # the same two descents with the extrapolation of App. C inside ks_descend
+    # (the extrapolated mixed run switches to double at sqrt(J) = 1e-5, about the float floor of
+    # this loop: the jumps of the extrapolation restart the stall window the plain run waits on)
+    for name, mode in (("fp64_extrapolated", K.KS_FP64), ("mixed_extrapolated", K.KS_MIXED)):
+        sw = max(args.switch_tol, 1e-5) if mode == K.KS_MIXED else 0.0
+        h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, tol=args.tol,
+                     switch_tol=sw, max_steps=args.to_tol_max_steps, chunk=1000)
+        K.ks_set_option(h.handle, "extrapolate", 1)
         u = torch.from_numpy(w.packed()).to(dev, torch.float64)
+        T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
+        steps = torch.zeros(w.batch, dtype=torch.int64, device=dev)
+        sq = torch.zeros(w.batch, dtype=torch.float64, device=dev)
+        st = torch.zeros(w.batch, dtype=torch.int32, device=dev)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        r = descend_extrapolated(h, u, float(w.T0[0]), tol=args.tol,
-                                 max_steps=args.to_tol_max_steps, chunk=1000)
+        K.ks_descend(h.handle, u, T, args.to_tol_max_steps, args.tol, steps, sq, st)
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
-        out["fp64_extrapolated"] = {
-            "seconds": el, "steps": [r.steps], "sqrtJ": [r.sqrtJ],
-            "status": [K.STATUS_NAMES.get(int(r.status), str(int(r.status)))], "T": [r.T],
-            "extrapolations": r.extrapolations, "rejected": r.rejected,
-            "note": "App. C: from sqrt(J) = 1e-3, geometric extrapolation each time sqrt(J) halves"}
+        hs, hq, hp = K.ks_get_history(h.handle, 0)
+        switch = int(hs[np.nonzero(hp == 0)[0][0]]) if (mode == K.KS_MIXED and (hp == 0).any()) else None
+        out[name] = {"seconds": el, "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8],
+                     "status": [K.STATUS_NAMES.get(int(v), str(int(v))) for v in st.tolist()[:8]],
+                     "T": T.tolist()[:8],
+                     "extrapolations": K.ks_get_option(h.handle, "extrapolations"),
+                     "rejected": K.ks_get_option(h.handle, "extrapolations_rejected"),
+                     "loop0_switch_step": switch, "switch_tol": sw,
+                     "note": "App. C inside ks_descend: from sqrt(J) = 1e-3, geometric extrapolation "
+                             "each time sqrt(J) (evaluated in double every 1000 steps) halves"}
         h.close()
-        h32 = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP32, w.scheme, w.dtau)
-        h64 = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP64, w.scheme, w.dtau)
-        u = torch.from_numpy(w.packed()).to(dev, torch.float64)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        r = descend_extrapolated_mixed(h32, h64, u, float(w.T0[0]), tol=args.tol,
-                                       max_steps=args.to_tol_max_steps, chunk=1000)
-        torch.cuda.synchronize(dev)
-        el = time.perf_counter() - t0
-        out["mixed_extrapolated"] = {
-            "seconds": el, "steps": [r.steps], "sqrtJ": [r.sqrtJ],
-            "status": [K.STATUS_NAMES.get(int(r.status), str(int(r.status)))], "T": [r.T],
-            "extrapolations": r.extrapolations, "rejected": r.rejected,
-            "switch_step": r.switch_step,
-            "note": "float bulk and double finish, both with the App. C extrapolation; "
-                    "sqrt(J) of the float state evaluated in double"}
-        h32.close()
-        h64.close()
     out["clocks"] = clk.stop()
     return out
 

@@ -273,6 +273,14 @@ struct ks_loop {
     int cgrid[3] = {0, 0, 0};
     int finish_f32_adjoint = 1;     // mixed descents: finishing steps form the adjoint in float
     int xi = 0;                     // 1: loads, gradients and updates projected onto the Xi subspace
+    // ks_descend with the extrapolation of App. C (knob "extrapolate")
+    int extrapolate = 0;
+    double* anc = nullptr;          // [nband] complex double: each loop's anchor band
+    double* cand = nullptr;         // [nband] complex double: the current bands, widened
+    double* coef = nullptr;         // [B] extrapolation coefficient of each loop (0: none)
+    int* esel = nullptr;            // [3][B] selections: new anchor, accepted, rejected
+    std::vector<double> anc_sq, anc_T;  // sqrt(J) and T at each anchor (sqrt(J) < 0: no anchor)
+    long long n_extrap = 0, n_extrap_rejected = 0;
     int test_barrier_extra = 0;     // test hook: the grid barrier waits for arrivals that never come
     // persistent kernel
     bool persistent = true;
@@ -1125,6 +1133,51 @@ __global__ void k_band_merge(const cpx<float>* s32, const cpx<double>* s64, cpx<
     }
 }
 
+// dst[b] = src[b] (double bands) for the loops with sel[b]
+__global__ void k_band_copy_sel(const cpx<double>* src, cpx<double>* dst, const long long* boff,
+                                const int* sel, int B, int nkx, const int* ks) {
+    const int b = blockIdx.y;
+    if (b >= B || !sel[b]) return;
+    const long long n = (long long)nkx * (2 * ks[b] + 1);
+    const long long o = boff[b];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[o + i] = src[o + i];
+}
+
+// out[b] = cur[b] + (cur[b] - anc[b]) c_b for every loop (c_b = 0: out[b] = cur[b])
+__global__ void k_band_extrap(const cpx<double>* cur, const cpx<double>* anc, const double* coef,
+                              cpx<double>* out, const long long* boff, int B, int nkx,
+                              const int* ks) {
+    const int b = blockIdx.y;
+    if (b >= B) return;
+    const long long n = (long long)nkx * (2 * ks[b] + 1);
+    const long long o = boff[b];
+    const double c = coef[b];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cpx<double> v = cur[o + i];
+        out[o + i] = (c == 0.0) ? v : v + scale(v - anc[o + i], c);
+    }
+}
+
+// the double band src becomes the resident band of each selected loop, in the loop's precision
+__global__ void k_band_store_sel(const cpx<double>* src, cpx<double>* s64, cpx<float>* s32,
+                                 const long long* boff, const int* prec, const int* sel, int B,
+                                 int nkx, const int* ks) {
+    const int b = blockIdx.y;
+    if (b >= B || !sel[b]) return;
+    const long long n = (long long)nkx * (2 * ks[b] + 1);
+    const long long o = boff[b];
+    const bool f = prec[b] == 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cpx<double> v = src[o + i];
+        if (f) s32[o + i] = mk<float>((float)v.x, (float)v.y);
+        else s64[o + i] = v;
+    }
+}
+
 namespace {
 
 int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
@@ -1153,6 +1206,9 @@ int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
     h->hist_steps.assign(B, {});
     h->hist_sqrtJ.assign(B, {});
     h->hist_prec.assign(B, {});
+    h->anc_sq.assign(B, -1.0);
+    h->anc_T.assign(B, 0.0);
+    h->n_extrap = h->n_extrap_rejected = 0;
     return KS_OK;
 }
 
@@ -1299,6 +1355,125 @@ int monitor_f64(ks_loop* h, cudaStream_t s, std::vector<double>& out, bool doubl
     return KS_OK;
 }
 
+// One extrapolation round of App. C over the running loops, from sqrt(J) of the current states
+// (val, evaluated in double).  A loop below extrap_start without an anchor takes its current
+// state as the anchor; a loop whose sqrt(J) has fallen to half its anchor's is extrapolated
+// geometrically, l* ~ l + (l - l_a) rho / (1 - rho), rho = sqrt(J) / sqrt(J_a), on the band and
+// T.  The candidate is kept only if its sqrt(J), evaluated in double, is lower; either way the
+// loop's anchor moves to the state it continues from.  touched[b] marks the loops handled.
+constexpr double kExtrapStart = 1e-3, kExtrapDrop = 0.5;
+
+int extrapolate_round(ks_loop* h, cudaStream_t s, const std::vector<double>& val,
+                      std::vector<char>& touched) {
+    Work& w = h->st;
+    Work& a = h->api;
+    const int B = h->d.B;
+    const long long nb = h->nband;
+    if (!h->anc) {
+        void* p = nullptr;
+        KS_TRY(dev_alloc(h, &p, nb * sizeof(cpx<double>)));
+        h->anc = (double*)p;
+        KS_TRY(dev_alloc(h, &p, nb * sizeof(cpx<double>)));
+        h->cand = (double*)p;
+        KS_TRY(dev_alloc(h, &p, B * sizeof(double)));
+        h->coef = (double*)p;
+        KS_TRY(dev_alloc(h, &p, 3 * B * sizeof(int)));
+        h->esel = (int*)p;
+    }
+    std::vector<double> Tcur(B), wTcur(B);
+    KS_CUDA(cudaMemcpyAsync(Tcur.data(), w.T + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(wTcur.data(), w.wT + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    dim3 g(8, B);
+    k_band_merge<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (const cpx<double>*)w.uh[P64],
+                                   (cpx<double>*)h->cand, h->d_boff, w.prec, B, h->d.nkx, h->d_ks);
+    KS_CUDA(cudaGetLastError());
+    KS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> selA(B, 0), selAcc(B, 0), selRej(B, 0);
+    std::vector<double> c(B, 0.0), Tc(Tcur);
+    bool anyA = false, anyC = false;
+    for (int b = 0; b < B; ++b) {
+        if (h->h_status[b] != KS_RUNNING || !(val[b] <= kExtrapStart)) continue;
+        if (h->anc_sq[b] < 0.0) {
+            selA[b] = 1;
+            h->anc_sq[b] = val[b];
+            h->anc_T[b] = Tcur[b];
+            anyA = true;
+            continue;
+        }
+        if (val[b] > kExtrapDrop * h->anc_sq[b]) continue;
+        const double rho = val[b] / h->anc_sq[b];
+        c[b] = rho / (1.0 - rho);
+        Tc[b] = Tcur[b] + (Tcur[b] - h->anc_T[b]) * c[b];
+        anyC = true;
+    }
+    if (anyA) {
+        KS_CUDA(cudaMemcpyAsync(h->esel, selA.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_band_copy_sel<<<g, 256, 0, s>>>((const cpx<double>*)h->cand, (cpx<double>*)h->anc,
+                                          h->d_boff, h->esel, B, h->d.nkx, h->d_ks);
+        KS_CUDA(cudaGetLastError());
+    }
+    if (!anyC) {
+        KS_CUDA(cudaStreamSynchronize(s));
+        return KS_OK;
+    }
+    // candidates into the API workspace, their sqrt(J) in double
+    KS_CUDA(cudaMemcpyAsync(h->coef, c.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_band_extrap<<<g, 256, 0, s>>>((const cpx<double>*)h->cand, (const cpx<double>*)h->anc,
+                                    h->coef, (cpx<double>*)a.uh[P64], h->d_boff, B, h->d.nkx,
+                                    h->d_ks);
+    KS_CUDA(cudaGetLastError());
+    KS_CUDA(cudaMemcpyAsync(a.T, Tc.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    a.par = 0;
+    k_prep_wT<<<(B + 127) / 128, 128, 0, s>>>(a.T, a.wT, B);
+    KS_CUDA(cudaGetLastError());
+    KS_TRY(run_residual<double>(h, a, P64, s));
+    KS_TRY(run_finalize(h, a, a.T, P64, 0, s));
+    std::vector<double> sqe(B);
+    KS_CUDA(cudaMemcpyAsync(sqe.data(), a.sqrtJ, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    bool anyAcc = false, anyRej = false;
+    for (int b = 0; b < B; ++b) {
+        if (c[b] == 0.0) continue;
+        touched[b] = 1;
+        if (sqe[b] == sqe[b] && sqe[b] < val[b]) {
+            selAcc[b] = 1;
+            anyAcc = true;
+            h->anc_sq[b] = sqe[b];
+            h->anc_T[b] = Tc[b];
+            Tcur[b] = Tc[b];
+            wTcur[b] = 2.0 * 3.14159265358979323846 / Tc[b];
+            ++h->n_extrap;
+        } else {
+            selRej[b] = 1;
+            anyRej = true;
+            h->anc_sq[b] = val[b];
+            h->anc_T[b] = Tcur[b];
+            ++h->n_extrap_rejected;
+        }
+    }
+    if (anyAcc) {
+        KS_CUDA(cudaMemcpyAsync(h->esel + B, selAcc.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_band_store_sel<<<g, 256, 0, s>>>((const cpx<double>*)a.uh[P64], (cpx<double>*)w.uh[P64],
+                                           (cpx<float>*)w.uh[P32], h->d_boff, w.prec, h->esel + B,
+                                           B, h->d.nkx, h->d_ks);
+        KS_CUDA(cudaGetLastError());
+        k_band_copy_sel<<<g, 256, 0, s>>>((const cpx<double>*)a.uh[P64], (cpx<double>*)h->anc,
+                                          h->d_boff, h->esel + B, B, h->d.nkx, h->d_ks);
+        KS_CUDA(cudaGetLastError());
+        KS_CUDA(cudaMemcpyAsync(w.T + (size_t)w.par * B, Tcur.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+        KS_CUDA(cudaMemcpyAsync(w.wT + (size_t)w.par * B, wTcur.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+        w.mix_valid[P64] = w.mix_valid[P32] = false;  // the mixed values derive from the band
+    }
+    if (anyRej) {
+        KS_CUDA(cudaMemcpyAsync(h->esel + 2 * B, selRej.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_band_copy_sel<<<g, 256, 0, s>>>((const cpx<double>*)h->cand, (cpx<double>*)h->anc,
+                                          h->d_boff, h->esel + 2 * B, B, h->d.nkx, h->d_ks);
+        KS_CUDA(cudaGetLastError());
+    }
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
 // write the resident state to u (grid) in the handle's I/O precision
 int get_state_impl(ks_loop* h, void* u, double* T, cudaStream_t s) {
     Work& w = h->st;
@@ -1427,10 +1602,10 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
         KS_TRY(steps_impl(h, c, tl, s, !monitor));
         done += c;
         KS_TRY(readback(h, s));
-        if (monitor) KS_TRY(monitor_f64(h, s, mon));
+        if (monitor || h->extrapolate) KS_TRY(monitor_f64(h, s, mon));
         std::vector<double> val(B);
         for (int b = 0; b < B; ++b)
-            val[b] = (monitor && h->h_prec[b] == P32) ? mon[b] : h->h_sqrtJ[b];
+            val[b] = ((monitor && h->h_prec[b] == P32) || h->extrapolate) ? mon[b] : h->h_sqrtJ[b];
         for (int b = 0; b < B; ++b) {
             if (!h->hist_steps[b].empty() && h->hist_steps[b].back() == h->h_steps[b]) continue;
             h->hist_steps[b].push_back(h->h_steps[b]);
@@ -1493,6 +1668,12 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
                 }
         }
         if (status_dirty) KS_TRY(set_status(h, s));
+        if (h->extrapolate && any_live) {
+            std::vector<char> touched(B, 0);
+            KS_TRY(extrapolate_round(h, s, val, touched));
+            for (int b = 0; b < B; ++b)
+                if (touched[b]) win_val[b] = -1.0;  // sqrt(J) moved by a jump: restart the window
+        }
         if (!any_live) break;
     }
     // final residual at the resident state (in double for every loop of a mixed descent),
@@ -1576,6 +1757,8 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         h->test_barrier_extra = value ? 1 : 0;
     } else if (k == "finish_f32_adjoint") {
         h->finish_f32_adjoint = value != 0;
+    } else if (k == "extrapolate") {
+        h->extrapolate = value ? 1 : 0;
     } else if (k == "symmetry") {
         if (value < 0 || value > 1) return fail(KS_ERR_ARG, "symmetry must be 0 (none) or 1 (Xi)");
         h->xi = (int)value;
@@ -1611,6 +1794,9 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "stall_window") *value = h->stall_window;
     else if (k == "chunk") *value = h->chunk;
     else if (k == "symmetry") *value = h->xi;
+    else if (k == "extrapolate") *value = h->extrapolate;
+    else if (k == "extrapolations") *value = h->n_extrap;
+    else if (k == "extrapolations_rejected") *value = h->n_extrap_rejected;
     else return fail(KS_ERR_ARG, "unknown option " + k);
     return KS_OK;
 }

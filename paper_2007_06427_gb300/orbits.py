@@ -57,10 +57,11 @@ def classify(u: np.ndarray, L: float, trivial: float = 1e-6, steady: float = 1e-
 
 def descend_guesses(guesses: List[Guess], L: float, dtau: float = 0.15, tol: float = 1e-10,
                     max_steps: int = 2_000_000, symmetric: bool = True, mode: str = "mixed",
-                    chunk: int = 5000, device: str = "cuda", states: Optional[list] = None
-                    ) -> List[OrbitResult]:
-    """Descend all guesses as one batch; returns one result per guess (and appends the final
-    loops u[n, m] to ``states`` when given)."""
+                    chunk: int = 5000, device: str = "cuda", states: Optional[list] = None,
+                    extrapolate: bool = True) -> List[OrbitResult]:
+    """Descend all guesses as one batch (with the extrapolation of App. C inside the descent
+    unless extrapolate is False); returns one result per guess (and appends the final loops
+    u[n, m] to ``states`` when given)."""
     import torch
     from . import ks_loop as K
     if not guesses:
@@ -81,6 +82,8 @@ def descend_guesses(guesses: List[Guess], L: float, dtau: float = 0.15, tol: flo
                   chunk=chunk) as h:
         if symmetric:
             K.ks_set_option(h.handle, "symmetry", 1)
+        if extrapolate:
+            K.ks_set_option(h.handle, "extrapolate", 1)
         K.ks_residual(h.handle, u, T, None, J0)
         K.ks_descend(h.handle, u, T, max_steps, tol, steps, sq, st)
         torch.cuda.synchronize()
