@@ -5,7 +5,9 @@ scheme, dtau, tolerances), the band state of every loop (ks_get_band: the Fourie
 coefficients u_hat of Eq. 2D_Fourier, widened to double), T, the step counters, the
 precision each loop descends in, and each loop's convergence history.  Resuming creates a
 handle with the same configuration and installs the band with ks_set_band, so the continued
-descent is bit-identical to an uninterrupted one.
+descent is bit-identical to an uninterrupted one.  (With the "extrapolate" knob the anchors of
+the extrapolation are not saved: a resumed descent takes new anchors at its first read-back, so
+its later extrapolations can differ from an uninterrupted run's.)
 """
 from __future__ import annotations
 
