@@ -78,3 +78,32 @@ def test_large8_256x1024_sampled_fp32():
     d = ko.descend(us[3], w.T0[3], w.L, w.dtau, w.scheme, 1)
     assert rel(out[3], d["u"]) < 1e-5
     assert abs(T[3] - d["T"]) < 1e-5 * d["T"]
+
+
+@pytest.mark.parametrize("nx,ns", [(1024, 8), (8, 1024), (1024, 16)])
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+def test_maximum_transform_lengths(nx, ns, mode):
+    """The largest supported length (1024) in x or s: residual, gradient and two descent steps
+    against the oracle.  L keeps the largest retained wavenumber near the workloads' (L = 22 nx / 64)
+    and the init spectrum reaches the band edge, as in the other parity tests."""
+    from paper_2007_06427_gb300.inputs import spectral_loop
+    L = 22.0 * max(1.0, nx / 64)
+    u0, T0, _ = spectral_loop(3, nx, L, ns=ns, T_range=(20.0, 80.0),
+                              decay=(max(2.0, (nx // 3) / 10.0), max(2.0, (ns // 3) / 10.0)))
+    if mode == K.KS_FP32:
+        u0 = u0.astype(np.float32).astype(np.float64)
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    u = torch.from_numpy(u0.ravel()).to("cuda", dt)
+    T = torch.tensor([T0], dtype=torch.float64, device="cuda")
+    with K.KSLoop(L, nx, [ns], mode, K.KS_IMEX, 0.15, chunk=1) as h:
+        G = torch.empty_like(u)
+        dJdT = torch.empty(1, dtype=torch.float64, device="cuda")
+        K.ks_adjoint_grad(h.handle, u, T, G, dJdT)
+        K.ks_descend(h.handle, u, T, 2, 0.0)
+        torch.cuda.synchronize()
+    ref = ko.adjoint_grad(u0, T0, L)
+    assert rel(G.double().cpu().numpy().reshape(ns, nx), ref["G"]) < TOL[mode]
+    assert abs(dJdT.item() - ref["dJdT"]) <= TOL[mode] * abs(ref["dJdT"])
+    d = ko.descend(u0, T0, L, 0.15, ko.IMEX, 2)
+    assert rel(u.double().cpu().numpy().reshape(ns, nx), d["u"]) < TOL[mode]
+    assert abs(T.item() - d["T"]) < TOL[mode] * d["T"]
