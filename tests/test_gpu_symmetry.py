@@ -213,3 +213,21 @@ def test_flow_preserves_symmetry_without_projection():
     a = u.cpu().numpy().reshape(nss[0], nx)
     odd_part = 0.5 * (a - np.roll(a[:, ::-1], 1, axis=1))
     assert np.abs(a - odd_part).max() < 1e-10 * np.abs(a).max()
+
+
+def test_extrapolated_descent_stays_invariant():
+    """The extrapolation of App. C inside ks_descend moves a loop along a combination of two
+    invariant states, so with the knob set the band stays exactly invariant through it."""
+    L, nx, nss = 22.0, 32, [32, 64]
+    us, Ts = make(nx, nss, L, T_range=(30.0, 50.0))
+    us = [1e-2 * a for a in us]
+    u, T = dev(us, Ts, K.KS_FP64)
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    with K.KSLoop(L, nx, nss, K.KS_MIXED, K.KS_IMEX, 0.15, tol=1e-10, switch_tol=1e-6,
+                  chunk=500) as h:
+        K.ks_set_option(h.handle, "symmetry", 1)
+        K.ks_set_option(h.handle, "extrapolate", 1)
+        K.ks_descend(h.handle, u, T, 400000, 1e-10, None, None, st)
+        assert K.ks_get_option(h.handle, "extrapolations") >= 1
+        assert band_violations(h, nx, nss) == 0
+    assert st.tolist() == [K.KS_CONVERGED] * 2
