@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--autotune", action="store_true",
+                    help="create the timed handles with the autotuner (launch shape by timing)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="number of loops, for the batched workloads (default: the workload's)")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--e2e-tau-steps", type=int, default=100)
     ap.add_argument("--e2e-calls", type=int, default=10)
@@ -185,7 +189,7 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle import ks_oracle as ko
 from paper_2007_06427_gb300.inputs import workload
-w = workload({wl!r})
+w = workload({wl!r}, {batch!r})
 gs = [ko.grid(w.nx, n, w.L) for n in w.ns]
 uh = [ko.band_state(u, w.L) for u in w.u]
 T = list(w.T0)
@@ -210,12 +214,12 @@ print(json.dumps({{"steps": steps, "seconds": el, "gridpoint_steps": gp}}))
 
 
 def run_cpu_oracle(workload_name: str, budget_s: float = 0.0, max_steps: int = 0,
-                   threads: int = 1):
+                   threads: int = 1, batch=None):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = CPU_SNIPPET.format(root=ROOT, wl=workload_name, mode="fp64", budget=budget_s,
+    code = CPU_SNIPPET.format(root=ROOT, wl=workload_name, batch=batch, mode="fp64", budget=budget_s,
                               max_steps=max_steps)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                          timeout=900)
@@ -237,11 +241,11 @@ def reference_arm(args):
     if rank != 0:
         return 0
     from paper_2007_06427_gb300.inputs import workload
-    w = workload(args.workload)
+    w = workload(args.workload, args.batch)
     # warm-up steps, then exactly K timed oracle tau-steps
     if args.warmup:
-        run_cpu_oracle(args.workload, 0.0, args.warmup)
-    r = run_cpu_oracle(args.workload, 0.0, args.steps)
+        run_cpu_oracle(args.workload, 0.0, args.warmup, batch=args.batch)
+    r = run_cpu_oracle(args.workload, 0.0, args.steps, batch=args.batch)
     value = r["gridpoint_steps"] / r["seconds"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -278,25 +282,26 @@ def ours_arm(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            r = run_cpu_oracle(args.workload, args.cpu_seconds, 0)
+            r = run_cpu_oracle(args.workload, args.cpu_seconds, 0, batch=args.batch)
             cpu = {"value": r["gridpoint_steps"] / r["seconds"], "unit": UNIT, "cores": 1,
                    "kind": "oracle",
                    "sample": f"{r['steps']} oracle tau-steps of {args.workload} "
                              f"({r['seconds']:.1f} s, NumPy FP64 dense DFTs, 1 BLAS thread)"}
             nc = os.cpu_count() or 1
             if nc > 1:
-                ra = run_cpu_oracle(args.workload, args.cpu_seconds / 2, 0, threads=nc)
+                ra = run_cpu_oracle(args.workload, args.cpu_seconds / 2, 0, threads=nc,
+                                    batch=args.batch)
                 cpu["all_cores"] = {"value": ra["gridpoint_steps"] / ra["seconds"], "cores": nc,
                                     "sample": f"{ra['steps']} oracle tau-steps, {nc} BLAS threads"}
         except Exception as e:  # keep the GPU line even if the host leg fails
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {str(e)[-200:]}"}
 
-    w = workload(args.workload)
+    w = workload(args.workload, args.batch)
     if ws > 1:
         # every rank descends its own loops: seeds offset by rank
         from paper_2007_06427_gb300.inputs import make_loops
-        base = workload(args.workload)
+        base = workload(args.workload, args.batch)
         w = make_loops(base.name, base.nx, base.L, [rank * base.batch + i for i in range(base.batch)],
                        ns=base.ns[0] if len(set(base.ns)) == 1 else None,
                        ns_choices=None if len(set(base.ns)) == 1 else (32, 64, 128, 256),
@@ -308,7 +313,7 @@ def ours_arm(args):
     stream = torch.cuda.current_stream(dev)
     u = torch.from_numpy(w.packed()).to(dev, dt)
     T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
-    h = K.KSLoop(w.L, nx, nss, mode, w.scheme, w.dtau)
+    h = K.KSLoop(w.L, nx, nss, mode, w.scheme, w.dtau, autotune=int(args.autotune))
     K.ks_set_state(h.handle, u, T, stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     for _ in range(args.warmup):
@@ -387,6 +392,10 @@ def ours_arm(args):
     if not args.no_fp32 and mode == K.KS_FP64:
         fp32 = throughput_fp32(args, w, dev, flush, K)
 
+    launch_shape = {"path": K.ks_get_option(h.handle, "path"),
+                    "cluster": K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64"),
+                    "threads": K.ks_get_option(h.handle, "cluster_threads"),
+                    "autotuned": bool(args.autotune)}
     h.close()
     if rank == 0:
         line = {
@@ -397,7 +406,8 @@ def ours_arm(args):
             "config": {"workload": w.name, "L": w.L, "nx": nx, "ns": nss[:8], "batch": w.batch,
                        "scheme": "imex" if w.scheme else "explicit", "dtau": w.dtau,
                        "l2": "flushed (256 MiB write) before every timed step",
-                       "gridpoints": gp},
+                       "gridpoints": gp,
+                       "launch": launch_shape},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -472,7 +482,7 @@ def throughput_fp32(args, w, dev, flush, K):
     stream = torch.cuda.current_stream(dev)
     u = torch.from_numpy(w.packed()).to(dev, torch.float32)
     T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
-    h = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP32, w.scheme, w.dtau)
+    h = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP32, w.scheme, w.dtau, autotune=int(args.autotune))
     K.ks_set_state(h.handle, u, T, stream)
     for _ in range(args.warmup):
         K.ks_step(h.handle, 1, 0.0, stream)
@@ -573,7 +583,7 @@ def ncu_case(args):
     import torch
     from paper_2007_06427_gb300 import ks_loop as K
     from paper_2007_06427_gb300.inputs import workload
-    w = workload(args.workload)
+    w = workload(args.workload, args.batch)
     mode = K.KS_FP32 if args.mode == "fp32" else K.KS_FP64
     dt = torch.float32 if mode == K.KS_FP32 else torch.float64
     u = torch.from_numpy(w.packed()).cuda().to(dt)
