@@ -137,7 +137,9 @@ KS_API int ks_adjoint_grad(ks_loop_t h, const void* u, const double* T, void* G,
  *   status   : out, int[batch], KS_CONVERGED / KS_STEP_CAP / KS_STALLED / KS_DIVERGED
  *              (nullable)
  * Loops are frozen individually when they converge or diverge; the call returns when every
- * loop is frozen or has taken max_steps steps.  The final state also stays resident. */
+ * loop is frozen or has taken max_steps steps.  The final state also stays resident.  The
+ * knobs "extrapolate" (App. C), "symmetry" (centre-symmetric subspace), "stall_window" and the
+ * mixed-precision switch act here (see ks_set_option). */
 KS_API int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, double tol,
                long long* steps, double* sqrtJ, int* status, void* stream);
 
