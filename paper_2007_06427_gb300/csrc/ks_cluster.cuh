@@ -139,20 +139,36 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
     R* const s_lin = s_qv + nkx;
     R* const s_cq = s_lin + nkx;
     RA* const s_lina = reinterpret_cast<RA*>(s_cq + nkx);
-    for (int i = tid; i < nkx; i += nt) {
+    // Start-up: every load that depends on nothing is issued before any of them is waited on
+    // (the first loop's index, the first entries of the per-mode tables, the twiddles), so they
+    // share one round trip to memory instead of one each.  No barrier after the copies: the
+    // tables are first read after the barrier that closes the state load below.
+    const int b_first = (cid < B) ? p.colorder[cid] : 0;
+    R q0 = 0, l0 = 0, c0 = 0;
+    RA la0 = 0;
+    if (tid < nkx) {
+        q0 = p.qv[tid];
+        l0 = p.lin[tid];
+        c0 = p.cq[tid];
+        la0 = ta.lin[tid];
+    }
+    copy16_g2s(tws, p.tw, (int)(NMAX * sizeof(cpx<R>)));
+    if (!kSame) copy16_g2s(tws_a, ta.tw, (int)(NMAX * sizeof(cpx<RA>)));
+    if (tid < nkx) {
+        s_qv[tid] = q0;
+        s_lin[tid] = l0;
+        s_cq[tid] = c0;
+        s_lina[tid] = la0;
+    }
+    for (int i = tid + nt; i < nkx; i += nt) {
         s_qv[i] = p.qv[i];
         s_lin[i] = p.lin[i];
         s_cq[i] = p.cq[i];
         s_lina[i] = ta.lin[i];
     }
 
-    // no barrier after the table copies: the twiddles are first read after the barrier that
-    // closes the state load below, so the copies overlap the per-loop loads
-    copy16_g2s(tws, p.tw, (int)(NMAX * sizeof(cpx<R>)));
-    if (!kSame) copy16_g2s(tws_a, ta.tw, (int)(NMAX * sizeof(cpx<RA>)));
-
     for (int bi = cid; bi < B; bi += ncl) {
-        const int b = p.colorder[bi];
+        const int b = (bi == cid) ? b_first : p.colorder[bi];
         // the skip test and the per-loop scalars in one round of loads; every rank reads the
         // same global words, so the skip is uniform across the cluster
         const int prec_b = p.prec[b], status_b = p.status[b];
