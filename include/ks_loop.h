@@ -211,14 +211,18 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *                    non-invariant part (set the state again after changing the knob);
  *                    ks_set_band stores the band as given.
  *   "extrapolate"    1: ks_descend accelerates each loop by the extrapolation of App. C: once
- *                    sqrt(J) (evaluated in double at the read-backs) is below 1e-3, every time it
- *                    has halved since the loop's anchor state, the loop is moved to
- *                    l + (l - l_anchor) rho / (1 - rho), rho = sqrt(J) / sqrt(J_anchor), on its
- *                    band and T; the move is kept only if it lowers sqrt(J).  Read-backs happen
- *                    every "chunk" steps, so the chunk sets how finely the halvings are caught.
- *                    0 (default): plain descent.  ks_get_option "extrapolations" and
+ *                    sqrt(J) (evaluated in double at the read-backs) is below the start
+ *                    threshold, every time it has halved since the loop's anchor state, the loop
+ *                    is moved to l + (l - l_anchor) rho / (1 - rho), rho = sqrt(J) / sqrt(J_anchor),
+ *                    on its band and T; the move is kept only if it lowers sqrt(J).  Read-backs
+ *                    happen every "chunk" steps, so the chunk sets how finely the halvings are
+ *                    caught.  0 (default): plain descent.  ks_get_option "extrapolations" and
  *                    "extrapolations_rejected" count the moves kept and dropped by the last
  *                    ks_descend.
+ *   "extrapolate_start_ppm"  the start threshold on sqrt(J) in parts per million, 1 .. 1e9
+ *                    (default 1000, i.e. 1e-3, the value of the example of App. C)
+ *   "extrapolate_drop_ppm"   the fraction of the anchor's sqrt(J) at which the next move is
+ *                    made, in parts per million, 1 .. 999999 (default 500000: "has halved")
  *   "stall_window"   tau-steps over which ks_descend measures progress (default 40000)
  *   "stall_drop_ppm" a loop whose sqrt(J) fell by less than this many parts per million over
  *                    a window is stalled (default 1000): the float phase of a mixed descent
@@ -236,7 +240,8 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
  * "cluster_f32", "cluster_mixed_finish" (cluster
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk", "symmetry",
- * "extrapolate", "extrapolations", "extrapolations_rejected". */
+ * "extrapolate", "extrapolate_start_ppm", "extrapolate_drop_ppm", "extrapolations",
+ * "extrapolations_rejected". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
 
 /* Residual of ONE double-precision loop without allocating any device memory.

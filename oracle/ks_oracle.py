@@ -300,6 +300,71 @@ def descend(u: np.ndarray, T: float, L: float, dtau: float, scheme: int, nsteps:
     return out
 
 
+def sqrt_cost(uh: np.ndarray, T: float, g: Grid) -> float:
+    """sqrt(J) of the band state (uh, T): the convergence measure of Sec. 4.3."""
+    rh, _, _ = residual_hat(uh, T, g)
+    return math.sqrt(max(cost(rh, g), 0.0))
+
+
+def descend_extrapolated(u: np.ndarray, T: float, L: float, dtau: float, scheme: int,
+                         nsteps: int, tol: float, chunk: int, start: float = 1e-3,
+                         drop: float = 0.5, xi: bool = False) -> dict:
+    """Tau-descent accelerated by linear extrapolation along the trajectory (App. C).
+
+    App. C alternates integration of Eq. KS_G with an extrapolation along the leading
+    eigendirection of the linearised loop dynamics about the attracting loop: the first one
+    once sqrt(J) has reached ``start`` (1e-3 in its example), and then each time sqrt(J) has
+    halved since the previous one (``drop`` = 1/2).  The paper gives no formula; the reading
+    used here: the loop is observed every ``chunk`` steps; below ``start`` the first
+    observation becomes the anchor l_a; at an observation l_b with sqrt(J_b) <= drop *
+    sqrt(J_a), if the approach were a single decaying eigendirection, l(tau) = l* + c rho^tau,
+    the fixed point would be l* = l_b + (l_b - l_a) rho / (1 - rho) with rho = sqrt(J_b) /
+    sqrt(J_a) (J is quadratic in the distance to l*).  This l* (for the band state and T) is
+    kept only if its sqrt(J) is below sqrt(J_b); either way the state the descent continues
+    from becomes the next anchor.  The convergence test is that of ``descend``: stop before a
+    step whose starting state has sqrt(J) < tol.
+
+    Returns the final grid field, T, the step count, sqrt(J) of the final state, and the
+    numbers of extrapolations kept and rejected.
+    """
+    g = grid(u.shape[1], u.shape[0], L)
+    uh = band_state(u, L, xi)
+    steps = 0
+    anchor = None            # (uh, T, sqrt(J)) at the start of the current halving segment
+    kept = rejected = 0
+    converged = False
+    while steps < nsteps and not converged:
+        for _ in range(min(chunk, nsteps - steps)):
+            if sqrt_cost(uh, T, g) < tol:
+                converged = True
+                break
+            uh, T, _, _ = step_hat(uh, T, g, dtau, scheme, xi)
+            steps += 1
+        if converged:
+            break
+        sq = sqrt_cost(uh, T, g)
+        if not sq <= start:
+            continue
+        if anchor is None:
+            anchor = (uh, T, sq)
+            continue
+        if sq > drop * anchor[2]:
+            continue
+        rho = sq / anchor[2]
+        c = rho / (1.0 - rho)
+        uh_e = uh + (uh - anchor[0]) * c
+        T_e = T + (T - anchor[1]) * c
+        sq_e = sqrt_cost(uh_e, T_e, g)
+        if sq_e < sq:
+            uh, T, sq = uh_e, T_e, sq_e
+            kept += 1
+        else:
+            rejected += 1
+        anchor = (uh, T, sq)
+    return {"u": g.real_grid(uh), "uh": uh, "T": T, "steps": steps,
+            "sqrtJ": sqrt_cost(uh, T, g), "extrapolations": kept, "rejected": rejected}
+
+
 # ---------------------------------------------------------------------------------------
 # Independent forms used only to pin the above (App. B; Eq. KS_G_1)
 # ---------------------------------------------------------------------------------------

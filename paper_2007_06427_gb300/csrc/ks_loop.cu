@@ -275,6 +275,8 @@ struct ks_loop {
     int xi = 0;                     // 1: loads, gradients and updates projected onto the Xi subspace
     // ks_descend with the extrapolation of App. C (knob "extrapolate")
     int extrapolate = 0;
+    double extrap_start = 1e-3;  // sqrt(J) below which a loop takes its first anchor (App. C)
+    double extrap_drop = 0.5;    // extrapolate once sqrt(J) has fallen to this fraction of the anchor's
     double* anc = nullptr;          // [nband] complex double: each loop's anchor band
     double* cand = nullptr;         // [nband] complex double: the current bands, widened
     double* coef = nullptr;         // [B] extrapolation coefficient of each loop (0: none)
@@ -1361,7 +1363,8 @@ int monitor_f64(ks_loop* h, cudaStream_t s, std::vector<double>& out, bool doubl
 // geometrically, l* ~ l + (l - l_a) rho / (1 - rho), rho = sqrt(J) / sqrt(J_a), on the band and
 // T.  The candidate is kept only if its sqrt(J), evaluated in double, is lower; either way the
 // loop's anchor moves to the state it continues from.  touched[b] marks the loops handled.
-constexpr double kExtrapStart = 1e-3, kExtrapDrop = 0.5;
+// The start threshold and the drop ratio are the handle's knobs; their defaults, 1e-3 and
+// 1/2, are the values of the example of App. C.
 
 int extrapolate_round(ks_loop* h, cudaStream_t s, const std::vector<double>& val,
                       std::vector<char>& touched) {
@@ -1392,7 +1395,7 @@ int extrapolate_round(ks_loop* h, cudaStream_t s, const std::vector<double>& val
     std::vector<double> c(B, 0.0), Tc(Tcur);
     bool anyA = false, anyC = false;
     for (int b = 0; b < B; ++b) {
-        if (h->h_status[b] != KS_RUNNING || !(val[b] <= kExtrapStart)) continue;
+        if (h->h_status[b] != KS_RUNNING || !(val[b] <= h->extrap_start)) continue;
         if (h->anc_sq[b] < 0.0) {
             selA[b] = 1;
             h->anc_sq[b] = val[b];
@@ -1400,7 +1403,7 @@ int extrapolate_round(ks_loop* h, cudaStream_t s, const std::vector<double>& val
             anyA = true;
             continue;
         }
-        if (val[b] > kExtrapDrop * h->anc_sq[b]) continue;
+        if (val[b] > h->extrap_drop * h->anc_sq[b]) continue;
         const double rho = val[b] / h->anc_sq[b];
         c[b] = rho / (1.0 - rho);
         Tc[b] = Tcur[b] + (Tcur[b] - h->anc_T[b]) * c[b];
@@ -1759,6 +1762,12 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         h->finish_f32_adjoint = value != 0;
     } else if (k == "extrapolate") {
         h->extrapolate = value ? 1 : 0;
+    } else if (k == "extrapolate_start_ppm") {
+        if (value < 1 || value > 1000000000LL) return fail(KS_ERR_ARG, "extrapolate_start_ppm in [1, 1e9]");
+        h->extrap_start = (double)value * 1e-6;
+    } else if (k == "extrapolate_drop_ppm") {
+        if (value < 1 || value >= 1000000) return fail(KS_ERR_ARG, "extrapolate_drop_ppm in [1, 1e6)");
+        h->extrap_drop = (double)value * 1e-6;
     } else if (k == "symmetry") {
         if (value < 0 || value > 1) return fail(KS_ERR_ARG, "symmetry must be 0 (none) or 1 (Xi)");
         h->xi = (int)value;
@@ -1795,6 +1804,8 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "chunk") *value = h->chunk;
     else if (k == "symmetry") *value = h->xi;
     else if (k == "extrapolate") *value = h->extrapolate;
+    else if (k == "extrapolate_start_ppm") *value = std::llround(h->extrap_start * 1e6);
+    else if (k == "extrapolate_drop_ppm") *value = std::llround(h->extrap_drop * 1e6);
     else if (k == "extrapolations") *value = h->n_extrap;
     else if (k == "extrapolations_rejected") *value = h->n_extrap_rejected;
     else return fail(KS_ERR_ARG, "unknown option " + k);

@@ -58,10 +58,11 @@ def classify(u: np.ndarray, L: float, trivial: float = 1e-6, steady: float = 1e-
 def descend_guesses(guesses: List[Guess], L: float, dtau: float = 0.15, tol: float = 1e-10,
                     max_steps: int = 2_000_000, symmetric: bool = True, mode: str = "mixed",
                     chunk: int = 5000, device: str = "cuda", states: Optional[list] = None,
-                    extrapolate: bool = True) -> List[OrbitResult]:
+                    extrapolate: bool = True,
+                    extrapolate_start: float = 1e-3) -> List[OrbitResult]:
     """Descend all guesses as one batch (with the extrapolation of App. C inside the descent
-    unless extrapolate is False); returns one result per guess (and appends the final loops
-    u[n, m] to ``states`` when given)."""
+    unless extrapolate is False, first anchored once sqrt(J) <= extrapolate_start); returns one
+    result per guess (and appends the final loops u[n, m] to ``states`` when given)."""
     import torch
     from . import ks_loop as K
     if not guesses:
@@ -84,6 +85,7 @@ def descend_guesses(guesses: List[Guess], L: float, dtau: float = 0.15, tol: flo
             K.ks_set_option(h.handle, "symmetry", 1)
         if extrapolate:
             K.ks_set_option(h.handle, "extrapolate", 1)
+            K.ks_set_option(h.handle, "extrapolate_start_ppm", int(round(extrapolate_start * 1e6)))
         K.ks_residual(h.handle, u, T, None, J0)
         K.ks_descend(h.handle, u, T, max_steps, tol, steps, sq, st)
         torch.cuda.synchronize()
@@ -166,13 +168,17 @@ def main(argv: Optional[List[str]] = None) -> int:
     ap.add_argument("--refine-best", type=int, default=0,
                     help="continue this many of the best unconverged loops with extrapolation")
     ap.add_argument("--refine-steps", type=int, default=4_000_000)
+    ap.add_argument("--extrapolate-start", type=float, default=1e-3,
+                    help="sqrt(J) at which the batched descent takes its first extrapolation "
+                         "anchor (App. C's example: 1e-3)")
     args = ap.parse_args(argv)
     gs, res, t_guess, t_desc = search(L=args.L, nx=args.nx, ns=args.ns, t_end=args.t_end,
                                       seed=args.seed, guesses=args.guesses,
                                       symmetric=not args.no_symmetry, tol=args.tol,
                                       max_steps=args.max_steps, mode=args.mode,
                                       refine_best=args.refine_best,
-                                      refine_steps=args.refine_steps)
+                                      refine_steps=args.refine_steps,
+                                      extrapolate_start=args.extrapolate_start)
     print(json.dumps({"L": args.L, "nx": args.nx, "ns": args.ns, "guesses": len(gs),
                       "seconds_guesses": t_guess, "seconds_descent": t_desc,
                       "results": [asdict(r) for r in res]}))
