@@ -71,22 +71,25 @@ __device__ __forceinline__ void store_pair(cpx<X>* dst, cpx<X> a, cpx<X> b) {
     }
 }
 
-// 16-byte copy global -> shared with up to eight loads in flight per thread (bytes % 16 == 0)
-__device__ __forceinline__ void copy16_g2s(void* dst, const void* src, int bytes) {
-    const int4* s = reinterpret_cast<const int4*>(src);
-    int4* d = reinterpret_cast<int4*>(dst);
-    const int n = bytes >> 4;
-    for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
-        int4 v[8];
+// The twiddles a transform of length n <= nm reads: entries t of exp(2 pi i t / NMAX) with t a
+// multiple of NMAX / n (every pass indexes the table by multiples of NMAX / (4 span) or more, and
+// 4 span <= n), hence of NMAX / nm.  Only those entries are fetched into the shared-memory copy of
+// the table, at their own positions: the values the transforms read are unchanged, and the
+// bytes fetched drop by NMAX / nm (8x for 128-point columns).
+template <typename X>
+__device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, int nm) {
+    const int st = NMAX / nm;
+    for (int base = threadIdx.x; base < nm; base += 4 * blockDim.x) {
+        cpx<X> v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int i = base + u * blockDim.x;
-            if (i < n) v[u] = s[i];
+            if (i < nm) v[u] = src[(size_t)i * st];
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int i = base + u * blockDim.x;
-            if (i < n) d[i] = v[u];
+            if (i < nm) dst[(size_t)i * st] = v[u];
         }
     }
 }
@@ -104,8 +107,13 @@ struct AdjTables {
 // the forward transform and G_hat assembly of phase B').  RA = R is the plain float or double
 // descent; R = double, RA = float is the finishing stage of a mixed descent, where r, J,
 // dJ/dT and the update stay in double and only the descent direction is formed in float.
+// Launch bounds: up to 256 threads, at least one resident block per SM.  With the first bound
+// alone ptxas held the double kernel to 64 registers and spilled 120 bytes per thread, whose
+// stores and reloads reached L2 and DRAM after a flush; with both it uses ~150 registers and
+// spills nothing.  The single loop runs one block per SM anyway, and the batched workloads
+// (64x64 batch, ragged, 256x1024) measured no slower with the fewer resident blocks.
 template <typename R, typename RA>
-__global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA> ta,
+__global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables<RA> ta,
                                                  ClusterPlan cp, int nsteps, int par0, int use_M) {
     typedef typename PartT<R>::type Part;
     constexpr bool kSame = sizeof(R) == sizeof(RA);
@@ -140,8 +148,8 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
     R* const s_cq = s_lin + nkx;
     RA* const s_lina = reinterpret_cast<RA*>(s_cq + nkx);
     // Start-up: every load that depends on nothing is issued before any of them is waited on
-    // (the first loop's index, the first entries of the per-mode tables, the twiddles), so they
-    // share one round trip to memory instead of one each.  No barrier after the copies: the
+    // (the first loop's index, the first entries of the per-mode tables, the twiddles the
+    // launch's transforms read), so they share one round trip to memory instead of one each.  No barrier after the copies: the
     // tables are first read after the barrier that closes the state load below.
     const int b_first = (cid < B) ? p.colorder[cid] : 0;
     R q0 = 0, l0 = 0, c0 = 0;
@@ -152,8 +160,9 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
         c0 = p.cq[tid];
         la0 = ta.lin[tid];
     }
-    copy16_g2s(tws, p.tw, (int)(NMAX * sizeof(cpx<R>)));
-    if (!kSame) copy16_g2s(tws_a, ta.tw, (int)(NMAX * sizeof(cpx<RA>)));
+    const int nm = max(nx, cp.nsmax);  // longest transform of the launch
+    load_twiddles(tws, p.tw, nm);
+    if (!kSame) load_twiddles(tws_a, ta.tw, nm);
     if (tid < nkx) {
         s_qv[tid] = q0;
         s_lin[tid] = l0;
@@ -404,11 +413,17 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
             cl.sync();
 
             // ======== phase B': J, L2, freeze test, G_hat, update, v = s-inverse (a9, a10) ===
-            // warp 0 sums the partials; thread 0 forms J, L^dag_2 and the next T, 2 pi / T
-            if (tid < 32) {
+            // The last warp sums the partials and its first lane forms J, L^dag_2 and the next
+            // T, 2 pi / T.  With the adjoint half in float, the s-transform of w_hat runs at the
+            // same time: float transforms are warp-owned, so the last warp owns none for up to
+            // (warps - 1) columns and only joins the transform's closing barrier.  (Its result
+            // is not used when the loop stops at this step.)  A double transform needs every
+            // warp, so there it follows the freeze test as before.
+            constexpr bool kFftFirst = sizeof(RA) == 4;
+            if (tid >= nt - 32) {
                 double sJ, sL;
                 sum_partials(part, part + nkx, nkx, sJ, sL);
-                if (tid == 0) {
+                if (tid == nt - 32) {
                     const double J = sJ * d.L;
                     const double L2 = sL * d.L * (wT * wT) * kInv2Pi;  // (L / T^2) 2 pi sum
                     const double Tn = T - d.dtau * L2;    // explicit Euler for T (Sec. 4.2)
@@ -423,6 +438,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
                     reinterpret_cast<int*>(red + 3)[0] = sv;
                 }
             }
+            if (kFftFirst && ncol > 0) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
             __syncthreads();
             const double J = red[0], Tnext = red[1], wTnext = red[2];
             st = reinterpret_cast<const int*>(red + 3)[0];
@@ -430,7 +446,7 @@ __global__ void __launch_bounds__(256) k_cluster(Dims d, Bufs<R> p, AdjTables<RA
             Jlast = J;
             if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
             if (ncol > 0) {
-                col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
+                if (!kFftFirst) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;
