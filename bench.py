@@ -348,7 +348,8 @@ def ours_arm(args):
         tmax = float(t.item())
     value = ws * gp * args.steps / (tmax / 1e3)
 
-    roof = roofline_entry(prof, total_ms / args.steps, w, nx, nss)
+    roof = annotate_sms(roofline_entry(prof, total_ms / args.steps, w, nx, nss), K, h, mode,
+                        w.batch, dev)
 
     # end to end through the public call with pinned host buffers
     e2e = None
@@ -476,6 +477,22 @@ def roofline_entry(prof, ms_per_step, w, nx, nss):
                             else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")}
 
 
+def annotate_sms(roof, K, h, mode, batch, dev):
+    """For the cluster-resident kernel: the SMs a launch occupies (one CTA per SM; C CTAs per
+    loop) and the roofline fraction against the peak of those SMs alone."""
+    import torch
+    if not roof or K.ks_get_option(h.handle, "path") != 0:
+        return roof
+    C = K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64")
+    if C <= 0:
+        return roof
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    used = min(n_sms, C * batch)
+    roof["sms_used"] = used
+    roof["frac_of_sms_used"] = roof["frac"] * n_sms / used
+    return roof
+
+
 def throughput_fp32(args, w, dev, flush, K):
     """Same timed loop on an FP32 handle (the bulk phase of a mixed descent)."""
     import torch
@@ -500,11 +517,12 @@ def throughput_fp32(args, w, dev, flush, K):
         evs.append((e0, e1))
     torch.cuda.synchronize(dev)
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    h.close()
     out = {"value": w.gridpoints * args.steps / (total_ms / 1e3), "unit": UNIT,
            "ms_per_step": total_ms / args.steps, "dtype": "f32",
            "gpu_launches": int(round(per_step * args.steps))}
-    roof = roofline_entry(prof, total_ms / args.steps, w, w.nx, w.ns)
+    roof = annotate_sms(roofline_entry(prof, total_ms / args.steps, w, w.nx, w.ns), K, h,
+                        K.KS_FP32, w.batch, dev)
+    h.close()
     if roof:
         out["roofline"] = roof
     return out
