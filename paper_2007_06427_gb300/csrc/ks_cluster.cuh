@@ -50,7 +50,7 @@ __host__ __device__ inline int cluster_rows_per_rank(int ns, int C) {
 template <typename R>
 __device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                                 const cpx<R>* tw) {
-    cpx<R>* r = fft_warp(a, b, lg, cnt, dir, tw);
+    cpx<R>* r = fft_warp<R, true>(a, b, lg, cnt, dir, tw);
     if (r != a) {
         const int n = cnt << lg;
         for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = r[i];
@@ -74,8 +74,9 @@ __device__ __forceinline__ void store_pair(cpx<X>* dst, cpx<X> a, cpx<X> b) {
 // The twiddles a transform of length n <= nm reads: entries t of exp(2 pi i t / NMAX) with t a
 // multiple of NMAX / n (every pass indexes the table by multiples of NMAX / (4 span) or more, and
 // 4 span <= n), hence of NMAX / nm.  Only those entries are fetched into the shared-memory copy of
-// the table, at their own positions: the values the transforms read are unchanged, and the
-// bytes fetched drop by NMAX / nm (8x for 128-point columns).
+// the table, at their bank-swizzled positions (tw_swz; every transform of the cluster kernel
+// reads the table through it): the values the transforms read are unchanged, and the bytes
+// fetched drop by NMAX / nm (8x for 128-point columns).
 template <typename X>
 __device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, int nm) {
     const int st = NMAX / nm;
@@ -89,7 +90,7 @@ __device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, in
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = base + u * blockDim.x;
-            if (i < nm) dst[(size_t)i * st] = v[u];
+            if (i < nm) dst[tw_swz<X>(i * st)] = v[u];
         }
     }
 }
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     A[(size_t)r * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<R>* z = fft_warp(A, Bf, lgnx, nr, +1, tws);
+                cpx<R>* z = fft_warp<R, true>(A, Bf, lgnx, nr, +1, tws);
                 cpx<R>* Y = (z == A) ? Bf : A;
                 const int np = nr >> 1;
                 for (int i = tid; i < np * nx; i += nt) {
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_warp(Y, z, lgnx, np, -1, tws);
+                cpx<R>* F = fft_warp<R, true>(Y, z, lgnx, np, -1, tws);
                 const int lgp = lgnr - 1;
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 }
                 __syncthreads();
                 // inverse of i q r_hat (scr holds the spectra, Mloc is scratch), then push rho
-                push_columns(fft_warp(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a);
+                push_columns(fft_warp<RA, true>(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a);
             }
             cl.sync();
 
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     A[(size_t)pr * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<RA>* z = fft_warp(A, Bf, lgnx, np, +1, tws_a);
+                cpx<RA>* z = fft_warp<RA, true>(A, Bf, lgnx, np, +1, tws_a);
                 cpx<RA>* Y = (z == A) ? Bf : A;
                 for (int i = tid; i < np * nx; i += nt) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                                   (RA)Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
                 }
                 __syncthreads();
-                cpx<RA>* F = fft_warp(Y, z, lgnx, np, -1, tws_a);
+                cpx<RA>* F = fft_warp<RA, true>(Y, z, lgnx, np, -1, tws_a);
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
                     const cpx<RA> yj = F[(size_t)pr * nx + j];
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     Y[i] = x;
                 }
                 __syncthreads();
-                push_columns(fft_warp(Y, p.xi ? scr : Mloc, lg, ncol, +1, tws), Rin);
+                push_columns(fft_warp<R, true>(Y, p.xi ? scr : Mloc, lg, ncol, +1, tws), Rin);
             }
             T = Tnext;
             wT = wTnext;
