@@ -71,30 +71,6 @@ __device__ __forceinline__ void store_pair(cpx<X>* dst, cpx<X> a, cpx<X> b) {
     }
 }
 
-// The twiddles a transform of length n <= nm reads: entries t of exp(2 pi i t / NMAX) with t a
-// multiple of NMAX / n (every pass indexes the table by multiples of NMAX / (4 span) or more, and
-// 4 span <= n), hence of NMAX / nm.  Only those entries are fetched into the shared-memory copy of
-// the table, at their bank-swizzled positions (tw_swz; every transform of the cluster kernel
-// reads the table through it): the values the transforms read are unchanged, and the bytes
-// fetched drop by NMAX / nm (8x for 128-point columns).
-template <typename X>
-__device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, int nm) {
-    const int st = NMAX / nm;
-    for (int base = threadIdx.x; base < nm; base += 4 * blockDim.x) {
-        cpx<X> v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = base + u * blockDim.x;
-            if (i < nm) v[u] = src[(size_t)i * st];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = base + u * blockDim.x;
-            if (i < nm) dst[tw_swz<X>(i * st)] = v[u];
-        }
-    }
-}
-
 // Tables in the precision of the adjoint half of a step (twiddles, q_j, q_j^2 - q_j^4).
 template <typename RA>
 struct AdjTables {

@@ -387,6 +387,30 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
     return a;
 }
 
+// The twiddles a transform of length n <= nm reads: entries t of exp(2 pi i t / NMAX) with t a
+// multiple of NMAX / n (every pass indexes the table by multiples of NMAX / (4 span) or more, and
+// 4 span <= n), hence of NMAX / nm.  Only those entries are fetched into the shared-memory copy of
+// the table, at their bank-swizzled positions (tw_swz; every transform of the cluster and
+// persistent kernels reads the table through it): the values the transforms read are
+// unchanged, and the bytes fetched drop by NMAX / nm (8x for 128-point columns).
+template <typename X>
+__device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, int nm) {
+    const int st = NMAX / nm;
+    for (int base = threadIdx.x; base < nm; base += 4 * blockDim.x) {
+        cpx<X> v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * blockDim.x;
+            if (i < nm) v[u] = src[(size_t)i * st];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * blockDim.x;
+            if (i < nm) dst[tw_swz<X>(i * st)] = v[u];
+        }
+    }
+}
+
 template <typename R, bool SWZ = false>
 __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                             const cpx<R>* tw) {
@@ -730,7 +754,8 @@ KS_HD void store_pair_spectra(const Dims& d, const cpx<R>* Y, cpx<R>* Mb, int ns
     }
 }
 
-template <typename R, int MODE>
+// SWZ: p.tw is the bank-swizzled shared-memory copy of the twiddle table (load_twiddles).
+template <typename R, int MODE, bool SWZ = false>
 KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem) {
     const RowItem it = p.rows[item];
     const int b = it.b;
@@ -757,13 +782,13 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = mk<R>(ra[m], ra[nx + m]);
         }
         KS_SYNC();
-        cpx<R>* Y = fft_batch(A, Bf, lgnx, npairs, -1, p.tw);
+        cpx<R>* Y = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, -1, p.tw);
         store_pair_spectra(d, Y, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_SYNTH) {
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_batch(A, Bf, lgnx, npairs, +1, p.tw);
+        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw);
         const int total = npairs * nx;
         for (int i = KS_TID; i < total; i += KS_NT) {
             const int pr = i >> lgnx;
@@ -789,7 +814,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[(size_t)r * nx + J] = z;
         }
         KS_SYNC();
-        cpx<R>* z = fft_batch(A, Bf, lgnx, nr, +1, p.tw);
+        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, nr, +1, p.tw);
         cpx<R>* Y = (z == A) ? Bf : A;
         // keep u, form p = u u_x for the row pairs (a3)
         const int tp = npairs * nx;
@@ -804,14 +829,14 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
         }
         KS_SYNC();
-        cpx<R>* F = fft_batch(Y, z, lgnx, npairs, -1, p.tw);  // a4 (x-pass)
+        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw);  // a4 (x-pass)
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_ADJ) {
         // r_x rows from the column pass output rho = s-inverse of i q_j r_hat   (a7)
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_batch(A, Bf, lgnx, npairs, +1, p.tw);
+        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw);
         cpx<R>* Y = (z == A) ? Bf : A;
         const int tp = npairs * nx;
         for (int i = KS_TID; i < tp; i += KS_NT) {
@@ -822,7 +847,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(ua[m] * rx.x, ua[nx + m] * rx.y);  // w = u r_x  (a8)
         }
         KS_SYNC();
-        cpx<R>* F = fft_batch(Y, z, lgnx, npairs, -1, p.tw);
+        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw);
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     }
@@ -853,7 +878,7 @@ constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
 // cluster kernel of 128 or 256 threads.
 constexpr int COL_ACC_LANES = 128;
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool SWZ = false>
 KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem, int par) {
     const int nkx = d.nkx;
     const int b = p.colorder[item / nkx];
@@ -892,14 +917,14 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = (k >= -ks && k <= ks) ? src[bo + (k + ks)] : mk<R>(0, 0);
         }
         KS_SYNC();
-        cpx<R>* v = fft_batch(A, Bf, lg, 1, +1, p.tw);
+        cpx<R>* v = fft_batch<R, SWZ>(A, Bf, lg, 1, +1, p.tw);
         for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
         KS_SYNC();
     } else {
         // the remaining modes start with a forward s-transform of the column of M
         for (int i = KS_TID; i < ns; i += KS_NT) A[i] = col[i];
         KS_SYNC();
-        cpx<R>* F = fft_batch(A, Bf, lg, 1, -1, p.tw);
+        cpx<R>* F = fft_batch<R, SWZ>(A, Bf, lg, 1, -1, p.tw);
         cpx<R>* X = (F == A) ? Bf : A;
         const R ins = p.insv[b];
 
@@ -937,7 +962,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 X[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch(X, F, lg, 1, +1, p.tw);
+            cpx<R>* v = fft_batch<R, SWZ>(X, F, lg, 1, +1, p.tw);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             block_reduce(acc, red);
             if (KS_TID == 0) {
@@ -1043,7 +1068,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 Y[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch(Y, p.xi ? X : F, lg, 1, +1, p.tw);
+            cpx<R>* v = fft_batch<R, SWZ>(Y, p.xi ? X : F, lg, 1, +1, p.tw);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             if (j == 0 && KS_TID == 0) {
                 const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)

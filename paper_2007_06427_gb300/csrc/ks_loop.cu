@@ -120,19 +120,30 @@ __device__ __forceinline__ bool grid_sync(const GridBar& g) {
 
 // All phases of nsteps tau-steps in one cooperative launch: every CTA walks the row items,
 // barrier, the column items, barrier, ... (four phases per step).
+// The CTA's twiddles (the entries its transforms read, at bank-swizzled positions) are copied
+// to shared memory at tw_off once per launch; the items then read them there instead of from
+// the global table (the same values, so the same bits as the per-phase launches).
+// Launch bounds: always COL_ACC_LANES = 128 threads; six resident blocks per SM caps the
+// registers at 85 (80 used, no spills; with (256) alone ptxas chose 64 and spilled).
 template <typename R>
-__global__ void __launch_bounds__(256) k_persist(Dims d, Bufs<R> p, int nsteps, int par0,
-                                                 int nrow, int ncol, GridBar bar) {
+__global__ void __launch_bounds__(128, 6) k_persist(Dims d, Bufs<R> p, int nsteps, int par0,
+                                                 int nrow, int ncol, GridBar bar, int tw_off,
+                                                 int nm) {
     extern __shared__ __align__(16) unsigned char smem[];
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem + tw_off);
+    load_twiddles(tws, p.tw, nm);
+    __syncthreads();
+    Bufs<R> q = p;
+    q.tw = tws;
     for (int s = 0; s < nsteps; ++s) {
         const int par = (par0 + s) & 1;
-        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_NONLIN>(d, p, it, smem);
+        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_NONLIN, true>(d, q, it, smem);
         if (!grid_sync(bar)) return;
-        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_RESID>(d, p, it, smem, par);
+        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_RESID, true>(d, q, it, smem, par);
         if (!grid_sync(bar)) return;
-        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ>(d, p, it, smem);
+        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ, true>(d, q, it, smem);
         if (!grid_sync(bar)) return;
-        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_UPDATE>(d, p, it, smem, par);
+        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_UPDATE, true>(d, q, it, smem, par);
         if (s + 1 < nsteps && !grid_sync(bar)) return;
     }
 }
@@ -288,6 +299,7 @@ struct ks_loop {
     bool persistent = true;
     int pgrid[2] = {0, 0};
     size_t psmem[2] = {0, 0};
+    int ptw_off[2] = {0, 0};  // offset of the twiddle table in the persistent kernel's smem
     unsigned int* d_bar = nullptr;  // count, gen
     int* d_err = nullptr;
     Work st;   // resident descent state
@@ -555,7 +567,10 @@ int set_smem_attrs(ks_loop* h) {
 template <typename R>
 int setup_persistent(ks_loop* h) {
     const int pr = std::is_same<R, double>::value ? P64 : P32;
-    const size_t sm = std::max(h->lrow[pr].smem, h->lcol[pr].smem);
+    // the items' buffers, then the twiddle table (NMAX entries, swizzled positions)
+    const size_t items_sm = (std::max(h->lrow[pr].smem, h->lcol[pr].smem) + 15) & ~(size_t)15;
+    const size_t sm = items_sm + (size_t)NMAX * sizeof(cpx<R>);
+    h->ptw_off[pr] = (int)items_sm;
     KS_CUDA(cudaFuncSetAttribute(k_persist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0, sms = 0, coop = 0;
     KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R>, COL_ACC_LANES, sm));
@@ -705,7 +720,9 @@ int run_persist(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     int nrow = (int)h->rows.size();
     int ncol = h->d.B * h->d.nkx;
     GridBar bar{h->d_bar, h->d_bar + 1, h->d_err, (unsigned int)h->test_barrier_extra};
-    void* args[] = {&d, &p, &ns_i, &par0, &nrow, &ncol, &bar};
+    int tw_off = h->ptw_off[pr];
+    int nm = std::max(h->d.nx, h->nsmax);  // longest transform
+    void* args[] = {&d, &p, &ns_i, &par0, &nrow, &ncol, &bar, &tw_off, &nm};
     LaunchScope ls(h, s, std::string("persist") + prec_suffix(pr));
     KS_CUDA(cudaLaunchCooperativeKernel((const void*)k_persist<R>, dim3(h->pgrid[pr]), dim3(COL_ACC_LANES),
                                         args, h->psmem[pr], s));
