@@ -424,6 +424,16 @@ def ours_arm(args):
                     if key in to_tol:
                         n = sum(to_tol[key]["steps"]) if w.batch == 1 else to_tol[key]["steps"][0]
                         to_tol[key]["cpu_oracle_seconds_extrapolated"] = n * w.gridpoints / cpu["value"]
+            # the whole descent against the roofline: algorithmic flops of its steps over its
+            # wall time (read-backs, monitors and extrapolations included); FP64 runs against
+            # the FP64 peak, mixed runs (mostly FP32 steps) reported as achieved only
+            fl = step_flops(nx, nss)
+            for key, v in to_tol.items():
+                if w.batch == 1 and isinstance(v, dict) and v.get("seconds"):
+                    ach = fl * sum(v["steps"]) / v["seconds"] / 1e12
+                    v["achieved_tflops"] = ach
+                    if key.startswith("fp64"):
+                        v["frac_of_fp64_peak"] = ach / PEAK_TFLOPS["f64"]
             line["time_to_tol"] = to_tol
         if fp32:
             line["fp32"] = fp32
