@@ -124,59 +124,67 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     R* const s_lin = s_qv + nkx;
     R* const s_cq = s_lin + nkx;
     RA* const s_lina = reinterpret_cast<RA*>(s_cq + nkx);
-    // Start-up: every load that depends on nothing is issued before any of them is waited on
-    // (the first loop's index, the first entries of the per-mode tables, the twiddles the
-    // launch's transforms read), so they share one round trip to memory instead of one each.  No barrier after the copies: the
-    // tables are first read after the barrier that closes the state load below.
-    const int b_first = (cid < B) ? p.colorder[cid] : 0;
-    R q0 = 0, l0 = 0, c0 = 0;
-    RA la0 = 0;
-    if (tid < nkx) {
-        q0 = p.qv[tid];
-        l0 = p.lin[tid];
-        c0 = p.cq[tid];
-        la0 = ta.lin[tid];
+    // Start-up: the per-mode tables and the twiddles the launch's transforms read are copied
+    // with asynchronous copies (cp_async), which the threads do not wait for; the loop's state
+    // follows the same way, so all of them share one round trip to memory.  They are waited
+    // for before the barrier that closes the state load; the tables are first read after it.
+    // A launch of one loop (B = 1) needs no load to find it: index 0, offsets 0, Ns = nsmax.
+    const bool one = (B == 1);
+    const int b_first = (!one && cid < B) ? p.colorder[cid] : 0;
+    for (int i = tid; i < nkx; i += nt) {
+        cp_async<sizeof(R)>(s_qv + i, p.qv + i);
+        cp_async<sizeof(R)>(s_lin + i, p.lin + i);
+        cp_async<sizeof(R)>(s_cq + i, p.cq + i);
+        cp_async<sizeof(RA)>(s_lina + i, ta.lin + i);
     }
     const int nm = max(nx, cp.nsmax);  // longest transform of the launch
     load_twiddles(tws, p.tw, nm);
     if (!kSame) load_twiddles(tws_a, ta.tw, nm);
-    if (tid < nkx) {
-        s_qv[tid] = q0;
-        s_lin[tid] = l0;
-        s_cq[tid] = c0;
-        s_lina[tid] = la0;
-    }
-    for (int i = tid + nt; i < nkx; i += nt) {
-        s_qv[i] = p.qv[i];
-        s_lin[i] = p.lin[i];
-        s_cq[i] = p.cq[i];
-        s_lina[i] = ta.lin[i];
-    }
 
     for (int bi = cid; bi < B; bi += ncl) {
-        const int b = (bi == cid) ? b_first : p.colorder[bi];
+        const int b = one ? 0 : ((bi == cid) ? b_first : p.colorder[bi]);
         // the skip test and the per-loop scalars in one round of loads; every rank reads the
         // same global words, so the skip is uniform across the cluster
         const int prec_b = p.prec[b], status_b = p.status[b];
-        const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b], nk = 2 * ks + 1;
+        const int ns = one ? cp.nsmax : p.ns[b];
+        const int lg = one ? __ffs(cp.nsmax) - 1 : p.lgns[b];
+        const int ks = one ? cp.nsmax / 3 : p.ks[b];
+        const int nk = 2 * ks + 1;
         const R ins = p.insv[b];
-        const size_t bo = (size_t)p.boff[b];
-        const long long moff_b = p.moff[b], goff_b = p.goff[b];
+        const size_t bo = one ? 0 : (size_t)p.boff[b];
+        const long long moff_b = one ? 0 : p.moff[b], goff_b = one ? 0 : p.goff[b];
         double T = p.T[(size_t)par0 * B + b];
         double wT = p.wT[(size_t)par0 * B + b];
-        if (prec_b != p.myprec || status_b != ST_RUNNING) {
-            if (rank == 0 && tid == 0 && status_b != ST_RUNNING) {
-                p.T[(size_t)(par0 ^ 1) * B + b] = T;
-                p.wT[(size_t)(par0 ^ 1) * B + b] = wT;
-            }
-            continue;
-        }
         const int ncol = (rank < nkx) ? (nkx - rank + C - 1) / C : 0;
         const int rpr = cluster_rows_per_rank(ns, C);
         const int row0 = rank * rpr;
         const int nrow = (row0 < ns) ? min(rpr, ns - row0) : 0;
         cpx<R>* Mg = p.M + moff_b;
         R* Ul = cp.u_global ? p.U + goff_b + (size_t)row0 * nx : Us;
+
+        // ---- the band of the owned columns, and the rows' mixed values (when valid) ----
+        auto load_state = [&]() {
+            for (int i = tid; i < ncol * nk; i += nt) {
+                const int q = i / nk, kk = i - q * nk;
+                cp_async<sizeof(cpx<R>)>(uhl + i, p.uh + bo + (size_t)(rank + q * C) * nk + kk);
+            }
+            if (use_M) {
+                for (int i = tid; i < nkx * nrow; i += nt) {
+                    const int j = i / nrow, r = i - j * nrow;
+                    cp_async<sizeof(cpx<R>)>(Rin + (size_t)j * rmax + r, Mg + (size_t)j * ns + row0 + r);
+                }
+            }
+        };
+        if (one) load_state();  // its addresses need no load: issued with the scalars
+        if (prec_b != p.myprec || status_b != ST_RUNNING) {
+            if (rank == 0 && tid == 0 && status_b != ST_RUNNING) {
+                p.T[(size_t)(par0 ^ 1) * B + b] = T;
+                p.wT[(size_t)(par0 ^ 1) * B + b] = wT;
+            }
+            cp_async_wait();  // no copy may land in shared memory the next loop reuses
+            continue;
+        }
+        if (!one) load_state();
 
         // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)],
         // two rows per store (rows per rank and rmax are even, so a pair has one owner)
@@ -189,46 +197,10 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             }
         };
 
-        // ---- load the band, and the rows' mixed values (or prime them from the band) ----
-        for (int base = tid; base < ncol * nk; base += 4 * nt) {
-            cpx<R> v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = base + u * nt;
-                if (i < ncol * nk) {
-                    const int q = i / nk, kk = i - q * nk;
-                    v[u] = p.uh[bo + (size_t)(rank + q * C) * nk + kk];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = base + u * nt;
-                if (i < ncol * nk) uhl[i] = v[u];
-            }
-        }
-        if (use_M) {
-            for (int base = tid; base < nkx * nrow; base += 4 * nt) {
-                cpx<R> v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = base + u * nt;
-                    if (i < nkx * nrow) {
-                        const int j = i / nrow, r = i - j * nrow;
-                        v[u] = Mg[(size_t)j * ns + row0 + r];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = base + u * nt;
-                    if (i < nkx * nrow) {
-                        const int j = i / nrow, r = i - j * nrow;
-                        Rin[(size_t)j * rmax + r] = v[u];
-                    }
-                }
-            }
-            __syncthreads();
-        } else {
-            __syncthreads();
+        cp_async_wait();
+        __syncthreads();
+        if (!use_M) {
+            // no valid mixed values: prime them from the band (s-inverse of the owned columns)
             for (int i = tid; i < ncol << lg; i += nt) {
                 const int q = i >> lg, n = i & (ns - 1);
                 const int k = (n < (ns >> 1)) ? n : n - ns;
@@ -503,6 +475,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         }
         cl.sync();
     }
+    cp_async_wait();  // a cluster whose loops were all skipped still has its table copies
 }
 
 }  // namespace ks

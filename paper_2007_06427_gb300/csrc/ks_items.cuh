@@ -387,28 +387,31 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
     return a;
 }
 
+// Asynchronous global -> shared copy of N bytes (N = 4, 8 or 16; both addresses N-aligned).
+// The issuing thread does not wait for the data, so copies issued back to back share one round
+// trip to memory; cp_async_wait() waits for all of the thread's copies (a block barrier after
+// it makes them visible to the block).
+template <int N>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
+    static_assert(N == 4 || N == 8 || N == 16, "cp.async copies 4, 8 or 16 bytes");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gsrc), "n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // The twiddles a transform of length n <= nm reads: entries t of exp(2 pi i t / NMAX) with t a
 // multiple of NMAX / n (every pass indexes the table by multiples of NMAX / (4 span) or more, and
-// 4 span <= n), hence of NMAX / nm.  Only those entries are fetched into the shared-memory copy of
-// the table, at their bank-swizzled positions (tw_swz; every transform of the cluster and
-// persistent kernels reads the table through it): the values the transforms read are
-// unchanged, and the bytes fetched drop by NMAX / nm (8x for 128-point columns).
+// 4 span <= n), hence of NMAX / nm.  Only those entries are copied into the shared-memory copy
+// of the table (asynchronously, see cp_async), at their bank-swizzled positions (tw_swz; every
+// transform of the cluster and persistent kernels reads the table through it): the values the
+// transforms read are unchanged, and the bytes fetched drop by NMAX / nm (8x for 128-point
+// columns).
 template <typename X>
 __device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, int nm) {
     const int st = NMAX / nm;
-    for (int base = threadIdx.x; base < nm; base += 4 * blockDim.x) {
-        cpx<X> v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = base + u * blockDim.x;
-            if (i < nm) v[u] = src[(size_t)i * st];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = base + u * blockDim.x;
-            if (i < nm) dst[tw_swz<X>(i * st)] = v[u];
-        }
-    }
+    for (int i = threadIdx.x; i < nm; i += blockDim.x)
+        cp_async<sizeof(cpx<X>)>(dst + tw_swz<X>(i * st), src + (size_t)i * st);
 }
 
 template <typename R, bool SWZ = false>

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(128, 6) k_persist(Dims d, Bufs<R> p, int nstep
     extern __shared__ __align__(16) unsigned char smem[];
     cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem + tw_off);
     load_twiddles(tws, p.tw, nm);
+    cp_async_wait();
     __syncthreads();
     Bufs<R> q = p;
     q.tw = tws;
