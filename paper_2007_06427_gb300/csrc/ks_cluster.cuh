@@ -45,16 +45,20 @@ __host__ __device__ inline int cluster_rows_per_rank(int ns, int C) {
     return r < 2 ? 2 : r;
 }
 
-// FFT of `cnt` columns stored [q][n] at `a` with `b` as scratch (warp-owned transforms); the
-// result is left in `a`.
+// FFT of `cnt` columns stored [q][n] at `a` with `b` as scratch; the result is left in `a`.
+// nthr > 0: a double transform run by the first nthr threads only (see fft_batch), which alone
+// call this; otherwise every thread of the block calls it.
 template <typename R>
 __device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
-                                                const cpx<R>* tw) {
-    cpx<R>* r = fft_warp<R, true>(a, b, lg, cnt, dir, tw);
+                                                const cpx<R>* tw, int nthr = 0) {
+    cpx<R>* r = nthr > 0 ? fft_batch<R, true>(a, b, lg, cnt, dir, tw, nthr)
+                         : fft_warp<R, true>(a, b, lg, cnt, dir, tw);
     if (r != a) {
         const int n = cnt << lg;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = r[i];
-        __syncthreads();
+        const int NT = nthr > 0 ? nthr : (int)blockDim.x;
+        for (int i = threadIdx.x; i < n; i += NT) a[i] = r[i];
+        if (nthr > 0) part_sync(nthr);
+        else __syncthreads();
     }
 }
 
@@ -363,12 +367,12 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
 
             // ======== phase B': J, L2, freeze test, G_hat, update, v = s-inverse (a9, a10) ===
             // The last warp sums the partials and its first lane forms J, L^dag_2 and the next
-            // T, 2 pi / T.  With the adjoint half in float, the s-transform of w_hat runs at the
-            // same time: float transforms are warp-owned, so the last warp owns none for up to
-            // (warps - 1) columns and only joins the transform's closing barrier.  (Its result
-            // is not used when the loop stops at this step.)  A double transform needs every
-            // warp, so there it follows the freeze test as before.
-            constexpr bool kFftFirst = sizeof(RA) == 4;
+            // T, 2 pi / T, while the other warps run the s-transform of w_hat (its result is not
+            // used when the loop stops at this step).  A float transform is warp-owned: the last
+            // warp owns none for up to (warps - 1) columns and only joins its closing barrier.  A
+            // double transform runs on the other warps alone, synchronised by a named barrier
+            // (the block has 128 or 256 threads, so there are other warps).
+            constexpr bool kFloatAdj = sizeof(RA) == 4;
             if (tid >= nt - 32) {
                 double sJ, sL;
                 sum_partials(part, part + nkx, nkx, sJ, sL);
@@ -386,8 +390,10 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     red[2] = 2.0 * 3.14159265358979323846 / Tn;
                     reinterpret_cast<int*>(red + 3)[0] = sv;
                 }
+            } else if constexpr (!kFloatAdj) {
+                if (ncol > 0) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a, nt - 32);
             }
-            if (kFftFirst && ncol > 0) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
+            if (kFloatAdj && ncol > 0) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
             __syncthreads();
             const double J = red[0], Tnext = red[1], wTnext = red[2];
             st = reinterpret_cast<const int*>(red + 3)[0];
@@ -395,7 +401,6 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             Jlast = J;
             if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
             if (ncol > 0) {
-                if (!kFftFirst) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;

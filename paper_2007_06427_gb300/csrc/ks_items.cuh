@@ -253,9 +253,28 @@ KS_HD cpx<R> twid(const cpx<R>* tw, int t, int dir) {
     return w;
 }
 
+// Barrier of the first nthr threads of the block (a multiple of 32): a plain block barrier when
+// that is the whole block, else named barrier 1, which the other warps never use.
+KS_HD void part_sync(int nthr) {
+#ifdef KS_HOST_EMULATION
+    (void)nthr;
+#else
+    if (nthr == (int)blockDim.x) __syncthreads();
+    else asm volatile("bar.sync 1, %0;\n" ::"r"(nthr) : "memory");
+#endif
+}
+
 // SWZ: the table is the swizzled shared-memory copy (see tw_swz); the global table is not.
+// nthr > 0: only the first nthr threads (a multiple of 32) run the transform and meet at
+// part_sync(nthr); every one of them must call it.  The arithmetic is the same either way.
 template <typename R, bool SWZ = false>
-KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw) {
+KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
+                        int nthr = 0) {
+#ifdef KS_HOST_EMULATION
+    const int NT = KS_NT;
+#else
+    const int NT = nthr > 0 ? nthr : KS_NT;
+#endif
     const int n = 1 << lg;
     int span = 1;  // size of the sub-transforms completed so far
     int p = lg;
@@ -263,7 +282,7 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
         // radix-2 pass with span 1: no twiddles
         const int nb = n >> 1;
         const int total = cnt * nb;
-        for (int i = KS_TID; i < total; i += KS_NT) {
+        for (int i = KS_TID; i < total; i += NT) {
             const int f = i >> (lg - 1);
             const int j = i & (nb - 1);
             const cpx<R>* s = a + (size_t)f * n;
@@ -272,7 +291,8 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
             d[2 * j] = v0 + v1;
             d[2 * j + 1] = v0 - v1;
         }
-        KS_SYNC();
+        if (nthr > 0) part_sync(nthr);
+        else KS_SYNC();
         cpx<R>* t = a;
         a = b;
         b = t;
@@ -283,7 +303,7 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
         const int nb = n >> 2;
         const int total = cnt * nb;
         const int tu = NMAX / (span * 4);
-        for (int i = KS_TID; i < total; i += KS_NT) {
+        for (int i = KS_TID; i < total; i += NT) {
             const int f = i >> (lg - 2);
             const int j = i & (nb - 1);
             const cpx<R>* s = a + (size_t)f * n;
@@ -304,7 +324,8 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
             d[od + 2 * span] = t0 - t2;
             d[od + 3 * span] = t1 - t3;
         }
-        KS_SYNC();
+        if (nthr > 0) part_sync(nthr);
+        else KS_SYNC();
         cpx<R>* t = a;
         a = b;
         b = t;

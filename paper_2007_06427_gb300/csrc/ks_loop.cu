@@ -1882,8 +1882,15 @@ bool cache_lookup(const std::string& key, TuneChoice& c) {
         std::string ln(line);
         const size_t bar = ln.find('|');
         if (bar == std::string::npos || ln.substr(0, bar) != key) continue;
-        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d", &c.path, &c.cluster, &c.threads) == 3)
+        TuneChoice t{};
+        // only the launch shapes the tuner itself tries (the cluster kernel needs 128 or 256
+        // threads: its phase B' splits the block into the last warp and the rest)
+        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d", &t.path, &t.cluster, &t.threads) == 3 &&
+            t.path >= 0 && t.path <= 2 && t.cluster >= 0 && t.cluster <= 16 &&
+            (t.threads == 128 || t.threads == 256)) {
+            c = t;
             found = true;
+        }
     }
     std::fclose(f);
     return found;
