@@ -41,3 +41,22 @@ def test_tuned_handle_reproduces_default(mode, tmp_path, monkeypatch):
     with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15, autotune=1) as h:
         pass
     assert len(open(tmp_path / "tune.txt").read().strip().splitlines()) == 1
+
+
+def test_invalid_cache_entry_is_ignored(tmp_path, monkeypatch):
+    """A cache line naming a launch shape the tuner never tries (here 32 threads, which the
+    cluster kernel cannot run) is ignored: the handle times the candidates again and appends a
+    valid entry."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("KS_AUTOTUNE_CACHE", str(cache))
+    L, nx, nss = 22.0, 32, [32]
+    with K.KSLoop(L, nx, nss, K.KS_FP64, K.KS_IMEX, 0.15, autotune=1):
+        pass
+    key, choice = cache.read_text().strip().split("|")
+    path, cluster, threads = map(int, choice.split())
+    cache.write_text(f"{key}|0 {cluster} 32\n")
+    with K.KSLoop(L, nx, nss, K.KS_FP64, K.KS_IMEX, 0.15, autotune=1) as h:
+        assert K.ks_get_option(h.handle, "cluster_threads") in (128, 256)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 2 and lines[0].endswith(" 32")
+    assert int(lines[1].split("|")[1].split()[2]) in (128, 256)
