@@ -32,3 +32,49 @@ def test_reference_arm_other_ranks_exit_quietly():
                           "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
                          timeout=300, cwd=ROOT, env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_roofline_entry_arithmetic():
+    """The roofline of the dominant kernel: its launch time is the timed step time times its
+    share of the profiled device time, its work the flop model; the cluster kernel's entry also
+    carries the fraction of the peak of the SMs it occupies."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class W:
+        name, batch, nx, ns = "single_64x128_imex", 1, 64, [128]
+
+    prof = {"cluster_f64": (2.0, 20), "prep": (0.02, 1)}   # ms, launches in the profiled pass
+    roof = bench.roofline_entry(prof, 0.05, W, 64, [128])
+    share = 2.0 / 2.02
+    assert roof["kernel"] == "cluster_f64" and abs(roof["share"] - share) < 1e-12
+    ms = 0.05 * share / (20 / bench.PROFILE_STEPS)
+    assert abs(roof["ms_per_launch"] - ms) < 1e-12
+    fl = bench.kernel_flops("cluster_f64", 64, [128])
+    assert abs(roof["achieved"] - fl / (ms / 1e3) / 1e12) < 1e-12
+    assert roof["peak"] == bench.PEAK_TFLOPS["f64"] and roof["bound"] == "alu"
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-15
+    # the flop model of one tau-step: five 2-D transforms plus the pointwise terms
+    assert fl == bench.step_flops(64, [128]) and 1.0e6 < fl < 1.3e6
+
+    class FakeK:
+        KS_FP32 = 1
+
+        @staticmethod
+        def ks_get_option(handle, key):
+            return {"path": 0, "cluster_f64": 16}[key]
+
+    class H:
+        handle = None
+
+    class Props:
+        multi_processor_count = 152
+
+    import torch
+    orig = torch.cuda.get_device_properties
+    torch.cuda.get_device_properties = lambda dev: Props()
+    try:
+        r2 = bench.annotate_sms(dict(roof), FakeK, H, 0, 1, None)
+    finally:
+        torch.cuda.get_device_properties = orig
+    assert r2["sms_used"] == 16 and abs(r2["frac_of_sms_used"] - roof["frac"] * 152 / 16) < 1e-15
