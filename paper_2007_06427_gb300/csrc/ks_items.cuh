@@ -209,6 +209,8 @@ struct Bufs {
     double switch_tol;      // float phase of a mixed descent: freeze as ST_SWITCH once sqrt(J) <= switch_tol
     int check_active;       // 1: skip loops that are not running in this precision
     int xi;                 // 1: descent restricted to the Xi-invariant (centre-symmetric) subspace
+    int twsh;               // tw is a compact swizzled shared-memory table: entry t at
+                            // tw_swz(t >> twsh) (see load_twiddles_compact); 0 otherwise
 };
 
 // Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 4.1, the
@@ -247,8 +249,8 @@ KS_HD int tw_swz(int t) {
 }
 
 template <typename R, bool SWZ = false>
-KS_HD cpx<R> twid(const cpx<R>* tw, int t, int dir) {
-    cpx<R> w = tw[SWZ ? tw_swz<R>(t) : t];
+KS_HD cpx<R> twid(const cpx<R>* tw, int t, int dir, int sh = 0) {
+    cpx<R> w = tw[SWZ ? tw_swz<R>(t >> sh) : t];
     if (dir < 0) w.y = -w.y;
     return w;
 }
@@ -267,9 +269,10 @@ KS_HD void part_sync(int nthr) {
 // SWZ: the table is the swizzled shared-memory copy (see tw_swz); the global table is not.
 // nthr > 0: only the first nthr threads (a multiple of 32) run the transform and meet at
 // part_sync(nthr); every one of them must call it.  The arithmetic is the same either way.
+// twsh: the swizzled table is compact (entry t at tw_swz(t >> twsh)).
 template <typename R, bool SWZ = false>
 KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
-                        int nthr = 0) {
+                        int nthr = 0, int twsh = 0) {
 #ifdef KS_HOST_EMULATION
     const int NT = KS_NT;
 #else
@@ -312,9 +315,9 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
             const int jm = j & (span - 1);
             if (span > 1) {
                 const int t = jm * tu;
-                v1 = cmul(v1, twid<R, SWZ>(tw, t, dir));
-                v2 = cmul(v2, twid<R, SWZ>(tw, 2 * t, dir));
-                v3 = cmul(v3, twid<R, SWZ>(tw, 3 * t, dir));
+                v1 = cmul(v1, twid<R, SWZ>(tw, t, dir, twsh));
+                v2 = cmul(v2, twid<R, SWZ>(tw, 2 * t, dir, twsh));
+                v3 = cmul(v3, twid<R, SWZ>(tw, 3 * t, dir, twsh));
             }
             const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
             const cpx<R> t3 = mul_i(v1 - v3, dir);
@@ -433,6 +436,16 @@ __device__ __forceinline__ void load_twiddles(cpx<X>* dst, const cpx<X>* src, in
     const int st = NMAX / nm;
     for (int i = threadIdx.x; i < nm; i += blockDim.x)
         cp_async<sizeof(cpx<X>)>(dst + tw_swz<X>(i * st), src + (size_t)i * st);
+}
+
+// The same entries in a compact table of nm slots: entry t = i NMAX / nm at slot tw_swz(i).  The
+// transforms read it with twsh = log2(NMAX / nm).  The strides a pass reads are again powers of
+// two, which the swizzle spreads over the banks as before.
+template <typename X>
+__device__ __forceinline__ void load_twiddles_compact(cpx<X>* dst, const cpx<X>* src, int nm) {
+    const int st = NMAX / nm;
+    for (int i = threadIdx.x; i < nm; i += blockDim.x)
+        cp_async<sizeof(cpx<X>)>(dst + tw_swz<X>(i), src + (size_t)i * st);
 }
 
 template <typename R, bool SWZ = false>
@@ -806,13 +819,13 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = mk<R>(ra[m], ra[nx + m]);
         }
         KS_SYNC();
-        cpx<R>* Y = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, -1, p.tw);
+        cpx<R>* Y = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, Y, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_SYNTH) {
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw);
+        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
         const int total = npairs * nx;
         for (int i = KS_TID; i < total; i += KS_NT) {
             const int pr = i >> lgnx;
@@ -838,7 +851,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[(size_t)r * nx + J] = z;
         }
         KS_SYNC();
-        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, nr, +1, p.tw);
+        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, nr, +1, p.tw, 0, p.twsh);
         cpx<R>* Y = (z == A) ? Bf : A;
         // keep u, form p = u u_x for the row pairs (a3)
         const int tp = npairs * nx;
@@ -853,14 +866,14 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
         }
         KS_SYNC();
-        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw);  // a4 (x-pass)
+        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_ADJ) {
         // r_x rows from the column pass output rho = s-inverse of i q_j r_hat   (a7)
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw);
+        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
         cpx<R>* Y = (z == A) ? Bf : A;
         const int tp = npairs * nx;
         for (int i = KS_TID; i < tp; i += KS_NT) {
@@ -871,7 +884,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(ua[m] * rx.x, ua[nx + m] * rx.y);  // w = u r_x  (a8)
         }
         KS_SYNC();
-        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw);
+        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     }
@@ -941,14 +954,14 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = (k >= -ks && k <= ks) ? src[bo + (k + ks)] : mk<R>(0, 0);
         }
         KS_SYNC();
-        cpx<R>* v = fft_batch<R, SWZ>(A, Bf, lg, 1, +1, p.tw);
+        cpx<R>* v = fft_batch<R, SWZ>(A, Bf, lg, 1, +1, p.tw, 0, p.twsh);
         for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
         KS_SYNC();
     } else {
         // the remaining modes start with a forward s-transform of the column of M
         for (int i = KS_TID; i < ns; i += KS_NT) A[i] = col[i];
         KS_SYNC();
-        cpx<R>* F = fft_batch<R, SWZ>(A, Bf, lg, 1, -1, p.tw);
+        cpx<R>* F = fft_batch<R, SWZ>(A, Bf, lg, 1, -1, p.tw, 0, p.twsh);
         cpx<R>* X = (F == A) ? Bf : A;
         const R ins = p.insv[b];
 
@@ -986,7 +999,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 X[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch<R, SWZ>(X, F, lg, 1, +1, p.tw);
+            cpx<R>* v = fft_batch<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             block_reduce(acc, red);
             if (KS_TID == 0) {
@@ -1092,7 +1105,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 Y[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch<R, SWZ>(Y, p.xi ? X : F, lg, 1, +1, p.tw);
+            cpx<R>* v = fft_batch<R, SWZ>(Y, p.xi ? X : F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             if (j == 0 && KS_TID == 0) {
                 const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)

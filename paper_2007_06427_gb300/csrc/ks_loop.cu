@@ -25,16 +25,34 @@ using namespace ks;
 // ------------------------------------------------------------------------------------------
 // Kernels
 // ------------------------------------------------------------------------------------------
-template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_rows(Dims d, Bufs<R> p, int nitems) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) row_item<R, MODE>(d, p, it, smem);
+// Per-phase launches.  Each CTA first copies the twiddles its transforms read (nm entries,
+// nm = the longest transform) into a compact bank-swizzled table at tw_off, after its item
+// buffers; the items read them there (the same values as the global table: the same bits).
+template <typename R>
+__device__ __forceinline__ Bufs<R> stage_twiddles(const Bufs<R>& p, unsigned char* smem,
+                                                  int tw_off, int nm) {
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem + tw_off);
+    load_twiddles_compact(tws, p.tw, nm);
+    cp_async_wait();
+    __syncthreads();
+    Bufs<R> q = p;
+    q.tw = tws;
+    q.twsh = __ffs(NMAX / nm) - 1;
+    return q;
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_cols(Dims d, Bufs<R> p, int nitems) {
+__global__ void __launch_bounds__(256) k_rows(Dims d, Bufs<R> p, int nitems, int tw_off, int nm) {
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) col_item<R, MODE>(d, p, it, smem, p.par);
+    const Bufs<R> q = stage_twiddles(p, smem, tw_off, nm);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) row_item<R, MODE, true>(d, q, it, smem);
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_cols(Dims d, Bufs<R> p, int nitems, int tw_off, int nm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Bufs<R> q = stage_twiddles(p, smem, tw_off, nm);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) col_item<R, MODE, true>(d, q, it, smem, q.par);
 }
 
 // float grid -> double grid
@@ -243,7 +261,8 @@ struct Work {
 struct Launch {
     int threads = 128;
     int grid = 0;
-    size_t smem = 0;
+    size_t smem = 0;    // item buffers plus the compact twiddle table
+    size_t tw_off = 0;  // the item buffers' size: offset of the twiddle table
 };
 
 }  // namespace
@@ -525,7 +544,8 @@ int launch_rows(ks_loop* h, const Bufs<R>& p, cudaStream_t s) {
     const Launch& l = h->lrow[pr];
     const int n = (int)h->rows.size();
     LaunchScope ls(h, s, std::string(kRowNames[MODE]) + prec_suffix(pr));
-    k_rows<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n);
+    k_rows<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n, (int)l.tw_off,
+                                                                     std::max(h->d.nx, h->nsmax));
     KS_CUDA(cudaGetLastError());
     ls.done();
     return KS_OK;
@@ -537,7 +557,8 @@ int launch_cols(ks_loop* h, const Bufs<R>& p, cudaStream_t s) {
     const Launch& l = h->lcol[pr];
     const int n = h->d.B * h->d.nkx;
     LaunchScope ls(h, s, std::string(kColNames[MODE]) + prec_suffix(pr));
-    k_cols<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n);
+    k_cols<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n, (int)l.tw_off,
+                                                                     std::max(h->d.nx, h->nsmax));
     KS_CUDA(cudaGetLastError());
     ls.done();
     return KS_OK;
@@ -569,7 +590,7 @@ template <typename R>
 int setup_persistent(ks_loop* h) {
     const int pr = std::is_same<R, double>::value ? P64 : P32;
     // the items' buffers, then the twiddle table (NMAX entries, swizzled positions)
-    const size_t items_sm = (std::max(h->lrow[pr].smem, h->lcol[pr].smem) + 15) & ~(size_t)15;
+    const size_t items_sm = std::max(h->lrow[pr].tw_off, h->lcol[pr].tw_off);  // 16-aligned
     const size_t sm = items_sm + (size_t)NMAX * sizeof(cpx<R>);
     h->ptw_off[pr] = (int)items_sm;
     KS_CUDA(cudaFuncSetAttribute(k_persist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1044,13 +1065,16 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     // launch shapes
     for (int pr = 0; pr < 2; ++pr) {
         const size_t cs = pr == P64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+        const size_t tw_bytes = (size_t)std::max(h->d.nx, h->nsmax) * cs;  // compact table
         Launch& lr = h->lrow[pr];
         lr.threads = 128;
-        lr.smem = 2 * (size_t)h->rows_per_tile * h->d.nx * cs;
+        lr.tw_off = (2 * (size_t)h->rows_per_tile * h->d.nx * cs + 15) & ~(size_t)15;
+        lr.smem = lr.tw_off + tw_bytes;
         lr.grid = 152 * 16;
         Launch& lc = h->lcol[pr];
         lc.threads = COL_ACC_LANES;  // the column partials' accumulation width (ks_items.cuh)
-        lc.smem = 2 * (size_t)h->nsmax * cs + COL_RED_DOUBLES * sizeof(double);
+        lc.tw_off = (2 * (size_t)h->nsmax * cs + COL_RED_DOUBLES * sizeof(double) + 15) & ~(size_t)15;
+        lc.smem = lc.tw_off + tw_bytes;
         lc.grid = 152 * 16;
     }
     if ((rc = set_smem_attrs<double>(h)) || (rc = set_smem_attrs<float>(h))) return cleanup(rc);

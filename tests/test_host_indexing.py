@@ -76,3 +76,32 @@ def test_swizzle_spreads_the_radix4_twiddle_loads(positions, esize):
         stats[name] = (worst, total / count)
     assert stats["plain"][0] >= 8
     assert stats["swizzled"][0] <= 3 and stats["swizzled"][1] < 1.5, stats
+
+
+@pytest.mark.parametrize("esize", [16, 8])
+@pytest.mark.parametrize("nm", [16, 64, 128, 256, 1024])
+def test_compact_swizzled_table(positions, esize, nm):
+    """The per-phase launches' compact table: entry t = i NMAX / nm at slot tw_swz(i), read with
+    t >> log2(NMAX / nm).  The slots are a permutation of 0 .. nm-1, and the radix-4 passes of
+    every length up to nm stay spread over the banks."""
+    pos = positions[esize]
+    sh = (NMAX // nm).bit_length() - 1
+    slots = [pos[i] for i in range(nm)]
+    assert sorted(slots) == list(range(nm))
+    lanes = 128 // esize
+    worst, total, count = 0, 0, 0
+    for lg in range(3, nm.bit_length()):
+        n = 1 << lg
+        span = 2 if lg & 1 else 1
+        while span * 4 <= n:
+            if span > 1:
+                tu = NMAX // (span * 4)
+                for mult in (1, 2, 3):
+                    for base in range(0, 32, lanes):
+                        addrs = [pos[(mult * ((l % (n // 4)) & (span - 1)) * tu) >> sh] * esize
+                                 for l in range(base, base + lanes)]
+                        w = _conflict_degree(addrs, esize)
+                        worst, total, count = max(worst, w), total + w, count + 1
+            span *= 4
+    if count:
+        assert worst <= 3 and total / count < 1.6, (worst, total / count)
