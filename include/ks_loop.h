@@ -278,7 +278,8 @@ KS_API int ks_residual_noalloc(double L, int nx, int ns, const double* u, double
  * fits, with 128 and 256 threads per CTA; grid-persistent kernel; four launches per step) on a
  * synthetic band-limited state and keep the fastest for the precision the descent spends its
  * bulk in.  If the environment variable KS_AUTOTUNE_CACHE names a file, choices are read from
- * and appended to it, keyed by Nx, the Ns list, the batch size, the mode and the scheme.
+ * and appended to it, keyed by Nx, the Ns list, the batch size, the mode and the scheme; a
+ * line naming a shape the tuner does not try (e.g. another thread count) is ignored.
  * Clears the resident state (call ks_set_state afterwards).  All candidates give the same
  * results bit for bit; only the time differs. */
 KS_API int ks_autotune(ks_loop_t h);
