@@ -427,10 +427,11 @@ def ours_arm(args):
             # the whole descent against the roofline: algorithmic flops of its steps over its
             # wall time (read-backs, monitors and extrapolations included); FP64 runs against
             # the FP64 peak, mixed runs (mostly FP32 steps) reported as achieved only
-            fl = step_flops(nx, nss)
+            # flops per loop-step (mean over the batch; exact for a single loop or equal Ns)
+            fl = step_flops(nx, nss) / w.batch
             for key, v in to_tol.items():
-                if w.batch == 1 and isinstance(v, dict) and v.get("seconds"):
-                    ach = fl * sum(v["steps"]) / v["seconds"] / 1e12
+                if isinstance(v, dict) and v.get("seconds") and len(set(nss)) == 1:
+                    ach = fl * v["total_steps"] / v["seconds"] / 1e12
                     v["achieved_tflops"] = ach
                     if key.startswith("fp64"):
                         v["frac_of_fp64_peak"] = ach / PEAK_TFLOPS["f64"]
@@ -538,6 +539,15 @@ def throughput_fp32(args, w, dev, flush, K):
     return out
 
 
+def outcome_counts(K, st):
+    """Loops of the batch per final status (converged, step cap, stalled, diverged)."""
+    out = {}
+    for v in st.tolist():
+        name = K.STATUS_NAMES.get(int(v), str(int(v)))
+        out[name] = out.get(name, 0) + 1
+    return out
+
+
 def run_to_tol(args, w, dev):
     """Plain FP64 descent vs FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol;
     then both again with the extrapolation of App. C inside ks_descend."""
@@ -569,6 +579,7 @@ def run_to_tol(args, w, dev):
         switch = int(hs[np.nonzero(hp == 0)[0][0]]) if (name == "mixed" and (hp == 0).any()) else None
         out[name] = {"seconds": el, "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8],
                      "status": [K.STATUS_NAMES.get(int(s), str(int(s))) for s in st.tolist()[:8]],
+                     "outcomes": outcome_counts(K, st), "total_steps": int(steps.sum().item()),
                      "T": T.tolist()[:8], "loop0_first_step_below": marks,
                      "loop0_switch_step": switch,
                      "loop0_history": [[int(a), float(c)] for a, c in zip(hs[::max(1, len(hs) // 40)], hq[::max(1, len(hq) // 40)])]}
@@ -595,6 +606,7 @@ def run_to_tol(args, w, dev):
         switch = int(hs[np.nonzero(hp == 0)[0][0]]) if (mode == K.KS_MIXED and (hp == 0).any()) else None
         out[name] = {"seconds": el, "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8],
                      "status": [K.STATUS_NAMES.get(int(v), str(int(v))) for v in st.tolist()[:8]],
+                     "outcomes": outcome_counts(K, st), "total_steps": int(steps.sum().item()),
                      "T": T.tolist()[:8],
                      "extrapolations": K.ks_get_option(h.handle, "extrapolations"),
                      "rejected": K.ks_get_option(h.handle, "extrapolations_rejected"),
