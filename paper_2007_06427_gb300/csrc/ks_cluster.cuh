@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         };
         if (one) load_state();  // its addresses need no load: issued with the scalars
         if (prec_b != p.myprec || status_b != ST_RUNNING) {
-            if (rank == 0 && tid == 0 && status_b != ST_RUNNING) {
+            if (rank == 0 && tid == 0 && status_b != ST_RUNNING &&
+                (prec_b == p.myprec || !p.own_frozen_only)) {
                 p.T[(size_t)(par0 ^ 1) * B + b] = T;
                 p.wT[(size_t)(par0 ^ 1) * B + b] = wT;
             }

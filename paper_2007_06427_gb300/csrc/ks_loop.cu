@@ -336,6 +336,10 @@ struct ks_loop {
     struct Rec { int kind; cudaEvent_t a, b; };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
+    // a second stream for the double-precision cluster launch of a mixed batch, so that it runs
+    // beside the float one (created on first use; non-blocking, ordered by the two events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // convergence history recorded by ks_descend at every read-back: (steps, sqrtJ, prec)
     std::vector<std::vector<long long>> hist_steps;
     std::vector<std::vector<double>> hist_sqrtJ;
@@ -705,8 +709,9 @@ int setup_cluster(ks_loop* h) {
 // nsteps tau-steps of the live loops of precision pr, one cluster per loop
 template <typename R, typename RA>
 int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, double switch_tol,
-                cudaStream_t s) {
+                cudaStream_t s, bool concurrent = false) {
     Bufs<R> p = make_bufs<R>(h, w, pr, 1, tol, switch_tol, (R*)nullptr);
+    p.own_frozen_only = concurrent ? 1 : 0;
     const int slot = std::is_same<R, RA>::value ? pr : 2;
     const int pa = std::is_same<RA, double>::value ? P64 : P32;
     AdjTables<RA> ta{(const cpx<RA>*)h->d_tw[pa], (const RA*)h->d_qv[pa], (const RA*)h->d_lin[pa]};
@@ -1102,6 +1107,9 @@ extern "C" int ks_destroy(ks_loop_t h) {
         cudaEventDestroy(r.b);
     }
     for (auto e : h->pool) cudaEventDestroy(e);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->side) cudaStreamDestroy(h->side);
     for (void* p : h->allocs) cudaFree(p);
     delete h;
     return KS_OK;
@@ -1273,14 +1281,34 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_
     const long long kMaxPerLaunch = 1 << 14;
     const bool clus[2] = {h->path == 0 && h->cplan[P64].bytes > 0, h->path == 0 && h->cplan[P32].bytes > 0};
     if ((!live[P32] || clus[P32]) && (!live[P64] || clus[P64])) {
+        // With loops live in both precisions (a mixed batch in mid-switch) the two launches
+        // touch disjoint loops: the double one runs on the side stream, concurrently, and each
+        // carries T forward only for the frozen loops of its own precision (a loop that
+        // freezes during the chunk is written by its own kernel alone).
+        const bool both = live[P32] && live[P64] && !h->prof;
+        if (both && !h->side) {
+            KS_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+            KS_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+            KS_CUDA(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+        }
         for (long long done = 0; done < n;) {
             const long long c = std::min(kMaxPerLaunch, n - done);
-            if (live[P32]) KS_TRY((run_cluster<float, float>(h, w, P32, c, tol, swt, s)));
+            cudaStream_t s64 = s;
+            if (both) {
+                KS_CUDA(cudaEventRecord(h->fork, s));
+                KS_CUDA(cudaStreamWaitEvent(h->side, h->fork, 0));
+                s64 = h->side;
+            }
+            if (live[P32]) KS_TRY((run_cluster<float, float>(h, w, P32, c, tol, swt, s, both)));
             if (live[P64]) {
                 if (h->mode == KS_MIXED && h->finish_f32_adjoint && h->cplan[2].bytes > 0)
-                    KS_TRY((run_cluster<double, float>(h, w, P64, c, tol, 0.0, s)));
+                    KS_TRY((run_cluster<double, float>(h, w, P64, c, tol, 0.0, s64, both)));
                 else
-                    KS_TRY((run_cluster<double, double>(h, w, P64, c, tol, 0.0, s)));
+                    KS_TRY((run_cluster<double, double>(h, w, P64, c, tol, 0.0, s64, both)));
+            }
+            if (both) {
+                KS_CUDA(cudaEventRecord(h->join, h->side));
+                KS_CUDA(cudaStreamWaitEvent(s, h->join, 0));
             }
             if (c & 1) w.par ^= 1;
             done += c;

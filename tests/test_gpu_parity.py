@@ -315,3 +315,31 @@ def test_mixed_descent_starts_below_float_floor_in_double():
     assert np.sqrt(J0.item()) < 1e-6
     assert hp[0] == 0                                       # double from the first chunk
     assert sq.item() <= np.sqrt(J0.item())
+
+
+def test_mixed_batch_concurrent_precisions_equal_sequential():
+    """While a mixed batch has loops in both precisions, the float and double cluster launches
+    run concurrently on two streams (each carrying T only for its own frozen loops).  With the
+    library's profiling on they run one after the other; the results agree bit for bit."""
+    L, nx, nss = 22.0, 32, [32, 32, 64, 32]
+    us, Ts = make(nx, nss, L, T_range=(30.0, 50.0))
+    us = [a * s for a, s in zip(us, (1e-2, 3e-3, 1e-2, 1.0))]   # loops that switch at different times
+    outs = []
+    for prof in (False, True):
+        u, T = dev_tensors(us, Ts, K.KS_FP64)
+        steps = torch.zeros(4, dtype=torch.int64, device="cuda")
+        sq = torch.zeros(4, dtype=torch.float64, device="cuda")
+        st = torch.zeros(4, dtype=torch.int32, device="cuda")
+        with K.KSLoop(L, nx, nss, K.KS_MIXED, K.KS_IMEX, 0.15, tol=1e-10, switch_tol=1e-5,
+                      chunk=500) as h:
+            K.ks_profile(h.handle, prof)
+            K.ks_descend(h.handle, u, T, 60000, 1e-10, steps, sq, st)
+            hp = [K.ks_get_history(h.handle, b)[2] for b in range(4)]
+        outs.append((u.cpu(), T.cpu(), steps.cpu(), st.cpu()))
+        # at some read-back one loop was in float while another was in double
+        mixed_phase = any((hp[a][i] == 1) and (hp[b][i] == 0)
+                          for a in range(4) for b in range(4)
+                          for i in range(min(len(hp[a]), len(hp[b]))))
+        assert mixed_phase
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
