@@ -24,7 +24,7 @@ Host-side preprocessing (NumPy); the loops it returns are inputs for the GPU des
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import List, Optional, Sequence
+from typing import List, Optional
 
 import numpy as np
 

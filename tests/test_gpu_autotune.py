@@ -1,7 +1,6 @@
 """The autotuner picks a launch shape by timing; every candidate computes the same thing, so a
 tuned handle reproduces an untuned one bit for bit.  The on-disk cache is written once and
 reused."""
-import os
 
 import numpy as np
 import pytest
