@@ -1,0 +1,67 @@
+"""The per-CTA work items of the per-phase launches (ks_items.cuh), compiled as sequential host
+code (KS_HOST_EMULATION) by tests/host/ks_host_step.cpp, against the oracle: analysis of a grid
+loop onto its band, tau-steps through the four phases, synthesis back to the grid.  No GPU: this
+pins the items' index arithmetic and formulas on the CPU.  The GPU tests check that the cluster
+and persistent kernels reproduce these items bit for bit."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import ks_oracle as ko
+from paper_2007_06427_gb300 import build as B
+from paper_2007_06427_gb300.inputs import spectral_loop
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path_factory.mktemp("items") / "ks_host_step"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", B.CSRC,
+                    os.path.join(HERE, "host", "ks_host_step.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+def run(exe, u, T, L, dtau, scheme, steps):
+    ns, nx = u.shape
+    inp = f"{L!r} {nx} {ns} {float(T)!r} {dtau!r} {scheme} {steps}\n"
+    inp += "\n".join(repr(float(x)) for x in u.ravel())
+    out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
+    return float(out[0]), float(out[1]), np.array(list(map(float, out[2:]))).reshape(ns, nx)
+
+
+@pytest.mark.parametrize("nx,ns,L,scheme,dtau,steps", [
+    (32, 32, 22.0, ko.IMEX, 0.15, 5),
+    (32, 64, 22.0, ko.IMEX, 0.15, 3),
+    (64, 32, 39.0, ko.IMEX, 0.15, 4),
+    (16, 16, 22.0, ko.EXPLICIT, 1e-3, 3),
+    (8, 8, 22.0, ko.IMEX, 0.15, 2),
+    (16, 128, 22.0, ko.IMEX, 0.15, 2),
+])
+def test_items_step_matches_oracle(harness, nx, ns, L, scheme, dtau, steps):
+    u, T, _ = spectral_loop(1, nx, L, ns=ns, T_range=(30.0, 50.0))
+    sq0, Tn, g = run(harness, u, T, L, dtau, scheme, steps)
+    ref = ko.descend(u, T, L, dtau, scheme, steps)
+    J0 = ko.residual(u, T, L)["J"]
+    assert abs(sq0 - np.sqrt(J0)) <= 1e-12 * np.sqrt(J0)
+    assert np.linalg.norm(g - ref["u"]) <= 1e-12 * np.linalg.norm(ref["u"])
+    assert abs(Tn - ref["T"]) <= 1e-12 * abs(ref["T"])
+    assert ref["T"] != T and np.linalg.norm(ref["u"] - u) > 1e-6 * np.linalg.norm(u)
+
+
+def test_items_analysis_synthesis_is_the_band_projection(harness):
+    """Zero steps: analysis then synthesis returns the band-limited part of the loop."""
+    u, T, _ = spectral_loop(2, 32, 22.0, ns=64, T_range=(30.0, 50.0))
+    noise = np.random.default_rng(0).standard_normal(u.shape)   # energy outside the band too
+    v = u + 0.1 * noise
+    _, Tn, g = run(harness, v, T, 22.0, 0.15, ko.IMEX, 0)
+    ref = ko.descend(v, T, 22.0, 0.15, ko.IMEX, 0)["u"]
+    assert Tn == T
+    assert np.linalg.norm(g - ref) <= 1e-13 * np.linalg.norm(ref)
+    assert np.linalg.norm(g - v) > 1e-3 * np.linalg.norm(v)
