@@ -1,6 +1,7 @@
 """The per-CTA work items of the per-phase launches (ks_items.cuh), compiled as sequential host
 code (KS_HOST_EMULATION) by tests/host/ks_host_step.cpp, against the oracle: analysis of a grid
-loop onto its band, tau-steps through the four phases, synthesis back to the grid.  No GPU: this
+loop onto its band, tau-steps through the four phases or the residual and adjoint gradient,
+synthesis back to the grid; in double and in float, plain and in the centre-symmetric subspace.  No GPU: this
 pins the items' index arithmetic and formulas on the CPU.  The GPU tests check that the cluster
 and persistent kernels reproduce these items bit for bit."""
 import os
@@ -28,9 +29,9 @@ def harness(tmp_path_factory):
     return str(exe)
 
 
-def run(exe, u, T, L, dtau, scheme, steps):
+def run(exe, u, T, L, dtau, scheme, steps, mode=0, prec=64, xi=0):
     ns, nx = u.shape
-    inp = f"{L!r} {nx} {ns} {float(T)!r} {dtau!r} {scheme} {steps}\n"
+    inp = f"{L!r} {nx} {ns} {float(T)!r} {dtau!r} {scheme} {steps} {mode} {prec} {xi}\n"
     inp += "\n".join(repr(float(x)) for x in u.ravel())
     out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
     return float(out[0]), float(out[1]), np.array(list(map(float, out[2:]))).reshape(ns, nx)
@@ -65,3 +66,47 @@ def test_items_analysis_synthesis_is_the_band_projection(harness):
     assert Tn == T
     assert np.linalg.norm(g - ref) <= 1e-13 * np.linalg.norm(ref)
     assert np.linalg.norm(g - v) > 1e-3 * np.linalg.norm(v)
+
+
+SHAPES = [(32, 32, 22.0), (32, 64, 22.0), (64, 32, 39.0), (16, 128, 22.0)]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("nx,ns,L", SHAPES)
+@pytest.mark.parametrize("xi", [0, 1])
+def test_items_gradient_matches_oracle_fp64(harness, nx, ns, L, xi):
+    """r, J, G = L^dag_1 r and dJ/dT (Eq. KS_R, Eq. KS_L_dagger) within 1e-12."""
+    u, T, _ = spectral_loop(1, nx, L, ns=ns, T_range=(30.0, 50.0), symmetric=bool(xi))
+    J, dJdT, G = run(harness, u, T, L, 0.15, ko.IMEX, 0, mode=1, prec=64, xi=xi)
+    ref = ko.adjoint_grad(u, T, L, xi=bool(xi))
+    assert rel(G, ref["G"]) <= 1e-12
+    assert abs(J - ref["J"]) <= 1e-12 * ref["J"]
+    assert abs(dJdT - ref["dJdT"]) <= 1e-12 * abs(ref["dJdT"])
+
+
+@pytest.mark.parametrize("nx,ns,L", SHAPES)
+@pytest.mark.parametrize("xi", [0, 1])
+def test_items_float_path_matches_oracle(harness, nx, ns, L, xi):
+    """The float items (float-float partials for J and L^dag_2) within 1e-5 of the oracle given
+    the same float-rounded field: gradient, and three IMEX steps."""
+    u, T, _ = spectral_loop(1, nx, L, ns=ns, T_range=(30.0, 50.0), symmetric=bool(xi))
+    uf = u.astype(np.float32).astype(np.float64)
+    J, dJdT, G = run(harness, uf, T, L, 0.15, ko.IMEX, 0, mode=1, prec=32, xi=xi)
+    ref = ko.adjoint_grad(uf, T, L, xi=bool(xi))
+    assert rel(G, ref["G"]) <= 1e-5
+    assert abs(J - ref["J"]) <= 1e-5 * ref["J"]
+    assert abs(dJdT - ref["dJdT"]) <= 1e-5 * abs(ref["dJdT"])
+    _, Tn, g = run(harness, uf, T, L, 0.15, ko.IMEX, 3, mode=0, prec=32, xi=xi)
+    d = ko.descend(uf, T, L, 0.15, ko.IMEX, 3, xi=bool(xi))
+    assert rel(g, d["u"]) <= 1e-5 and abs(Tn - d["T"]) <= 1e-5 * d["T"]
+
+
+def test_items_symmetric_step_keeps_the_loop_odd(harness):
+    """With the symmetry knob a centre-symmetric loop stays odd in x after steps."""
+    u, T, _ = spectral_loop(3, 32, 22.0, ns=32, T_range=(30.0, 50.0), symmetric=True)
+    _, _, g = run(harness, u, T, 22.0, 0.15, ko.IMEX, 4, mode=0, prec=64, xi=1)
+    reflected = -np.roll(g[:, ::-1], 1, axis=1)      # u(-x) on the grid m -> -m mod Nx
+    assert np.abs(g - reflected).max() <= 1e-13 * np.abs(g).max()
