@@ -5,13 +5,14 @@
 //           (ROW_NONLIN, COL_RESID, ROW_ADJ, COL_UPDATE) and is synthesised back to the grid, or
 //   mode 1: has its residual and adjoint gradient evaluated (COL_SYNTH_U, ROW_NONLIN, COL_RESID,
 //           ROW_ADJ, COL_GRAD) and G synthesised to the grid, with J and dJ/dT from the column
-//           partials summed in the fixed order of the finalising kernel.
+//           partials summed in the fixed order of the finalising kernel, or
+//   mode 2: the same residual pass only, with r synthesised to the grid (COL_SYNTH_R).
 // Test infrastructure: the CPU tests compare its output with the oracle, so the items' index
 // arithmetic and formulas are checked without a GPU.
 //
 // stdin:  L nx ns T dtau scheme steps mode prec(64|32) xi(0|1), then ns * nx values u[n][m]
 // stdout: mode 0: sqrt(J) of the initial state, T after the steps, then the grid u
-//         mode 1: J, dJ/dT, then the grid G
+//         mode 1: J, dJ/dT, then the grid G; mode 2: J, dJ/dT, then the grid r
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -132,8 +133,10 @@ int run(const Dims& d, int ns, double T0, int xi, int steps, int mode,
     } else {
         for (int it = 0; it < nrow; ++it) row_item<R, ROW_NONLIN>(d, p, it, smem);
         for (int j = 0; j < nkx; ++j) col_item<R, COL_RESID>(d, p, j, smem, 0);
-        for (int it = 0; it < nrow; ++it) row_item<R, ROW_ADJ>(d, p, it, smem);
-        for (int j = 0; j < nkx; ++j) col_item<R, COL_GRAD>(d, p, j, smem, 0);
+        if (mode == 1) {
+            for (int it = 0; it < nrow; ++it) row_item<R, ROW_ADJ>(d, p, it, smem);
+            for (int j = 0; j < nkx; ++j) col_item<R, COL_GRAD>(d, p, j, smem, 0);
+        }
         // J and dJ/dT = 2 L^dag_2 from the partials, in column order as the finalising kernel
         double sj = 0.0, sl = 0.0;
         for (int c = 0; c < nkx; ++c) {
@@ -141,7 +144,10 @@ int run(const Dims& d, int ns, double T0, int xi, int steps, int mode,
             sl += widen(h.L2part[c]);
         }
         const double J = d.L * sj, dJdT = 2.0 * d.L * 2.0 * kPi * sl / (T0 * T0);
-        for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_G>(d, p, j, smem, 0);
+        if (mode == 1)
+            for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_G>(d, p, j, smem, 0);
+        else
+            for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_R>(d, p, j, smem, 0);
         for (int it = 0; it < nrow; ++it) row_item<R, ROW_SYNTH>(d, p, it, smem);
         std::printf("%.17g %.17g\n", J, dJdT);
     }

@@ -83,6 +83,8 @@ def test_items_gradient_matches_oracle_fp64(harness, nx, ns, L, xi):
     J, dJdT, G = run(harness, u, T, L, 0.15, ko.IMEX, 0, mode=1, prec=64, xi=xi)
     ref = ko.adjoint_grad(u, T, L, xi=bool(xi))
     assert rel(G, ref["G"]) <= 1e-12
+    _, _, r = run(harness, u, T, L, 0.15, ko.IMEX, 0, mode=2, prec=64, xi=xi)
+    assert rel(r, ko.residual(u, T, L, xi=bool(xi))["r"]) <= 1e-12
     assert abs(J - ref["J"]) <= 1e-12 * ref["J"]
     assert abs(dJdT - ref["dJdT"]) <= 1e-12 * abs(ref["dJdT"])
 
