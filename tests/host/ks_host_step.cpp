@@ -1,6 +1,8 @@
 // Host run of the per-CTA work items (ks_items.cuh compiled as sequential code with
-// KS_HOST_EMULATION).  One loop is analysed onto its band (in double, as the library always
-// does), rounded to the working precision, and then either
+// KS_HOST_EMULATION) over a ragged batch of loops, laid out as the library lays them out (band,
+// mixed and grid offsets per loop, columns longest loop first, row tiles per loop).  The batch is
+// analysed onto its bands (in double, as the library always does), rounded to the working
+// precision, and then either
 //   mode 0: takes `steps` tau-steps through the four phases the per-phase launches run
 //           (ROW_NONLIN, COL_RESID, ROW_ADJ, COL_UPDATE) and is synthesised back to the grid, or
 //   mode 1: has its residual and adjoint gradient evaluated (COL_SYNTH_U, ROW_NONLIN, COL_RESID,
@@ -10,9 +12,11 @@
 // Test infrastructure: the CPU tests compare its output with the oracle, so the items' index
 // arithmetic and formulas are checked without a GPU.
 //
-// stdin:  L nx ns T dtau scheme steps mode prec(64|32) xi(0|1), then ns * nx values u[n][m]
-// stdout: mode 0: sqrt(J) of the initial state, T after the steps, then the grid u
-//         mode 1: J, dJ/dT, then the grid G; mode 2: J, dJ/dT, then the grid r
+// stdin:  L nx B dtau scheme steps mode prec(64|32) xi(0|1), then B pairs "Ns_b T_b", then the
+//         grid values of every loop, loop after loop, each u[n][m]
+// stdout: B lines "a_b c_b" (mode 0: sqrt(J) of the initial state and T after the steps;
+//         modes 1, 2: J and dJ/dT), then the grid values (u, G or r) of every loop in order
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -32,34 +36,59 @@ int lg2(int n) {
     return l;
 }
 
-// Host copies of every buffer of one precision, and the Bufs that point into them.
+// Host copies of every buffer of one precision for the whole batch, and the Bufs into them.
 template <typename R>
-struct HostLoop {
-    std::vector<int> ns, lgns, ks, colorder{0};
-    std::vector<long long> zero{0}, steps{0};
+struct HostBatch {
+    std::vector<int> ns, lgns, ks, colorder, status, prec;
+    std::vector<long long> boff, moff, goff, steps;
     std::vector<cpx<R>> uh, rh, gh, M, tw;
     std::vector<R> U, io, qv, lin, cq, insv;
-    std::vector<double> T, wT, sqrtJ{0.0};
+    std::vector<double> T, wT, sqrtJ;
     std::vector<typename PartT<R>::type> Jpart, L2part;
-    std::vector<int> status{ST_RUNNING}, prec;
     std::vector<RowItem> rows;
     Bufs<R> p{};
 
-    HostLoop(const Dims& d, int n, double T0, int xi) {
-        const int nkx = d.nkx, k3 = n / 3, nk = 2 * k3 + 1;
-        ns = {n};
-        lgns = {lg2(n)};
-        ks = {k3};
-        uh.assign((size_t)nkx * nk, mk<R>(0, 0));
+    HostBatch(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T0, int xi) {
+        const int B = d.B, nkx = d.nkx;
+        long long bo = 0, mo = 0, go = 0;
+        for (int b = 0; b < B; ++b) {
+            const int n = nsv[b];
+            ns.push_back(n);
+            lgns.push_back(lg2(n));
+            ks.push_back(n / 3);
+            boff.push_back(bo);
+            moff.push_back(mo);
+            goff.push_back(go);
+            bo += (long long)nkx * (2 * (n / 3) + 1);
+            mo += (long long)nkx * n;
+            go += (long long)n * d.nx;
+            insv.push_back((R)(1.0 / n));
+        }
+        uh.assign(bo, mk<R>(0, 0));
         rh = gh = uh;
-        M.assign((size_t)nkx * n, mk<R>(0, 0));
-        U.assign((size_t)n * d.nx, 0);
+        M.assign(mo, mk<R>(0, 0));
+        U.assign(go, 0);
         io = U;
-        T = {T0, T0};
-        wT = {2.0 * kPi / T0, 2.0 * kPi / T0};
-        Jpart.resize(nkx);
-        L2part.resize(nkx);
-        prec = {sizeof(R) == 8 ? 0 : 1};
+        T.resize(2 * B);
+        wT.resize(2 * B);
+        for (int b = 0; b < B; ++b) {
+            T[b] = T[B + b] = T0[b];
+            wT[b] = wT[B + b] = 2.0 * kPi / T0[b];
+        }
+        Jpart.resize((size_t)B * nkx);
+        L2part.resize((size_t)B * nkx);
+        status.assign(B, ST_RUNNING);
+        prec.assign(B, sizeof(R) == 8 ? 0 : 1);
+        steps.assign(B, 0);
+        sqrtJ.assign(B, 0.0);
+        // columns of the longest loops first (the library's order); rows in tiles of <= 8
+        for (int b = 0; b < B; ++b) colorder.push_back(b);
+        std::stable_sort(colorder.begin(), colorder.end(),
+                         [&](int a, int c) { return ns[a] > ns[c]; });
+        for (int b = 0; b < B; ++b) {
+            const int nr = std::min(ns[b], 8);
+            for (int n0 = 0; n0 < ns[b]; n0 += nr) rows.push_back(RowItem{b, n0, nr, lg2(nr)});
+        }
         tw.resize(NMAX);
         for (int t = 0; t < NMAX; ++t) {
             const double a = 2.0 * kPi * t / NMAX;
@@ -71,13 +100,17 @@ struct HostLoop {
             lin.push_back((R)(q * q - q * q * q * q));
             cq.push_back((R)(q * q * q * q * (q * q - 1.0) * (q * q - 1.0)));
         }
-        insv = {(R)(1.0 / n)};
-        const int nr = n < 8 ? n : 8;
-        for (int n0 = 0; n0 < n; n0 += nr) rows.push_back(RowItem{0, n0, nr, lg2(nr)});
+        point();
+        p.xi = xi;
+    }
+
+    void point() {
         p.ns = ns.data();
         p.lgns = lgns.data();
         p.ks = ks.data();
-        p.boff = p.moff = p.goff = zero.data();
+        p.boff = boff.data();
+        p.moff = moff.data();
+        p.goff = goff.data();
         p.uh = uh.data();
         p.rh = rh.data();
         p.gh = gh.data();
@@ -100,57 +133,75 @@ struct HostLoop {
         p.rows = rows.data();
         p.colorder = colorder.data();
         p.myprec = prec[0];
-        p.xi = xi;
     }
 };
 
+std::vector<double> g_smem(1 << 17);  // item scratch (1 MiB)
+
 template <typename R>
-int run(const Dims& d, int ns, double T0, int xi, int steps, int mode,
-        const std::vector<cpx<double>>& band) {
-    HostLoop<R> h(d, ns, T0, xi);
+void rows_pass(const Dims& d, HostBatch<R>& h, int mode) {
+    unsigned char* smem = reinterpret_cast<unsigned char*>(g_smem.data());
+    for (int it = 0; it < (int)h.rows.size(); ++it) {
+        switch (mode) {
+            case ROW_ANALYZE: row_item<R, ROW_ANALYZE>(d, h.p, it, smem); break;
+            case ROW_NONLIN: row_item<R, ROW_NONLIN>(d, h.p, it, smem); break;
+            case ROW_ADJ: row_item<R, ROW_ADJ>(d, h.p, it, smem); break;
+            default: row_item<R, ROW_SYNTH>(d, h.p, it, smem); break;
+        }
+    }
+}
+
+template <typename R, int MODE>
+void cols_pass(const Dims& d, HostBatch<R>& h, int par) {
+    unsigned char* smem = reinterpret_cast<unsigned char*>(g_smem.data());
+    for (int it = 0; it < d.B * d.nkx; ++it) col_item<R, MODE>(d, h.p, it, smem, par);
+}
+
+template <typename R>
+int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T0, int xi,
+        int steps, int mode, const std::vector<cpx<double>>& band) {
+    HostBatch<R> h(d, nsv, T0, xi);
     Bufs<R>& p = h.p;
     for (size_t i = 0; i < band.size(); ++i) h.uh[i] = mk<R>((R)band[i].x, (R)band[i].y);
-    std::vector<double> smem_d(1 << 17);  // item scratch (1 MiB)
-    unsigned char* smem = reinterpret_cast<unsigned char*>(smem_d.data());
-    const int nrow = (int)h.rows.size(), nkx = d.nkx;
+    const int B = d.B, nkx = d.nkx;
+    std::vector<double> a(B), c(B);
 
-    for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_U>(d, p, j, smem, 0);
+    cols_pass<R, COL_SYNTH_U>(d, h, 0);
     if (mode == 0) {
         p.check_active = 1;
-        double sqrtJ0 = -1.0;
         for (int s = 0; s < steps; ++s) {
             p.par = s & 1;
-            for (int it = 0; it < nrow; ++it) row_item<R, ROW_NONLIN>(d, p, it, smem);
-            for (int j = 0; j < nkx; ++j) col_item<R, COL_RESID>(d, p, j, smem, p.par);
-            for (int it = 0; it < nrow; ++it) row_item<R, ROW_ADJ>(d, p, it, smem);
-            for (int j = 0; j < nkx; ++j) col_item<R, COL_UPDATE>(d, p, j, smem, p.par);
-            if (s == 0) sqrtJ0 = h.sqrtJ[0];
+            rows_pass<R>(d, h, ROW_NONLIN);
+            cols_pass<R, COL_RESID>(d, h, p.par);
+            rows_pass<R>(d, h, ROW_ADJ);
+            cols_pass<R, COL_UPDATE>(d, h, p.par);
+            if (s == 0) a = h.sqrtJ;
         }
         p.check_active = 0;
-        for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_U>(d, p, j, smem, 0);
-        for (int it = 0; it < nrow; ++it) row_item<R, ROW_SYNTH>(d, p, it, smem);
-        std::printf("%.17g %.17g\n", sqrtJ0, h.T[steps & 1]);
+        for (int b = 0; b < B; ++b) c[b] = h.T[(size_t)(steps & 1) * B + b];
+        cols_pass<R, COL_SYNTH_U>(d, h, 0);
     } else {
-        for (int it = 0; it < nrow; ++it) row_item<R, ROW_NONLIN>(d, p, it, smem);
-        for (int j = 0; j < nkx; ++j) col_item<R, COL_RESID>(d, p, j, smem, 0);
+        rows_pass<R>(d, h, ROW_NONLIN);
+        cols_pass<R, COL_RESID>(d, h, 0);
         if (mode == 1) {
-            for (int it = 0; it < nrow; ++it) row_item<R, ROW_ADJ>(d, p, it, smem);
-            for (int j = 0; j < nkx; ++j) col_item<R, COL_GRAD>(d, p, j, smem, 0);
+            rows_pass<R>(d, h, ROW_ADJ);
+            cols_pass<R, COL_GRAD>(d, h, 0);
         }
         // J and dJ/dT = 2 L^dag_2 from the partials, in column order as the finalising kernel
-        double sj = 0.0, sl = 0.0;
-        for (int c = 0; c < nkx; ++c) {
-            sj += widen(h.Jpart[c]);
-            sl += widen(h.L2part[c]);
+        for (int b = 0; b < B; ++b) {
+            double sj = 0.0, sl = 0.0;
+            for (int k = 0; k < nkx; ++k) {
+                sj += widen(h.Jpart[(size_t)b * nkx + k]);
+                sl += widen(h.L2part[(size_t)b * nkx + k]);
+            }
+            a[b] = d.L * sj;
+            c[b] = 2.0 * d.L * 2.0 * kPi * sl / (T0[b] * T0[b]);
         }
-        const double J = d.L * sj, dJdT = 2.0 * d.L * 2.0 * kPi * sl / (T0 * T0);
-        if (mode == 1)
-            for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_G>(d, p, j, smem, 0);
-        else
-            for (int j = 0; j < nkx; ++j) col_item<R, COL_SYNTH_R>(d, p, j, smem, 0);
-        for (int it = 0; it < nrow; ++it) row_item<R, ROW_SYNTH>(d, p, it, smem);
-        std::printf("%.17g %.17g\n", J, dJdT);
+        if (mode == 1) cols_pass<R, COL_SYNTH_G>(d, h, 0);
+        else cols_pass<R, COL_SYNTH_R>(d, h, 0);
     }
+    rows_pass<R>(d, h, ROW_SYNTH);
+    for (int b = 0; b < B; ++b) std::printf("%.17g %.17g\n", a[b], c[b]);
     for (size_t i = 0; i < h.io.size(); ++i) std::printf("%.17g\n", (double)h.io[i]);
     return 0;
 }
@@ -158,13 +209,17 @@ int run(const Dims& d, int ns, double T0, int xi, int steps, int mode,
 }  // namespace
 
 int main() {
-    double L, T0, dtau;
-    int nx, ns, scheme, steps, mode, precision, xi;
-    if (std::scanf("%lf %d %d %lf %lf %d %d %d %d %d", &L, &nx, &ns, &T0, &dtau, &scheme, &steps,
-                   &mode, &precision, &xi) != 10)
+    double L, dtau;
+    int nx, B, scheme, steps, mode, precision, xi;
+    if (std::scanf("%lf %d %d %lf %d %d %d %d %d", &L, &nx, &B, &dtau, &scheme, &steps, &mode,
+                   &precision, &xi) != 9 || B < 1)
         return 2;
+    std::vector<int> nsv(B);
+    std::vector<double> T0(B);
+    for (int b = 0; b < B; ++b)
+        if (std::scanf("%d %lf", &nsv[b], &T0[b]) != 2) return 2;
     Dims d{};
-    d.B = 1;
+    d.B = B;
     d.nx = nx;
     d.lgnx = lg2(nx);
     d.kx = nx / 3;
@@ -174,15 +229,13 @@ int main() {
     d.scheme = scheme;
     d.hx = 0.5 / nx;
 
-    // analysis onto the band, always in double
-    HostLoop<double> a(d, ns, T0, xi);
-    for (auto& v : a.io)
+    // analysis onto the bands, always in double
+    HostBatch<double> an(d, nsv, T0, xi);
+    for (auto& v : an.io)
         if (std::scanf("%lf", &v) != 1) return 2;
-    std::vector<double> smem_d(1 << 17);
-    unsigned char* smem = reinterpret_cast<unsigned char*>(smem_d.data());
-    for (int it = 0; it < (int)a.rows.size(); ++it) row_item<double, ROW_ANALYZE>(d, a.p, it, smem);
-    for (int j = 0; j < d.nkx; ++j) col_item<double, COL_ANALYZE>(d, a.p, j, smem, 0);
+    rows_pass<double>(d, an, ROW_ANALYZE);
+    cols_pass<double, COL_ANALYZE>(d, an, 0);
 
-    if (precision == 32) return run<float>(d, ns, T0, xi, steps, mode, a.uh);
-    return run<double>(d, ns, T0, xi, steps, mode, a.uh);
+    if (precision == 32) return run<float>(d, nsv, T0, xi, steps, mode, an.uh);
+    return run<double>(d, nsv, T0, xi, steps, mode, an.uh);
 }

@@ -24,17 +24,30 @@ def harness(tmp_path_factory):
     if not cxx:
         pytest.skip("no host C++ compiler")
     exe = tmp_path_factory.mktemp("items") / "ks_host_step"
-    subprocess.run([cxx, "-std=c++17", "-O1", "-I", B.CSRC,
+    subprocess.run([cxx, "-std=c++17", "-O1", "-w", "-I", B.CSRC,
                     os.path.join(HERE, "host", "ks_host_step.cpp"), "-o", str(exe)], check=True)
     return str(exe)
 
 
-def run(exe, u, T, L, dtau, scheme, steps, mode=0, prec=64, xi=0):
-    ns, nx = u.shape
-    inp = f"{L!r} {nx} {ns} {float(T)!r} {dtau!r} {scheme} {steps} {mode} {prec} {xi}\n"
-    inp += "\n".join(repr(float(x)) for x in u.ravel())
+def run_batch(exe, loops, L, dtau, scheme, steps, mode=0, prec=64, xi=0):
+    """loops: [(u[n][m], T)]; returns [(a, c, grid)] per loop (mode 0: sqrt(J0), T after the
+    steps, u; modes 1 and 2: J, dJ/dT, and G or r)."""
+    nx = loops[0][0].shape[1]
+    inp = f"{L!r} {nx} {len(loops)} {dtau!r} {scheme} {steps} {mode} {prec} {xi}\n"
+    inp += "\n".join(f"{u.shape[0]} {float(T)!r}" for u, T in loops) + "\n"
+    inp += "\n".join(repr(float(x)) for u, _ in loops for x in u.ravel())
     out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
-    return float(out[0]), float(out[1]), np.array(list(map(float, out[2:]))).reshape(ns, nx)
+    res, o = [], 2 * len(loops)
+    for b, (u, _) in enumerate(loops):
+        n = u.size
+        res.append((float(out[2 * b]), float(out[2 * b + 1]),
+                    np.array(list(map(float, out[o:o + n]))).reshape(u.shape)))
+        o += n
+    return res
+
+
+def run(exe, u, T, L, dtau, scheme, steps, mode=0, prec=64, xi=0):
+    return run_batch(exe, [(u, T)], L, dtau, scheme, steps, mode, prec, xi)[0]
 
 
 @pytest.mark.parametrize("nx,ns,L,scheme,dtau,steps", [
@@ -112,3 +125,24 @@ def test_items_symmetric_step_keeps_the_loop_odd(harness):
     _, _, g = run(harness, u, T, 22.0, 0.15, ko.IMEX, 4, mode=0, prec=64, xi=1)
     reflected = -np.roll(g[:, ::-1], 1, axis=1)      # u(-x) on the grid m -> -m mod Nx
     assert np.abs(g - reflected).max() <= 1e-13 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_items_ragged_batch_matches_oracle(harness, mode):
+    """A ragged batch (Ns 8 .. 128, columns longest loop first, per-loop offsets): every loop
+    agrees with the oracle run on it alone."""
+    L, nx = 22.0, 32
+    loops = []
+    for i, n in enumerate([32, 8, 128, 16, 64, 32]):
+        u, T, _ = spectral_loop(10 + i, nx, L, ns=n, T_range=(30.0, 50.0))
+        loops.append((u, T))
+    res = run_batch(harness, loops, L, 0.15, ko.IMEX, 3, mode=mode)
+    for (u, T), (a, c, g) in zip(loops, res):
+        if mode == 0:
+            ref = ko.descend(u, T, L, 0.15, ko.IMEX, 3)
+            assert rel(g, ref["u"]) <= 1e-12 and abs(c - ref["T"]) <= 1e-12 * ref["T"]
+            assert abs(a - np.sqrt(ko.residual(u, T, L)["J"])) <= 1e-12 * a
+        else:
+            ref = ko.adjoint_grad(u, T, L)
+            assert rel(g, ref["G"]) <= 1e-12 and abs(a - ref["J"]) <= 1e-12 * ref["J"]
+            assert abs(c - ref["dJdT"]) <= 1e-12 * abs(ref["dJdT"])
