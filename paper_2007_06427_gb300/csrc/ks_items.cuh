@@ -211,8 +211,9 @@ struct Bufs {
     int xi;                 // 1: descent restricted to the Xi-invariant (centre-symmetric) subspace
     int twsh;               // tw is a compact swizzled shared-memory table: entry t at
                             // tw_swz(t >> twsh) (see load_twiddles_compact); 0 otherwise
-    int own_frozen_only;    // 1: carry T forward only for frozen loops of this precision (the
-                            // other precision's kernel runs concurrently and carries its own)
+    int own_frozen_only;    // cluster kernel: 1 = carry T forward only for frozen loops of this
+                            // precision (the other precision's launch runs concurrently and
+                            // carries its own)
 };
 
 // Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 4.1, the
