@@ -96,14 +96,23 @@ def kernel_flops(kind: str, nx: int, nss, steps_per_launch: int = 1) -> float:
     return 0.0
 
 
+def code_tokens(src: str) -> str:
+    """C++ source without its comments and with whitespace collapsed: what the compiler sees
+    (the device sources hold no string literal with a comment marker in it)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_source_hash() -> str:
     """Hash of the device code of the fused kernels (the per-CTA items and the cluster-resident
-    kernel); host-side changes leave it unchanged."""
+    kernel), comments and layout excluded; host-side changes leave it unchanged."""
     import hashlib
     h = hashlib.sha256()
     for f in ("ks_items.cuh", "ks_cluster.cuh"):
-        with open(os.path.join(ROOT, "paper_2007_06427_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2007_06427_gb300", "csrc", f)) as fh:
+            h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

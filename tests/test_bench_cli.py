@@ -78,3 +78,14 @@ def test_roofline_entry_arithmetic():
     finally:
         torch.cuda.get_device_properties = orig
     assert r2["sms_used"] == 16 and abs(r2["frac_of_sms_used"] - roof["frac"] * 152 / 16) < 1e-15
+
+
+def test_kernel_hash_ignores_comments_and_layout():
+    """The traffic entries stay valid across comment and layout edits of the device code, and
+    not across code edits."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) {\n    return x + 1;  // one more\n}\n/* note */"
+    b = "int f(int x) { return x + 1; }  // reworded comment"
+    c = "int f(int x) { return x + 2; }"
+    assert bench.code_tokens(a) == bench.code_tokens(b) != bench.code_tokens(c)
