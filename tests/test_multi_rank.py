@@ -84,3 +84,30 @@ def test_two_gloo_ranks_match_serial_descent():
     np.testing.assert_array_equal(uu, ref_u)
     np.testing.assert_array_equal(TT, ref_T)
     assert sum(sizes) == w.batch and min(sizes) >= 1
+
+
+def test_more_ranks_than_loops_and_round_trip():
+    """Ranks without loops get an empty list; each rank's slice of the packed field and the
+    reassembly in batch order invert each other; a missing loop is reported."""
+    ns, nx = [64, 32, 128], 16
+    parts = shard.partition(ns, nx, 5)
+    assert len(parts) == 5 and sorted(b for p in parts for b in p) == [0, 1, 2]
+    assert sum(1 for p in parts if not p) == 2
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(sum(ns) * nx)
+    T = [30.0, 40.0, 50.0]
+    results = {}
+    for p in parts:
+        ul, Tl, nsl = shard.local_batch(u, ns, nx, T, p)
+        assert ul.size == sum(n * nx for n in nsl) and list(Tl) == [T[b] for b in p]
+        o = 0
+        for b, n in zip(p, nsl):
+            results[b] = {"u": ul[o:o + n * nx], "T": Tl[p.index(b)]}
+            o += n * nx
+    u2, T2 = shard.scatter_back(results, ns, nx)
+    assert np.array_equal(u2, u) and list(T2) == T
+    del results[1]
+    with pytest.raises(ValueError, match="1"):
+        shard.scatter_back(results, ns, nx)
+    with pytest.raises(ValueError):
+        shard.partition(ns, nx, 0)
