@@ -1,0 +1,47 @@
+"""The seeded synthetic inputs: every named workload has the shape, periods, scheme and step of
+its configuration, and every loop follows the recipe (zero spatial mean, grid rms 1, band
+limited to |j| <= Nx/3, |k| <= Ns/3, reproducible from its seed)."""
+import numpy as np
+import pytest
+
+from paper_2007_06427_gb300 import inputs
+
+EXPECTED = {
+    # name: (loops, L, Nx, Ns set, T0 range (lo, hi) or fixed, scheme, dtau)
+    "single_32x32_explicit": (1, 22.0, 32, {32}, (40.0, 40.0), 0, 1e-4),
+    "single_64x128_imex": (1, 22.0, 64, {128}, (20.0, 80.0), 1, 0.15),
+    "batch16_64x64": (16, 22.0, 64, {64}, (20.0, 80.0), 1, 0.15),
+    "ragged256_64xNs": (256, 22.0, 64, {32, 64, 128, 256}, (10.0, 100.0), 1, 0.15),
+    "large8_256x1024": (8, 100.0, 256, {1024}, (120.0, 120.0), 1, 0.15),
+    "paper_L39_64x64": (1, 39.0, 64, {64}, (40.0, 40.0), 1, 0.15),
+    "paper_L39_xi_64x64": (1, 39.0, 64, {64}, (40.0, 40.0), 1, 0.15),
+}
+
+
+@pytest.mark.parametrize("name", inputs.WORKLOADS)
+def test_workload_configuration(name):
+    w = inputs.workload(name)
+    B, L, nx, nsset, (lo, hi), scheme, dtau = EXPECTED[name]
+    assert w.batch == B and w.L == L and w.nx == nx and w.scheme == scheme and w.dtau == dtau
+    assert set(w.ns) <= nsset and all(lo <= T <= hi for T in w.T0)
+    if name == "ragged256_64xNs":
+        assert set(w.ns) == nsset                     # every length occurs
+    assert w.packed().size == sum(w.ns) * nx
+
+
+@pytest.mark.parametrize("name", ["single_64x128_imex", "batch16_64x64", "paper_L39_xi_64x64"])
+def test_loops_follow_the_recipe(name):
+    w = inputs.workload(name)
+    again = inputs.workload(name)
+    for b, u in enumerate(w.u):
+        ns, nx = u.shape
+        assert np.array_equal(u, again.u[b])                     # seeded
+        assert abs(u.mean()) < 1e-12 and abs(np.sqrt((u * u).mean()) - 1.0) < 1e-12
+        c = np.fft.fft2(u) / u.size                                # test-side spectrum check
+        k = np.fft.fftfreq(ns, 1.0 / ns)[:, None]
+        j = np.fft.fftfreq(nx, 1.0 / nx)[None, :]
+        outside = (np.abs(j) > nx // 3) | (np.abs(k) > ns // 3)
+        assert np.abs(c[outside]).max() < 1e-13
+        assert np.abs(c[:, 0]).max() < 1e-13                        # j = 0 column zeroed
+        if name.startswith("paper_L39_xi"):
+            assert np.abs(u + np.roll(u[:, ::-1], 1, axis=1)).max() < 1e-12   # odd in x
