@@ -12,10 +12,11 @@
 // Test infrastructure: the CPU tests compare its output with the oracle, so the items' index
 // arithmetic and formulas are checked without a GPU.
 //
-// stdin:  L nx B dtau scheme steps mode prec(64|32) xi(0|1), then B pairs "Ns_b T_b", then the
-//         grid values of every loop, loop after loop, each u[n][m]
-// stdout: B lines "a_b c_b" (mode 0: sqrt(J) of the initial state and T after the steps;
-//         modes 1, 2: J and dJ/dT), then the grid values (u, G or r) of every loop in order
+// stdin:  L nx B dtau scheme steps mode prec(64|32) xi(0|1) tol, then B pairs "Ns_b T_b", then
+//         the grid values of every loop, loop after loop, each u[n][m]
+// stdout: B lines "a_b c_b s_b n_b" (mode 0: sqrt(J) of the initial state, T after the steps,
+//         the loop's status and steps taken; modes 1, 2: J, dJ/dT, 0, 0), then the grid values
+//         (u, G or r) of every loop in order
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -159,9 +160,10 @@ void cols_pass(const Dims& d, HostBatch<R>& h, int par) {
 
 template <typename R>
 int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T0, int xi,
-        int steps, int mode, const std::vector<cpx<double>>& band) {
+        int steps, int mode, double tol, const std::vector<cpx<double>>& band) {
     HostBatch<R> h(d, nsv, T0, xi);
     Bufs<R>& p = h.p;
+    p.tol = tol;
     for (size_t i = 0; i < band.size(); ++i) h.uh[i] = mk<R>((R)band[i].x, (R)band[i].y);
     const int B = d.B, nkx = d.nkx;
     std::vector<double> a(B), c(B);
@@ -201,7 +203,9 @@ int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T
         else cols_pass<R, COL_SYNTH_R>(d, h, 0);
     }
     rows_pass<R>(d, h, ROW_SYNTH);
-    for (int b = 0; b < B; ++b) std::printf("%.17g %.17g\n", a[b], c[b]);
+    for (int b = 0; b < B; ++b)
+        std::printf("%.17g %.17g %d %lld\n", a[b], c[b], mode == 0 ? h.status[b] : 0,
+                    mode == 0 ? h.steps[b] : 0LL);
     for (size_t i = 0; i < h.io.size(); ++i) std::printf("%.17g\n", (double)h.io[i]);
     return 0;
 }
@@ -210,9 +214,10 @@ int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T
 
 int main() {
     double L, dtau;
+    double tol;
     int nx, B, scheme, steps, mode, precision, xi;
-    if (std::scanf("%lf %d %d %lf %d %d %d %d %d", &L, &nx, &B, &dtau, &scheme, &steps, &mode,
-                   &precision, &xi) != 9 || B < 1)
+    if (std::scanf("%lf %d %d %lf %d %d %d %d %d %lf", &L, &nx, &B, &dtau, &scheme, &steps, &mode,
+                   &precision, &xi, &tol) != 10 || B < 1)
         return 2;
     std::vector<int> nsv(B);
     std::vector<double> T0(B);
@@ -236,6 +241,6 @@ int main() {
     rows_pass<double>(d, an, ROW_ANALYZE);
     cols_pass<double, COL_ANALYZE>(d, an, 0);
 
-    if (precision == 32) return run<float>(d, nsv, T0, xi, steps, mode, an.uh);
-    return run<double>(d, nsv, T0, xi, steps, mode, an.uh);
+    if (precision == 32) return run<float>(d, nsv, T0, xi, steps, mode, tol, an.uh);
+    return run<double>(d, nsv, T0, xi, steps, mode, tol, an.uh);
 }

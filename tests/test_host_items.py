@@ -18,7 +18,14 @@ from paper_2007_06427_gb300.inputs import spectral_loop
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.fixture(scope="module")
+_EXE = {}
+
+
+def harness_exe():
+    return _EXE["path"]
+
+
+@pytest.fixture(scope="module", autouse=True)
 def harness(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     if not cxx:
@@ -26,24 +33,27 @@ def harness(tmp_path_factory):
     exe = tmp_path_factory.mktemp("items") / "ks_host_step"
     subprocess.run([cxx, "-std=c++17", "-O1", "-w", "-I", B.CSRC,
                     os.path.join(HERE, "host", "ks_host_step.cpp"), "-o", str(exe)], check=True)
+    _EXE["path"] = str(exe)
     return str(exe)
 
 
-def run_batch(exe, loops, L, dtau, scheme, steps, mode=0, prec=64, xi=0):
+def run_batch(exe, loops, L, dtau, scheme, steps, mode=0, prec=64, xi=0, tol=0.0, status=False):
     """loops: [(u[n][m], T)]; returns [(a, c, grid)] per loop (mode 0: sqrt(J0), T after the
-    steps, u; modes 1 and 2: J, dJ/dT, and G or r)."""
+    steps, u; modes 1 and 2: J, dJ/dT, and G or r), and with status=True also the loops'
+    (status, steps taken)."""
     nx = loops[0][0].shape[1]
-    inp = f"{L!r} {nx} {len(loops)} {dtau!r} {scheme} {steps} {mode} {prec} {xi}\n"
+    inp = f"{L!r} {nx} {len(loops)} {dtau!r} {scheme} {steps} {mode} {prec} {xi} {tol!r}\n"
     inp += "\n".join(f"{u.shape[0]} {float(T)!r}" for u, T in loops) + "\n"
     inp += "\n".join(repr(float(x)) for u, _ in loops for x in u.ravel())
     out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
-    res, o = [], 2 * len(loops)
+    res, st, o = [], [], 4 * len(loops)
     for b, (u, _) in enumerate(loops):
         n = u.size
-        res.append((float(out[2 * b]), float(out[2 * b + 1]),
+        res.append((float(out[4 * b]), float(out[4 * b + 1]),
                     np.array(list(map(float, out[o:o + n]))).reshape(u.shape)))
+        st.append((int(out[4 * b + 2]), int(out[4 * b + 3])))
         o += n
-    return res
+    return (res, st) if status else res
 
 
 def run(exe, u, T, L, dtau, scheme, steps, mode=0, prec=64, xi=0):
@@ -146,3 +156,22 @@ def test_items_ragged_batch_matches_oracle(harness, mode):
             ref = ko.adjoint_grad(u, T, L)
             assert rel(g, ref["G"]) <= 1e-12 and abs(a - ref["J"]) <= 1e-12 * ref["J"]
             assert abs(c - ref["dJdT"]) <= 1e-12 * abs(ref["dJdT"])
+
+
+def test_items_freeze_rules():
+    """The per-loop freeze of the update item (convergence test of Sec. 4.3, divergence): a
+    converged loop stops before the step whose starting sqrt(J) is below tol and keeps its T; a
+    non-finite loop is frozen as diverged; the other loops of the batch run on."""
+    L, nx = 22.0, 16
+    u0, T0, _ = spectral_loop(4, nx, L, ns=16, T_range=(30.0, 50.0))
+    u1, T1, _ = spectral_loop(5, nx, L, ns=16, T_range=(30.0, 50.0))
+    flat = np.full((16, nx), 0.25)                    # u = const: r = 0 (an equilibrium)
+    bad = u1.copy()
+    bad[3, 5] = np.nan
+    loops = [(u0, T0), (flat, 35.0), (bad, T1)]
+    (res, st) = run_batch(harness_exe(), loops, L, 0.15, ko.IMEX, 4, tol=1e-10, status=True)
+    assert st[0] == (0, 4)                           # running, all four steps taken
+    assert st[1][0] == 1 and st[1][1] == 0 and res[1][1] == 35.0   # converged at once, T kept
+    assert st[2][0] == 4 and st[2][1] == 0           # diverged, no step taken
+    ref = ko.descend(u0, T0, L, 0.15, ko.IMEX, 4)
+    assert rel(res[0][2], ref["u"]) <= 1e-12
