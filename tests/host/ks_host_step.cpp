@@ -12,7 +12,7 @@
 // Test infrastructure: the CPU tests compare its output with the oracle, so the items' index
 // arithmetic and formulas are checked without a GPU.
 //
-// stdin:  L nx B dtau scheme steps mode prec(64|32) xi(0|1) tol, then B pairs "Ns_b T_b", then
+// stdin:  L nx B dtau scheme steps mode prec(64|32) xi(0|1) tol switch_tol, then B pairs "Ns_b T_b", then
 //         the grid values of every loop, loop after loop, each u[n][m]
 // stdout: B lines "a_b c_b s_b n_b" (mode 0: sqrt(J) of the initial state, T after the steps,
 //         the loop's status and steps taken; modes 1, 2: J, dJ/dT, 0, 0), then the grid values
@@ -160,10 +160,12 @@ void cols_pass(const Dims& d, HostBatch<R>& h, int par) {
 
 template <typename R>
 int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T0, int xi,
-        int steps, int mode, double tol, const std::vector<cpx<double>>& band) {
+        int steps, int mode, double tol, double switch_tol,
+        const std::vector<cpx<double>>& band) {
     HostBatch<R> h(d, nsv, T0, xi);
     Bufs<R>& p = h.p;
     p.tol = tol;
+    p.switch_tol = switch_tol;
     for (size_t i = 0; i < band.size(); ++i) h.uh[i] = mk<R>((R)band[i].x, (R)band[i].y);
     const int B = d.B, nkx = d.nkx;
     std::vector<double> a(B), c(B);
@@ -214,10 +216,10 @@ int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T
 
 int main() {
     double L, dtau;
-    double tol;
+    double tol, switch_tol;
     int nx, B, scheme, steps, mode, precision, xi;
-    if (std::scanf("%lf %d %d %lf %d %d %d %d %d %lf", &L, &nx, &B, &dtau, &scheme, &steps, &mode,
-                   &precision, &xi, &tol) != 10 || B < 1)
+    if (std::scanf("%lf %d %d %lf %d %d %d %d %d %lf %lf", &L, &nx, &B, &dtau, &scheme, &steps,
+                   &mode, &precision, &xi, &tol, &switch_tol) != 11 || B < 1)
         return 2;
     std::vector<int> nsv(B);
     std::vector<double> T0(B);
@@ -241,6 +243,6 @@ int main() {
     rows_pass<double>(d, an, ROW_ANALYZE);
     cols_pass<double, COL_ANALYZE>(d, an, 0);
 
-    if (precision == 32) return run<float>(d, nsv, T0, xi, steps, mode, tol, an.uh);
-    return run<double>(d, nsv, T0, xi, steps, mode, tol, an.uh);
+    if (precision == 32) return run<float>(d, nsv, T0, xi, steps, mode, tol, switch_tol, an.uh);
+    return run<double>(d, nsv, T0, xi, steps, mode, tol, switch_tol, an.uh);
 }

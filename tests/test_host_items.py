@@ -37,12 +37,13 @@ def harness(tmp_path_factory):
     return str(exe)
 
 
-def run_batch(exe, loops, L, dtau, scheme, steps, mode=0, prec=64, xi=0, tol=0.0, status=False):
+def run_batch(exe, loops, L, dtau, scheme, steps, mode=0, prec=64, xi=0, tol=0.0, status=False,
+              switch_tol=0.0):
     """loops: [(u[n][m], T)]; returns [(a, c, grid)] per loop (mode 0: sqrt(J0), T after the
     steps, u; modes 1 and 2: J, dJ/dT, and G or r), and with status=True also the loops'
     (status, steps taken)."""
     nx = loops[0][0].shape[1]
-    inp = f"{L!r} {nx} {len(loops)} {dtau!r} {scheme} {steps} {mode} {prec} {xi} {tol!r}\n"
+    inp = f"{L!r} {nx} {len(loops)} {dtau!r} {scheme} {steps} {mode} {prec} {xi} {tol!r} {switch_tol!r}\n"
     inp += "\n".join(f"{u.shape[0]} {float(T)!r}" for u, T in loops) + "\n"
     inp += "\n".join(repr(float(x)) for u, _ in loops for x in u.ravel())
     out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
@@ -176,3 +177,20 @@ def test_items_freeze_rules():
     assert st[2][0] == 4 and st[2][1] == 0           # diverged, no step taken
     ref = ko.descend(u0, T0, L, 0.15, ko.IMEX, 4)
     assert rel(res[0][2], ref["u"]) <= 1e-12
+
+
+def test_items_float_switch_rule():
+    """The float update item hands a loop to the double phase (status switch, no step taken)
+    once its sqrt(J) is at or below switch_tol; a loop above it steps on."""
+    L, nx = 22.0, 16
+    small, T0, _ = spectral_loop(6, nx, L, ns=16, T_range=(30.0, 50.0))
+    big, T1, _ = spectral_loop(7, nx, L, ns=16, T_range=(30.0, 50.0))
+    small = 1e-4 * small
+    sq_small = np.sqrt(ko.residual(small, T0, L)["J"])
+    sq_big = np.sqrt(ko.residual(big, T1, L)["J"])
+    sw = 10 * sq_small
+    assert sw < sq_big
+    res, st = run_batch(harness_exe(), [(small, T0), (big, T1)], L, 0.15, ko.IMEX, 2, prec=32,
+                        status=True, switch_tol=float(sw))
+    assert st[0] == (5, 0) and res[0][1] == float(np.float64(T0))   # switched at once, T kept
+    assert st[1] == (0, 2)
