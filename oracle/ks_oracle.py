@@ -38,6 +38,11 @@ Readings where the paper is silent (each also listed in the design notes):
 * IMEX: Lambda_jk uses T at the start of the step; u and T are both advanced from the same
   state l^n.
 * Names: ``G`` is +L^dag_1 r (the ascent direction); ``dJdT`` is dJ/dT = 2 L^dag_2.
+* Extrapolation (App. C): ``descend_extrapolated`` observes the loop every ``chunk`` steps and,
+  from sqrt(J) <= 1e-3 on, each time sqrt(J) has halved since its anchor, moves it to
+  l_b + (l_b - l_a) rho / (1 - rho), rho = sqrt(J_b) / sqrt(J_a), keeping the move only if it
+  lowers sqrt(J) (the paper gives no formula; this geometric reading is exact for one decaying
+  eigendirection, which is how it is pinned).
 * Centre-symmetric subspace (Sec. 4.1, Eq. KS_loop_sym; Sec. 4.4): with ``xi=True`` the loop is
   restricted to the fields invariant under Xi: (x, s) -> (-x, s), u -> -u.  The input is
   projected onto that subspace with the band, and the descent direction L^dag_1 r is
