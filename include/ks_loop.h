@@ -252,25 +252,26 @@ KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
  * synchronisation, and a call that can fail) is not acceptable.  The paper has no counterpart:
  * this is a deployment variant of ks_residual.
  *
- * Computes what ks_residual computes for a handle with batch 1 and mode KS_FP64: the residual
- * of [P u; T] (Eq. KS_R) on the grid and J (Eq. cost_function).  No handle is needed.
+ * Returns the same r and J as ks_residual for a handle with batch 1 and mode KS_FP64, given
+ * the same u and T.  No handle is needed.
  *   L     : domain length, > 0
  *   nx, ns: grid size, powers of two with 8 <= nx <= 256 and 8 <= ns <= 256 (larger sizes are
  *           rejected with KS_ERR_ARG)
- *   u     : in,  device pointer, ns x nx doubles, layout [n][m]
- *   T     : the period (by value)
- *   r     : out, device pointer, ns x nx doubles, nullable
- *   J     : out, device pointer to one double
+ *   u     : in,  device pointer on the current device, ns x nx doubles, layout [n][m]
+ *   T     : the period (by value), finite and > 0 (else KS_ERR_ARG)
+ *   r     : out, device pointer on the current device, ns x nx doubles, nullable
+ *   J     : out, device pointer on the current device, one double
  *   stream: cudaStream_t; the call is stream ordered
- * Host pointers are rejected with KS_ERR_ARG.
+ * Host pointers, and device pointers of another device, are rejected with KS_ERR_ARG.
  *
  * All intermediates live in one file-scope device array of about 1.4 MB (at most 2 MB) that
  * every GPU loading the library holds until the process exits.  The first call on a device
- * (with that device current) looks up the array's device address and uploads the twiddle
- * table there; make that first call before any stream capture.  Every call shares the array
- * and overwrites what the previous call left in it, so calls that overlap on the GPU (on
- * different streams, or from several threads) race: serialise them.  Errors are reported
- * through ks_last_error(). */
+ * (with that device current), and the first call after that device's context was destroyed and
+ * created again (e.g. by cudaDeviceReset), looks up the array's device address and uploads the
+ * twiddle table there with a synchronous copy; make that first call before any stream capture.
+ * Every call shares the array and overwrites what the previous call left in it, so calls that
+ * overlap on the GPU (on different streams, or from several threads) race: serialise them.
+ * Errors are reported through ks_last_error(). */
 KS_API int ks_residual_noalloc(double L, int nx, int ns, const double* u, double T, double* r,
                                double* J, void* stream);
 

@@ -148,6 +148,10 @@ void na_twiddles(cpx<double>* tw) {
 constexpr int NA_MAXDEV = 64;
 std::mutex g_na_mutex;
 unsigned char* g_na_base[NA_MAXDEV] = {nullptr};
+// the context the set-up of each device was done in: a device reset or a context torn down and
+// created again reloads the module, which leaves the array without its twiddle table (and may
+// move it), so a new context id triggers the set-up again
+unsigned long long g_na_ctx[NA_MAXDEV] = {0};
 
 }  // namespace
 
@@ -164,12 +168,42 @@ int na_fail(int code, const char* msg) {
 // Once per device, with that device current: the device address of the scratch array (the
 // host-side symbol is only a stand-in), the twiddle table copied into it, and the shared
 // memory limits of the kernels.
+// Id of the current context (the driver's cuCtxGetCurrent / cuCtxGetId, reached through the
+// runtime's entry-point query so that the library needs no link against the driver library).
+int na_context_id(unsigned long long* id) {
+    typedef int (*get_current_t)(void**);
+    typedef int (*get_id_t)(void*, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return na_fail(KS_ERR_CUDA, "the driver's context queries are not available");
+        }
+        get_current = reinterpret_cast<get_current_t>(f1);
+        get_id = reinterpret_cast<get_id_t>(f2);
+    }
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0)
+        return na_fail(KS_ERR_CUDA, "no current CUDA context");
+    return KS_OK;
+}
+
 int na_setup(int dev, unsigned char** base) {
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (g_na_base[dev]) {
+    unsigned long long ctx = 0;
+    int rc = na_context_id(&ctx);
+    if (rc != KS_OK) return rc;
+    if (g_na_base[dev] && g_na_ctx[dev] == ctx) {
         *base = g_na_base[dev];
         return KS_OK;
     }
+    g_na_base[dev] = nullptr;
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_ks_noalloc_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -193,17 +227,19 @@ int na_setup(int dev, unsigned char** base) {
         return na_fail(KS_ERR_CUDA, "kernel attribute setup failed");
     }
     g_na_base[dev] = static_cast<unsigned char*>(ptr);
+    g_na_ctx[dev] = ctx;
     *base = g_na_base[dev];
     return KS_OK;
 }
 
-bool na_is_device(const void* p) {
+// device (or managed) memory of device dev
+bool na_is_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -213,19 +249,21 @@ static_assert(KS_NOALLOC_BYTES <= 2 * 1024 * 1024, "the no-allocation scratch mu
 extern "C" int ks_residual_noalloc(double L, int nx, int ns, const double* u, double T, double* r,
                                    double* J, void* stream) {
     ks_internal_set_error("");
+    cudaGetLastError();  // an error left by an unrelated earlier launch is not this call's
     if (!(L > 0.0) || !std::isfinite(L)) return na_fail(KS_ERR_ARG, "L must be > 0");
+    if (!(T > 0.0) || !std::isfinite(T)) return na_fail(KS_ERR_ARG, "T must be finite and > 0");
     if (nx < 8 || nx > NA_NXMAX || (nx & (nx - 1)))
         return na_fail(KS_ERR_ARG, "nx must be a power of two in [8, 256] for the no-allocation call");
     if (ns < 8 || ns > NA_NSMAX || (ns & (ns - 1)))
         return na_fail(KS_ERR_ARG, "ns must be a power of two in [8, 256] for the no-allocation call");
     if (!u || !J) return na_fail(KS_ERR_ARG, "u and J are required");
-    if (!na_is_device(u) || !na_is_device(J) || (r && !na_is_device(r)))
-        return na_fail(KS_ERR_ARG, "the no-allocation call takes device pointers only");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAXDEV) {
         cudaGetLastError();
         return na_fail(KS_ERR_CUDA, "no usable CUDA device");
     }
+    if (!na_is_device(u, dev) || !na_is_device(J, dev) || (r && !na_is_device(r, dev)))
+        return na_fail(KS_ERR_ARG, "the no-allocation call takes device pointers of the current device only");
     unsigned char* base = nullptr;
     int rc = na_setup(dev, &base);
     if (rc != KS_OK) return rc;
