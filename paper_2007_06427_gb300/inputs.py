@@ -92,6 +92,29 @@ def spectral_loop(seed: int, nx: int, L: float, ns: Optional[int] = None,
     return u, T, ns
 
 
+def with_white_noise(u: np.ndarray, seed: int, amp: float = 0.5) -> np.ndarray:
+    """u plus seeded white noise of grid rms ``amp``: energy in every Fourier mode of the grid,
+    inside and outside the 2/3 band, the Nyquist modes included (generator
+    ``numpy.random.default_rng(10_000 + seed)``)."""
+    rng = np.random.default_rng(10_000 + seed)
+    return u + amp * rng.standard_normal(u.shape)
+
+
+def outside_band_modes(nx: int, ns: int, amp: float = 1.0) -> np.ndarray:
+    """A real grid field [Ns, Nx] made only of Fourier modes just outside the 2/3 band and at
+    the Nyquist frequencies: (j, k) = (Kx+1, 0), (Nx/2, 0), (1, Ks+1), (0, Ns/2), (Kx+1, Ks+1)
+    and (Nx/2, Ns/2), with Kx = Nx // 3, Ks = Ns // 3, each a cosine of amplitude ``amp`` with
+    a fixed phase.  Its projection onto the band is zero."""
+    kx, ks = nx // 3, ns // 3
+    m = np.arange(nx)[None, :] / nx
+    n = np.arange(ns)[:, None] / ns
+    out = np.zeros((ns, nx))
+    for i, (j, k) in enumerate(((kx + 1, 0), (nx // 2, 0), (1, ks + 1), (0, ns // 2),
+                                (kx + 1, ks + 1), (nx // 2, ns // 2))):
+        out += amp * np.cos(2.0 * np.pi * (j * m + k * n) + 0.3 * (i + 1))
+    return out
+
+
 def make_loops(name: str, nx: int, L: float, seeds: Sequence[int], *, ns=None, ns_choices=None,
                T0=None, T_range=None, decay=(2.0, 2.0), scheme=1, dtau=0.15, meta=None,
                symmetric=False):
@@ -106,38 +129,70 @@ def make_loops(name: str, nx: int, L: float, seeds: Sequence[int], *, ns=None, n
 
 
 # The named workloads: sizes, periods and init decay rates of the descent benchmarks.
-def workload(name: str, batch: Optional[int] = None) -> Workload:
+def workload(name: str, batch: Optional[int] = None,
+             seeds: Optional[Sequence[int]] = None) -> Workload:
+    """The named workload; ``batch`` overrides the number of loops of the batched ones (seeds
+    0..batch-1), ``seeds`` gives the loops' seeds explicitly (any workload, same recipe)."""
+    def sd(default_batch: int):
+        if seeds is not None:
+            return list(seeds)
+        return list(range(default_batch if batch is None else batch))
+
     if name == "single_32x32_explicit":
-        return make_loops(name, 32, 22.0, [0], ns=32, T0=40.0, scheme=0, dtau=1e-4,
-                          meta={"steps": 2000})
+        return make_loops(name, 32, 22.0, sd(1) if seeds is not None else [0], ns=32, T0=40.0,
+                          scheme=0, dtau=1e-4, meta={"steps": 2000})
     if name == "single_64x128_imex":
-        return make_loops(name, 64, 22.0, [0], ns=128, T_range=(20.0, 80.0), scheme=1,
-                          dtau=0.15, meta={"tol": 1e-10, "max_steps": 1_000_000})
+        return make_loops(name, 64, 22.0, sd(1) if seeds is not None else [0], ns=128,
+                          T_range=(20.0, 80.0), scheme=1, dtau=0.15,
+                          meta={"tol": 1e-10, "max_steps": 1_000_000})
     if name == "batch16_64x64":
-        b = 16 if batch is None else batch
-        return make_loops(name, 64, 22.0, range(b), ns=64, T_range=(20.0, 80.0), scheme=1,
+        return make_loops(name, 64, 22.0, sd(16), ns=64, T_range=(20.0, 80.0), scheme=1,
                           dtau=0.15)
     if name == "ragged256_64xNs":
-        b = 256 if batch is None else batch
-        return make_loops(name, 64, 22.0, range(b), ns_choices=(32, 64, 128, 256),
+        return make_loops(name, 64, 22.0, sd(256), ns_choices=(32, 64, 128, 256),
                           T_range=(10.0, 100.0), scheme=1, dtau=0.15)
     if name == "large8_256x1024":
-        b = 8 if batch is None else batch
-        return make_loops(name, 256, 100.0, range(b), ns=1024, T0=120.0, decay=(8.0, 8.0),
+        return make_loops(name, 256, 100.0, sd(8), ns=1024, T0=120.0, decay=(8.0, 8.0),
                           scheme=1, dtau=0.15, meta={"switch_tol": 1e-5, "tol": 1e-10})
     if name == "paper_L39_64x64":
         # the paper's own numerical setting (Sec. 4.4): L = 39, 64 x 64 modes, dtau = 0.15,
         # T0 = 40, here on a seeded spectral loop in place of the authors' recurrence guess
-        b = 1 if batch is None else batch
-        return make_loops(name, 64, 39.0, range(b), ns=64, T0=40.0, scheme=1, dtau=0.15,
+        return make_loops(name, 64, 39.0, sd(1), ns=64, T0=40.0, scheme=1, dtau=0.15,
                           meta={"tol": 1e-12})
     if name == "paper_L39_xi_64x64":
         # the same setting restricted to centre-symmetric loops, as the paper's initial loops
         # and converged orbits are (Sec. 4.4); descended with the "symmetry" knob set to 1
-        b = 1 if batch is None else batch
-        return make_loops(name, 64, 39.0, range(b), ns=64, T0=40.0, scheme=1, dtau=0.15,
+        return make_loops(name, 64, 39.0, sd(1), ns=64, T0=40.0, scheme=1, dtau=0.15,
                           meta={"tol": 1e-12, "symmetry": 1}, symmetric=True)
     raise KeyError(name)
+
+
+def orbit_guess(path: Optional[str] = None) -> Workload:
+    """The stored initial loop at the paper's setting (L = 39, 64 x 64, dtau = 0.15, IMEX): a
+    centre-symmetric recurrence loop of a chaotic run (Sec. 4.3), kept as band coefficients
+    (``data/orbit_guess_L39.json``, written by ``data/make_orbit_guess.py``) and synthesised on
+    the grid here; descended with the "symmetry" knob it converges to a periodic orbit."""
+    import json
+    import os
+    if path is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                            "orbit_guess_L39.json")
+    with open(path) as f:
+        rec = json.load(f)
+    nx, ns = int(rec["nx"]), int(rec["ns"])
+    half = np.array(rec["c"], dtype=np.float64)            # [j-1][k][re, im], k = 0..Ks
+    ch = half[..., 0] + 1j * half[..., 1]
+    kx, ks = ch.shape[0], ch.shape[1] - 1
+    c = np.zeros((kx + 1, 2 * ks + 1), dtype=complex)       # j = 0..Kx, k = -Ks..Ks
+    c[1:, ks:] = ch
+    c[1:, :ks] = -np.conj(ch[:, :0:-1])                     # c_{j,-k} = -conj(c_{j,k})
+    j = np.arange(kx + 1)
+    k = np.arange(-ks, ks + 1)
+    ex = np.exp(2j * np.pi * np.outer(j, np.arange(nx)) / nx)
+    es = np.exp(2j * np.pi * np.outer(np.arange(ns), k) / ns)
+    u = 2.0 * (es @ c.T @ ex).real
+    return Workload("orbit_guess_L39_xi_64x64", float(rec["L"]), nx, [ns], [float(rec["T0"])],
+                    [u], 1, 0.15, {"tol": 1e-10, "symmetry": 1, "t0": rec["t0"]})
 
 
 WORKLOADS = ("single_32x32_explicit", "single_64x128_imex", "batch16_64x64",

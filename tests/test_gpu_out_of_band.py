@@ -1,0 +1,171 @@
+"""GPU parity on inputs with energy outside the 2/3 band, against the FP64 CPU oracle.
+
+The workload loops are band limited, so on them the input analysis (forward 2-D transform, 2/3
+cut, Nyquist zeroing; Sec. 4.2) only discards rounding.  Here every input carries energy in every
+Fourier mode of the grid: a workload loop plus seeded white noise, or plus modes placed just
+outside the band and at the Nyquist frequencies.  A cut-off one mode too wide, a kept Nyquist
+mode or a wrong fold of the half spectrum changes the results at O(1) and fails these tests.
+
+Each result is compared element by element with the oracle twice: in norm
+(||x_gpu - x_oracle|| / ||x_oracle||) and by its worst element (max |x_gpu - x_oracle| /
+max |x_oracle|), so that an error confined to a few modes is not diluted by the rest.  FP64
+mode at 1e-12, FP32 mode at 1e-5 (the oracle is given the float-rounded input).
+Shapes: the bench loop 64 x 128, the ragged batch Nx = 64 with Ns = 32..256, and the large
+domain 256 x 1024 (L = 100); descents run on each of the three launch paths.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ks_oracle as ko
+from paper_2007_06427_gb300 import ks_loop as K
+from paper_2007_06427_gb300.inputs import (outside_band_modes, spectral_loop,
+                                           with_white_noise)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {K.KS_FP64: 1e-12, K.KS_FP32: 1e-5}
+
+# (L, Nx, [Ns_b], init decay): the bench loop, the ragged batch, the large domain
+SHAPES = {
+    "64x128": (22.0, 64, [128], (2.0, 2.0)),
+    "ragged": (22.0, 64, [32, 64, 128, 256], (2.0, 2.0)),
+    "256x1024": (100.0, 256, [1024], (8.0, 8.0)),
+}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def maxrel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def check(a, b, tol, what):
+    assert rel(a, b) < tol, (what, "norm", rel(a, b))
+    assert maxrel(a, b) < tol, (what, "max", maxrel(a, b))
+
+
+def noisy_loops(L, nx, nss, decay, mode, amp=0.5):
+    us, Ts = [], []
+    for b, n in enumerate(nss):
+        u, T, _ = spectral_loop(b, nx, L, ns=n, T_range=(20.0, 80.0) if L < 50 else (120.0, 120.0),
+                                decay=decay)
+        u = with_white_noise(u, b, amp)
+        if mode == K.KS_FP32:
+            u = u.astype(np.float32).astype(np.float64)
+        us.append(u)
+        Ts.append(T)
+    return us, Ts
+
+
+def to_dev(us, Ts, mode):
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    u = torch.from_numpy(np.concatenate([a.ravel() for a in us])).to("cuda", dt)
+    T = torch.tensor(Ts, dtype=torch.float64, device="cuda")
+    return u, T
+
+
+def split(flat, nx, nss):
+    out, o = [], 0
+    for n in nss:
+        out.append(flat[o:o + n * nx].reshape(n, nx))
+        o += n * nx
+    return out
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+@pytest.mark.parametrize("shape", list(SHAPES))
+def test_noisy_residual_and_gradient_match_oracle(shape, mode):
+    """r, G, J and dJ/dT of loops carrying white noise in every mode of the grid."""
+    L, nx, nss, decay = SHAPES[shape]
+    us, Ts = noisy_loops(L, nx, nss, decay, mode)
+    u, T = to_dev(us, Ts, mode)
+    B = len(nss)
+    with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15) as h:
+        r = torch.empty_like(u)
+        G = torch.empty_like(u)
+        J = torch.empty(B, dtype=torch.float64, device="cuda")
+        dJdT = torch.empty_like(J)
+        K.ks_residual(h.handle, u, T, r, J)
+        K.ks_adjoint_grad(h.handle, u, T, G, dJdT)
+        torch.cuda.synchronize()
+    rs = split(r.double().cpu().numpy(), nx, nss)
+    Gs = split(G.double().cpu().numpy(), nx, nss)
+    tol = TOL[mode]
+    for b in range(B):
+        ref = ko.adjoint_grad(us[b], Ts[b], L)
+        res = ko.residual(us[b], Ts[b], L)
+        check(rs[b], res["r"], tol, ("r", b))
+        check(Gs[b], ref["G"], tol, ("G", b))
+        assert abs(J[b].item() - res["J"]) <= tol * res["J"], (b, J[b].item(), res["J"])
+        assert abs(dJdT[b].item() - ref["dJdT"]) <= tol * abs(ref["dJdT"]), (b, dJdT[b].item(), ref["dJdT"])
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+@pytest.mark.parametrize("shape", list(SHAPES))
+def test_noisy_descent_matches_oracle_on_every_path(shape, mode, path):
+    """The resident state loaded from a noisy field (ks_set_state projects it), stepped by
+    ks_step on launch path 0 (cluster-resident), 1 (grid-persistent) or 2 (per-phase), read
+    back on the grid: u and T against the oracle's descent from the same field."""
+    L, nx, nss, decay = SHAPES[shape]
+    nsteps = 1 if nx == 256 else 3
+    us, Ts = noisy_loops(L, nx, nss, decay, mode)
+    u, T = to_dev(us, Ts, mode)
+    with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15) as h:
+        K.ks_set_option(h.handle, "path", path)
+        K.ks_set_state(h.handle, u, T)
+        for _ in range(nsteps):
+            K.ks_step(h.handle, 1, 0.0)
+        K.ks_get_state(h.handle, u, T)
+        torch.cuda.synchronize()
+    out = split(u.double().cpu().numpy(), nx, nss)
+    tol = TOL[mode]
+    for b in range(len(nss)):
+        d = ko.descend(us[b], Ts[b], L, 0.15, ko.IMEX, nsteps)
+        check(out[b], d["u"], tol, ("u", b))
+        assert abs(T[b].item() - d["T"]) < tol * d["T"], (b, T[b].item(), d["T"])
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+@pytest.mark.parametrize("shape", ["64x128", "ragged"])
+def test_modes_outside_the_band_are_cut(shape, mode):
+    """Adding modes just outside the band (|j| = Kx + 1, |k| = Ks + 1) and at the Nyquist
+    frequencies leaves r, G, J and dJ/dT unchanged: their projection is zero.  Compared with
+    the GPU's own results on the band-limited loop and with the oracle."""
+    L, nx, nss, decay = SHAPES[shape]
+    base, Ts = [], []
+    for b, n in enumerate(nss):
+        u0, T0, _ = spectral_loop(b, nx, L, ns=n, T_range=(20.0, 80.0), decay=decay)
+        base.append(u0)
+        Ts.append(T0)
+    edge = [a + outside_band_modes(nx, a.shape[0]) for a in base]
+    if mode == K.KS_FP32:
+        base = [a.astype(np.float32).astype(np.float64) for a in base]
+        edge = [a.astype(np.float32).astype(np.float64) for a in edge]
+    res = {}
+    with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15) as h:
+        for name, us in (("base", base), ("edge", edge)):
+            u, T = to_dev(us, Ts, mode)
+            r = torch.empty_like(u)
+            G = torch.empty_like(u)
+            J = torch.empty(len(nss), dtype=torch.float64, device="cuda")
+            dJdT = torch.empty_like(J)
+            K.ks_residual(h.handle, u, T, r, J)
+            K.ks_adjoint_grad(h.handle, u, T, G, dJdT)
+            torch.cuda.synchronize()
+            res[name] = (split(r.double().cpu().numpy(), nx, nss),
+                         split(G.double().cpu().numpy(), nx, nss), J.cpu().numpy(), dJdT.cpu().numpy())
+    tol = TOL[mode]
+    for b in range(len(nss)):
+        ref = ko.adjoint_grad(edge[b], Ts[b], L)
+        r_ref = ko.grid(nx, nss[b], L).real_grid(ref["rh"])
+        for name in ("base", "edge"):
+            rs, Gs, J, dJdT = res[name]
+            check(rs[b], r_ref, tol, (name, "r", b))
+            check(Gs[b], ref["G"], tol, (name, "G", b))
+            assert abs(J[b] - ref["J"]) <= tol * ref["J"]
+            assert abs(dJdT[b] - ref["dJdT"]) <= tol * abs(ref["dJdT"])
