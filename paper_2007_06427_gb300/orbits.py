@@ -105,21 +105,42 @@ def descend_guesses(guesses: List[Guess], L: float, dtau: float = 0.15, tol: flo
     return out
 
 
+@dataclass
+class RefineResult:
+    u: np.ndarray         # final loop u[n, m]
+    T: float
+    steps: int
+    sqrtJ: float
+    status: int
+    extrapolations: int   # moves of App. C kept
+    rejected: int         # moves of App. C dropped
+
+
 def refine(u: np.ndarray, T: float, L: float, dtau: float = 0.15, tol: float = 1e-10,
-           max_steps: int = 4_000_000, symmetric: bool = True, device: str = "cuda"):
-    """Continue one loop with the extrapolated mixed descent (App. C); returns the AccelResult."""
+           max_steps: int = 4_000_000, symmetric: bool = True, device: str = "cuda",
+           chunk: int = 5000, switch_tol: float = 1e-5) -> RefineResult:
+    """Continue one loop with the mixed-precision descent and the extrapolation of App. C, both
+    inside ks_descend (a KS_MIXED handle with the "extrapolate" knob; the float phase ends at
+    sqrt(J) = switch_tol, about the float floor, or when sqrt(J) stalls)."""
     import torch
     from . import ks_loop as K
-    from .accel import descend_extrapolated_mixed
     ns, nx = u.shape
-    with K.KSLoop(L, nx, [ns], K.KS_FP32, K.KS_IMEX, dtau) as h32, \
-            K.KSLoop(L, nx, [ns], K.KS_FP64, K.KS_IMEX, dtau) as h64:
+    ut = torch.tensor(u.ravel(), dtype=torch.float64, device=device)
+    Tt = torch.tensor([T], dtype=torch.float64, device=device)
+    steps = torch.zeros(1, dtype=torch.int64, device=device)
+    sq = torch.zeros(1, dtype=torch.float64, device=device)
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    with K.KSLoop(L, nx, [ns], K.KS_MIXED, K.KS_IMEX, dtau, tol=tol, switch_tol=switch_tol,
+                  max_steps=max_steps, chunk=chunk) as h:
         if symmetric:
-            K.ks_set_option(h32.handle, "symmetry", 1)
-            K.ks_set_option(h64.handle, "symmetry", 1)
-        ut = torch.tensor(u.ravel(), device=device)
-        return descend_extrapolated_mixed(h32, h64, ut, T, tol=tol, max_steps=max_steps,
-                                          chunk=5000)
+            K.ks_set_option(h.handle, "symmetry", 1)
+        K.ks_set_option(h.handle, "extrapolate", 1)
+        K.ks_descend(h.handle, ut, Tt, max_steps, tol, steps, sq, st)
+        kept = K.ks_get_option(h.handle, "extrapolations")
+        dropped = K.ks_get_option(h.handle, "extrapolations_rejected")
+    return RefineResult(u=ut.cpu().numpy().reshape(ns, nx), T=float(Tt.item()),
+                        steps=int(steps.item()), sqrtJ=float(sq.item()), status=int(st.item()),
+                        extrapolations=kept, rejected=dropped)
 
 
 def search(L: float = 39.0, nx: int = 64, ns: int = 64, t_end: float = 3000.0,
@@ -129,7 +150,8 @@ def search(L: float = 39.0, nx: int = 64, ns: int = 64, t_end: float = 3000.0,
     """The whole pipeline; returns (guesses, results, seconds for the run and the descent).
 
     refine_best > 0: that many periodic loops with the smallest sqrt(J) that did not
-    converge in the batched descent continue with the extrapolated mixed descent."""
+    converge in the batched descent continue alone with the extrapolated mixed descent
+    (``refine``)."""
     t0 = time.perf_counter()
     ts, us = chaotic_run(L, nx, t_end, seed=seed, symmetric=symmetric)
     gs = recurrence_loops(ts, us, L, ns, T_range=T_range, tol=rec_tol, t_min=t_min,
@@ -143,8 +165,7 @@ def search(L: float = 39.0, nx: int = 64, ns: int = 64, t_end: float = 3000.0,
     from . import ks_loop as K
     for i in cand:
         a = refine(states[i], res[i].T, L, tol=tol, max_steps=refine_steps, symmetric=symmetric)
-        ub = a.u.double().cpu().numpy().reshape(states[i].shape)
-        kind, norm, ratio = classify(ub, L)
+        kind, norm, ratio = classify(a.u, L)
         r = res[i]
         r.refined_steps, r.extrapolations = a.steps, a.extrapolations
         r.T, r.sqrtJ, r.kind, r.norm, r.ds_ratio = a.T, a.sqrtJ, kind, norm, ratio

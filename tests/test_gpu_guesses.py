@@ -55,3 +55,33 @@ def test_descent_from_centre_symmetric_guess_at_L39():
     assert np.array_equal(a[1:, :, 0], -a[1:, ::-1, 0]) and np.array_equal(a[1:, :, 1], a[1:, ::-1, 1])
     v = u.cpu().numpy().reshape(ns, nx)
     assert np.abs(v + np.roll(v[:, ::-1], 1, axis=1)).max() < 1e-12 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("xi", [False, True])
+def test_recurrence_loop_residual_matches_oracle(xi):
+    """The stored recurrence loop at L = 39 (nonlinear content from a chaotic run, not a seeded
+    spectral loop): r, J, G and dJ/dT through the C ABI against the oracle at the FP64 tolerance,
+    in norm and by the worst element, with and without the centre-symmetric projection."""
+    from oracle import ks_oracle as ko
+    from paper_2007_06427_gb300.inputs import orbit_guess
+    w = orbit_guess()
+    u0 = w.u[0]
+    u = torch.tensor(u0.ravel(), device="cuda")
+    T = torch.tensor(w.T0, dtype=torch.float64, device="cuda")
+    with K.KSLoop(w.L, w.nx, w.ns, K.KS_FP64) as h:
+        if xi:
+            K.ks_set_option(h.handle, "symmetry", 1)
+        r = torch.empty_like(u)
+        G = torch.empty_like(u)
+        J = torch.empty(1, dtype=torch.float64, device="cuda")
+        dJdT = torch.empty(1, dtype=torch.float64, device="cuda")
+        K.ks_residual(h.handle, u, T, r, J)
+        K.ks_adjoint_grad(h.handle, u, T, G, dJdT)
+        torch.cuda.synchronize()
+    ref = ko.adjoint_grad(u0, w.T0[0], w.L, xi=xi)
+    r_ref = ko.grid(w.nx, w.ns[0], w.L).real_grid(ref["rh"])
+    for a, b in ((r.cpu().numpy().reshape(64, 64), r_ref), (G.cpu().numpy().reshape(64, 64), ref["G"])):
+        assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(b)
+        assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+    assert abs(J.item() - ref["J"]) < 1e-12 * ref["J"]
+    assert abs(dJdT.item() - ref["dJdT"]) < 1e-12 * abs(ref["dJdT"])

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2007_06427_gb300 import inputs
+from paper_2007_06427_gb300.inputs import spectral_loop
 
 EXPECTED = {
     # name: (loops, L, Nx, Ns set, T0 range (lo, hi) or fixed, scheme, dtau)
@@ -45,3 +46,25 @@ def test_loops_follow_the_recipe(name):
         assert np.abs(c[:, 0]).max() < 1e-13                        # j = 0 column zeroed
         if name.startswith("paper_L39_xi"):
             assert np.abs(u + np.roll(u[:, ::-1], 1, axis=1)).max() < 1e-12   # odd in x
+
+
+def test_stored_orbit_guess_is_a_centre_symmetric_recurrence_loop():
+    """The stored loop at the paper's setting: 64 x 64 at L = 39, band limited, odd in x, a
+    period in the recurrence range, and far closer to a solution than a random loop of the same
+    size (its J, evaluated by the oracle, is a small fraction of its energy)."""
+    import math
+    from oracle import ks_oracle as ko
+    from paper_2007_06427_gb300.inputs import orbit_guess
+    w = orbit_guess()
+    assert (w.L, w.nx, w.ns, w.batch) == (39.0, 64, [64], 1)
+    assert 20.0 <= w.T0[0] <= 32.0
+    u = w.u[0]
+    g = ko.grid(64, 64, 39.0)
+    spec = g.to_spectral(u)
+    assert np.abs(np.where(g.mask, 0, spec)).max() < 1e-13 * np.abs(spec).max()
+    assert np.abs(u + np.roll(u[:, ::-1], 1, axis=1)).max() < 1e-13 * np.abs(u).max()
+    J = ko.residual(u, w.T0[0], w.L, xi=True)["J"]
+    e = w.L * np.mean(u * u)
+    rnd, _, _ = spectral_loop(0, 64, 39.0, ns=64, T0=w.T0[0], symmetric=True)
+    J_rnd = ko.residual(rnd * math.sqrt(np.mean(u * u)), w.T0[0], w.L, xi=True)["J"]
+    assert J / e < 0.03 and J < 0.05 * J_rnd, (J / e, J / J_rnd)   # measured 0.0099, 0.017
