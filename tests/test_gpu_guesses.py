@@ -60,8 +60,15 @@ def test_descent_from_centre_symmetric_guess_at_L39():
 @pytest.mark.parametrize("xi", [False, True])
 def test_recurrence_loop_residual_matches_oracle(xi):
     """The stored recurrence loop at L = 39 (nonlinear content from a chaotic run, not a seeded
-    spectral loop): r, J, G and dJ/dT through the C ABI against the oracle at the FP64 tolerance,
-    in norm and by the worst element, with and without the centre-symmetric projection."""
+    spectral loop): r, J and dJ/dT through the C ABI against the oracle at the FP64 tolerance
+    (1e-12), in norm and by the worst element, with and without the centre-symmetric projection.
+
+    G is held to 5e-12: the x-spectrum of a chaotic state falls off exponentially (the band edge
+    j = 21 holds 1e-4 of the largest mode), so the rounding that any FP64 analysis leaves at the
+    band edge, amplified by the q^4 symbols of r and of G, limits every FP64 evaluation of G on
+    this loop to ~1e-12.  Against an extended-precision (80-bit) evaluation of the same formulas
+    the oracle's G is off by 1.7e-12 and the kernels' item arithmetic (run on the host) by 1.1e-12,
+    while r stays within 1.2e-13."""
     from oracle import ks_oracle as ko
     from paper_2007_06427_gb300.inputs import orbit_guess
     w = orbit_guess()
@@ -80,8 +87,9 @@ def test_recurrence_loop_residual_matches_oracle(xi):
         torch.cuda.synchronize()
     ref = ko.adjoint_grad(u0, w.T0[0], w.L, xi=xi)
     r_ref = ko.grid(w.nx, w.ns[0], w.L).real_grid(ref["rh"])
-    for a, b in ((r.cpu().numpy().reshape(64, 64), r_ref), (G.cpu().numpy().reshape(64, 64), ref["G"])):
-        assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(b)
-        assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+    for a, b, tol in ((r.cpu().numpy().reshape(64, 64), r_ref, 1e-12),
+                      (G.cpu().numpy().reshape(64, 64), ref["G"], 5e-12)):
+        assert np.linalg.norm(a - b) < tol * np.linalg.norm(b)
+        assert np.abs(a - b).max() < tol * np.abs(b).max()
     assert abs(J.item() - ref["J"]) < 1e-12 * ref["J"]
     assert abs(dJdT.item() - ref["dJdT"]) < 1e-12 * abs(ref["dJdT"])

@@ -113,7 +113,9 @@ def test_noisy_descent_matches_oracle_on_every_path(shape, mode, path):
     back on the grid: u and T against the oracle's descent from the same field."""
     L, nx, nss, decay = SHAPES[shape]
     nsteps = 1 if nx == 256 else 3
-    us, Ts = noisy_loops(L, nx, nss, decay, mode)
+    # noise of rms 0.2: large enough to fill every mode, small enough that T stays near T0 (at
+    # rms 0.5 the huge residual of the noise sends T below zero within three steps)
+    us, Ts = noisy_loops(L, nx, nss, decay, mode, amp=0.2)
     u, T = to_dev(us, Ts, mode)
     with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15) as h:
         K.ks_set_option(h.handle, "path", path)
@@ -127,19 +129,23 @@ def test_noisy_descent_matches_oracle_on_every_path(shape, mode, path):
     for b in range(len(nss)):
         d = ko.descend(us[b], Ts[b], L, 0.15, ko.IMEX, nsteps)
         check(out[b], d["u"], tol, ("u", b))
-        assert abs(T[b].item() - d["T"]) < tol * d["T"], (b, T[b].item(), d["T"])
+        assert abs(T[b].item() - d["T"]) < tol * abs(d["T"]), (b, T[b].item(), d["T"])
 
 
 @pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
 @pytest.mark.parametrize("shape", ["64x128", "ragged"])
 def test_modes_outside_the_band_are_cut(shape, mode):
     """Adding modes just outside the band (|j| = Kx + 1, |k| = Ks + 1) and at the Nyquist
-    frequencies leaves r, G, J and dJ/dT unchanged: their projection is zero.  Compared with
-    the GPU's own results on the band-limited loop and with the oracle."""
+    frequencies leaves r, G, J and dJ/dT unchanged: their projection is zero.  The GPU's results
+    on the loop with and without those modes are both compared with the oracle's."""
     L, nx, nss, decay = SHAPES[shape]
     base, Ts = [], []
     for b, n in enumerate(nss):
-        u0, T0, _ = spectral_loop(b, nx, L, ns=n, T_range=(20.0, 80.0), decay=decay)
+        # a flat band-limited spectrum (no decay): the band edge carries as much as the rest, so
+        # the rounding that the outside modes leave in the band stays far below every retained
+        # mode (with the workloads' steep decay the edge modes are ~1e-14 of the largest, and
+        # that rounding, times the q^4 and q^8 symbols, limits any FP64 evaluation to ~1e-12)
+        u0, T0, _ = spectral_loop(b, nx, L, ns=n, T_range=(20.0, 80.0), decay=(1e6, 1e6))
         base.append(u0)
         Ts.append(T0)
     edge = [a + outside_band_modes(nx, a.shape[0]) for a in base]
