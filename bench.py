@@ -1,13 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the KS loop tau-descent on GB300: tau-step gridpoints/s and (unless --no-to-tol)
-wall time to sqrt(J) < 1e-10 for plain FP64 against FP32-bulk + FP64-finish, plus the FP64
-descent with the extrapolation of App. C.
+wall time to sqrt(J) < 1e-10, plain FP64 against FP32 bulk + FP64 finish.
 
 One bench step is one tau-step of the whole hot path (residual, reductions, adjoint, update)
-over the workload's batch, on the resident state in HBM.  The L2 cache is flushed (a 256 MiB
-write) before every timed step and each step is timed with CUDA events on the launch stream.
-Under torchrun every rank descends its own seeded loops (weak scaling, no collective on the
-data path); the reported time is the max over ranks.
+over the workload's batch, on the resident state in HBM.  The K timed steps run as the descent
+driver runs them: ks_step launches of up to ``--chunk`` tau-steps each (the loop state stays in
+shared memory inside a launch), each launch preceded by an L2 flush (a 256 MiB write) and timed
+with CUDA events on the launch stream.  A latency line times one tau-step per launch the same
+way.  Under torchrun the workload's batch is replicated per rank with the same recipe (seeds
+continue across ranks) and sharded with shard.partition: every rank descends its own loops
+(weak scaling, no collective on the data path); the reported time is the max over ranks.
+
+Time to sqrt(J) < tol is measured on the single 64 x 128 loop, on a recurrence loop at the
+paper's setting (L = 39, centre-symmetric) that converges to a periodic orbit, on the ragged
+batch of 256 loops and on the 8 loops of 256 x 1024; a compact ``time_to_tol_summary`` closes
+the JSON line.
 
 ``--impl reference`` times the CPU oracle (NumPy FP64, naive DFTs) on the same workload.
 """
@@ -37,13 +44,17 @@ DEFAULT_WORKLOAD = "single_64x128_imex"
 PEAK_TFLOPS = {"f64": 1.25, "f32": 152 * 128 * 2 * 2.070e9 / 1e12}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--chunk", type=int, default=1000,
+                    help="tau-steps per timed launch (the descent driver's chunk)")
+    ap.add_argument("--latency-steps", type=int, default=100,
+                    help="one-step launches timed for the latency line (0: none)")
     ap.add_argument("--autotune", action="store_true",
                     help="create the timed handles with the autotuner (launch shape by timing)")
     ap.add_argument("--batch", type=int, default=None,
@@ -54,28 +65,44 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-to-tol", action="store_true",
-                    help="skip the FP64 vs mixed descent to sqrt(J) < tol")
+                    help="skip every time-to-tolerance run")
     ap.add_argument("--no-fp32", action="store_true", help="skip the float-path throughput line")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the ragged-batch throughput line")
     ap.add_argument("--to-tol-max-steps", type=int, default=1_000_000)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--switch-tol", type=float, default=0.0,
                     help="mixed: switch to double once sqrt(J) (evaluated in double) <= this; "
                          "0: switch when it stops falling over the stall window")
+    ap.add_argument("--orbit-max-steps", type=int, default=2_000_000,
+                    help="step cap of the periodic-orbit descents (0: skip them)")
+    ap.add_argument("--batched-max-steps", type=int, default=100_000,
+                    help="step cap of the ragged-batch descents to tolerance (0: skip them)")
+    ap.add_argument("--large-max-steps", type=int, default=20_000,
+                    help="step cap of the 256 x 1024 descents to tolerance (0: skip them)")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case: load the workload, run 3 x K tau-steps, no timing")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------------------
-# algorithmic work per launch (FFT counted as 5 n log2 n flops per complex transform)
+# algorithmic work per launch
 # ---------------------------------------------------------------------------------------
+def survey_step_flops(nx: int, nss) -> float:
+    """Algorithmic flops of one tau-step of the batch by the hot path's work count: five 2-D real
+    transforms of Nx Ns points, each 2.5 N log2 N flops (an unpruned real FFT), plus 40 flops per
+    gridpoint for the spectral and pointwise terms."""
+    return sum(5 * 2.5 * nx * n * math.log2(nx * n) + 40.0 * nx * n for n in nss)
+
+
 def fft_flops(n: int) -> float:
     return 5.0 * n * math.log2(n)
 
 
 def kernel_flops(kind: str, nx: int, nss, steps_per_launch: int = 1) -> float:
-    """Algorithmic flops of one launch of `kind` over the batch.
+    """Flops of one launch of `kind` by the pruned count: every complex transform the kernels
+    actually run (5 n log2 n), only over the retained x-modes in s, plus the pointwise terms.
 
     Fused kernels (cluster-resident, grid-persistent) run whole tau-steps: their work is the
     sum of the four phases times the steps per launch."""
@@ -94,6 +121,15 @@ def kernel_flops(kind: str, nx: int, nss, steps_per_launch: int = 1) -> float:
     if kind.startswith("cols_update"):
         return sum(nkx * (2 * fft_flops(n) + 30.0 * (2 * (n // 3) + 1)) for n in nss)
     return 0.0
+
+
+def survey_kernel_flops(kind: str, nx: int, nss, steps_per_launch: int = 1) -> float:
+    """Flops of one launch by the hot path's work count (``survey_step_flops``); a per-phase
+    kernel takes the share of the step that the pruned count gives its phase."""
+    if kind.startswith("cluster") or kind.startswith("persist"):
+        return steps_per_launch * survey_step_flops(nx, nss)
+    pruned = step_flops(nx, nss)
+    return kernel_flops(kind, nx, nss) * survey_step_flops(nx, nss) / pruned if pruned else 0.0
 
 
 def code_tokens(src: str) -> str:
@@ -116,8 +152,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch from the committed ncu capture, if the CUDA sources still match."""
+def measured_traffic(workload: str, kernel: str, steps_per_launch: int = 1):
+    """DRAM bytes per launch from the committed ncu capture, if the CUDA sources still match and
+    the capture ran the same number of tau-steps per launch."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -125,7 +162,7 @@ def measured_traffic(workload: str, kernel: str):
         return None
     if t.get("source_sha") != kernel_source_hash():
         return None
-    e = t.get("kernels", {}).get(f"{workload}/{kernel}")
+    e = t.get("kernels", {}).get(f"{workload}/{kernel}/{steps_per_launch}")
     return None if e is None else e.get("bytes_per_launch")
 
 
@@ -245,6 +282,27 @@ def dist_env():
     return ws, rank, lrank
 
 
+def workload_config(w) -> dict:
+    """The workload as both arms name it (identical keys and values in both lines)."""
+    return {"workload": w.name, "L": w.L, "nx": w.nx, "ns": w.ns[:8], "batch": w.batch,
+            "gridpoints": w.gridpoints, "scheme": "imex" if w.scheme else "explicit",
+            "dtau": w.dtau}
+
+
+def rank_workload(name: str, batch, ws: int, rank: int):
+    """This rank's loops: the workload's batch replicated ws times with the same recipe (seeds
+    0 .. ws * B - 1) and sharded with shard.partition (longest loops first, balanced by
+    Ns * Nx); weak scaling, every rank about one workload's batch."""
+    from paper_2007_06427_gb300.inputs import workload
+    from paper_2007_06427_gb300 import shard
+    base = workload(name, batch)
+    if ws == 1:
+        return base
+    full = workload(name, seeds=range(ws * base.batch))
+    mine = shard.partition(full.ns, full.nx, ws)[rank]
+    return workload(name, seeds=mine)
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -261,9 +319,7 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "L": w.L, "nx": w.nx, "ns": w.ns[:8],
-                   "batch": w.batch, "scheme": "imex" if w.scheme else "explicit",
-                   "dtau": w.dtau},
+        "config": workload_config(w),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{r['steps']} oracle tau-steps of the workload (NumPy FP64 "
                                    "dense DFTs, single-threaded BLAS)"},
@@ -273,11 +329,136 @@ def reference_arm(args):
     return 0
 
 
+def timed_launches(K, h, nsteps: int, chunk: int, flush, stream, no_flush: bool):
+    """nsteps tau-steps of the resident state in launches of up to `chunk` steps, each after an
+    L2 flush, each timed with CUDA events on the launch stream.  Returns [(ms, steps)]."""
+    import torch
+    evs = []
+    done = 0
+    while done < nsteps:
+        c = min(chunk, nsteps - done)
+        if not no_flush:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K.ks_step(h.handle, c, 0.0, stream)
+        e1.record(stream)
+        evs.append((e0, e1, c))
+        done += c
+    torch.cuda.synchronize()
+    return [(a.elapsed_time(b), c) for a, b, c in evs]
+
+
+def profile_pass(K, h, nsteps: int, chunk: int, flush, stream, no_flush: bool):
+    """An untimed pass with the same launch pattern and the library's per-kernel event timing
+    on.  Returns ({kind: (ms, launches)}, library launches, tau-steps).  The timed region runs
+    without the library's own events, which would add device work to every launch."""
+    K.ks_profile(h.handle, True)
+    K.ks_profile_read(h.handle, reset=True)
+    timed_launches(K, h, nsteps, chunk, flush, stream, no_flush)
+    prof, launches = K.ks_profile_read(h.handle, reset=True)
+    K.ks_profile(h.handle, False)
+    return prof, launches, nsteps
+
+
+def roofline_entry(prof, prof_steps: int, ms_per_step: float, w, nx, nss):
+    """Roofline of the dominant kernel.  Its mean launch duration is the timed region's time per
+    tau-step (CUDA events on the launch stream) times its share of the library's device time in
+    the profiled pass, divided by its launches per tau-step; its work is the hot path's flop
+    count (five unpruned real 2-D transforms plus 40 flops per gridpoint per tau-step), the
+    pruned count of the transforms actually run given beside it."""
+    dname = max(prof, key=lambda k: prof[k][0]) if prof else None
+    if not dname:
+        return None
+    ms_k, cnt = prof[dname]
+    tot = max(sum(v[0] for v in prof.values()), 1e-30)
+    share = ms_k / tot
+    launches_per_step = cnt / prof_steps
+    steps_per_launch = 1.0 / launches_per_step if dname[:7] in ("cluster", "persist") else 1
+    ms_launch = ms_per_step * share / max(launches_per_step, 1e-30)
+    spl = int(round(steps_per_launch))
+    fl = survey_kernel_flops(dname, nx, nss, spl)
+    fl_pruned = kernel_flops(dname, nx, nss, spl)
+    ach = fl / (ms_launch / 1e3) / 1e12 if ms_launch > 0 else 0.0
+    pk = PEAK_TFLOPS["f32" if "_f32" in dname and "adj" not in dname else "f64"]
+    trf = measured_traffic(w.name, dname, spl)
+    return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+            "frac": ach / pk, "traffic": trf, "kernel": dname,
+            "flops_per_launch": fl, "steps_per_launch": spl, "ms_per_launch": ms_launch,
+            "ms_per_launch_profiled": ms_k / cnt, "share": share,
+            "flops_per_launch_pruned": fl_pruned,
+            "frac_pruned": fl_pruned / (ms_launch / 1e3) / 1e12 / pk if ms_launch > 0 else 0.0,
+            "peak_source": ("nominal GB300 FP64 rate (1.25 TFLOP/s)" if pk == PEAK_TFLOPS["f64"]
+                            else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")}
+
+
+def annotate_sms(roof, K, h, mode, batch, dev):
+    """For the cluster-resident kernel: the SMs a launch occupies (one CTA per SM; C CTAs per
+    loop) and the roofline fraction against the peak of those SMs alone."""
+    import torch
+    if not roof or K.ks_get_option(h.handle, "path") != 0:
+        return roof
+    C = K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64")
+    if C <= 0:
+        return roof
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    used = min(n_sms, C * batch)
+    roof["sms_used"] = used
+    roof["frac_of_sms_used"] = roof["frac"] * n_sms / used
+    return roof
+
+
+def add_probe(roof, probe):
+    """The measured pipe peak of the roofline's precision (the library's FMA probe) and the
+    fraction of it, beside the nominal ones."""
+    if not roof:
+        return
+    key = "f64" if roof["peak"] == PEAK_TFLOPS["f64"] else "f32"
+    p = probe.get(key)
+    roof["peak_probe"] = p
+    roof["frac_of_probe"] = roof["achieved"] / p if p else None
+
+
+def launch_shape(K, h, mode, autotuned):
+    return {"path": K.ks_get_option(h.handle, "path"),
+            "cluster": K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64"),
+            "threads": K.ks_get_option(h.handle, "cluster_threads"),
+            "autotuned": bool(autotuned)}
+
+
+def throughput(args, w, mode, dev, flush, K, nsteps, autotune=False, latency_steps=0):
+    """The steady-state line of one handle: nsteps tau-steps in launches of args.chunk, each
+    after a flush; plus, if latency_steps, one-step launches (the latency of a single step)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    u = torch.from_numpy(w.packed()).to(dev, dt)
+    T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
+    h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, autotune=int(autotune))
+    K.ks_set_state(h.handle, u, T, stream)
+    # warm-up: W tau-steps in the timed launch pattern (untimed)
+    timed_launches(K, h, args.warmup, args.chunk, flush, stream, args.no_flush)
+    prof, plaunch, psteps = profile_pass(K, h, min(nsteps, 2 * args.chunk), args.chunk, flush,
+                                         stream, args.no_flush)
+    out = {"h": h, "prof": prof, "prof_steps": psteps, "launches_per_step": plaunch / psteps}
+    if latency_steps:
+        lprof, ll, ls_ = profile_pass(K, h, latency_steps, 1, flush, stream, args.no_flush)
+        lt = timed_launches(K, h, latency_steps, 1, flush, stream, args.no_flush)
+        lms = sum(m for m, _ in lt) / latency_steps
+        lroof = roofline_entry(lprof, ls_, lms, w, w.nx, w.ns)
+        out["latency"] = {"value": w.gridpoints / (lms / 1e3), "unit": UNIT,
+                          "ms_per_step": lms, "steps": latency_steps,
+                          "note": "one tau-step per launch, L2 flushed before each",
+                          "roofline": annotate_sms(lroof, K, h, mode, w.batch, dev)}
+    out["events"] = timed_launches(K, h, nsteps, args.chunk, flush, stream, args.no_flush)
+    return out
+
+
 def ours_arm(args):
     import numpy as np
     import torch
     from paper_2007_06427_gb300 import ks_loop as K
-    from paper_2007_06427_gb300.inputs import workload
 
     ws, rank, lrank = dist_env()
     torch.cuda.set_device(lrank)
@@ -306,59 +487,47 @@ def ours_arm(args):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {str(e)[-200:]}"}
 
-    w = workload(args.workload, args.batch)
-    if ws > 1:
-        # every rank descends its own loops: seeds offset by rank
-        from paper_2007_06427_gb300.inputs import make_loops
-        base = workload(args.workload, args.batch)
-        w = make_loops(base.name, base.nx, base.L, [rank * base.batch + i for i in range(base.batch)],
-                       ns=base.ns[0] if len(set(base.ns)) == 1 else None,
-                       ns_choices=None if len(set(base.ns)) == 1 else (32, 64, 128, 256),
-                       T_range=(20.0, 80.0), scheme=base.scheme, dtau=base.dtau)
+    # the FP64 and FP32 pipe peaks of this GPU, measured by the library's FMA probe (context for
+    # the roofline fractions, which are taken against the nominal rates)
+    probe = {}
+    for key, prec in (("f64", K.KS_FP64), ("f32", K.KS_FP32)):
+        try:
+            probe[key] = K.ks_probe_peak(prec)
+        except Exception:  # keep the line if the probe fails
+            probe[key] = None
+    w = rank_workload(args.workload, args.batch, ws, rank)
     mode = K.KS_FP32 if args.mode == "fp32" else K.KS_FP64
     dt = torch.float32 if mode == K.KS_FP32 else torch.float64
     nx, nss = w.nx, w.ns
     gp = w.gridpoints
-    stream = torch.cuda.current_stream(dev)
-    u = torch.from_numpy(w.packed()).to(dev, dt)
-    T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
-    h = K.KSLoop(w.L, nx, nss, mode, w.scheme, w.dtau, autotune=int(args.autotune))
-    K.ks_set_state(h.handle, u, T, stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
-    for _ in range(args.warmup):
-        K.ks_step(h.handle, 1, 0.0, stream)
-    torch.cuda.synchronize(dev)
-    prof, per_step = profile_pass(K, h, args, flush, stream, dev)
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
     clk = ClockSampler(lrank)
     clk.start()
-    evs = []
-    for _ in range(args.steps):
-        if not args.no_flush:
-            flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        K.ks_step(h.handle, 1, 0.0, stream)
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize(dev)
+    tp = throughput(args, w, mode, dev, flush, K, args.steps, args.autotune,
+                    args.latency_steps if ws == 1 else 0)
+    clocks = clk.stop()
     if pg:
         pg.barrier()
-    clocks = clk.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    launches = int(round(per_step * args.steps))
+    h = tp["h"]
+    total_ms = sum(m for m, _ in tp["events"])
+    launches = int(round(tp["launches_per_step"] * args.steps))
     tmax = total_ms
     if pg:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         tmax = float(t.item())
-    value = ws * gp * args.steps / (tmax / 1e3)
-
-    roof = annotate_sms(roofline_entry(prof, total_ms / args.steps, w, nx, nss), K, h, mode,
-                        w.batch, dev)
+    if pg:
+        g = torch.tensor([float(gp)], dtype=torch.float64, device=dev)
+        pg.all_reduce(g)
+        gp_all = float(g.item())
+    else:
+        gp_all = float(gp)
+    value = gp_all * args.steps / (tmax / 1e3)
+    roof = annotate_sms(roofline_entry(tp["prof"], tp["prof_steps"], total_ms / args.steps,
+                                       w, nx, nss), K, h, mode, w.batch, dev)
 
     # end to end through the public call with pinned host buffers
     e2e = None
@@ -388,163 +557,83 @@ def ours_arm(args):
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             el = float(t.item())
         ub = hu.numel() * hu.element_size()
-        e2e = {"value": ws * gp * E * args.e2e_calls / el, "unit": UNIT,
+        e2e = {"value": gp_all * E * args.e2e_calls / el, "unit": UNIT,
                "h2d_bytes_per_step": ub + 8 * w.batch,
                "d2h_bytes_per_step": ub + (8 + 8 + 8 + 4) * w.batch,
                "tau_steps_per_call": E,
                "note": "one bench step = one ks_descend call on pinned host buffers"}
+    shape = launch_shape(K, h, mode, args.autotune)
+    h.close()
+
+    fp32 = None
+    if not args.no_fp32 and mode == K.KS_FP64 and ws == 1:
+        t32 = throughput(args, w, K.KS_FP32, dev, flush, K, args.steps)
+        ms32 = sum(m for m, _ in t32["events"])
+        fp32 = {"value": gp * args.steps / (ms32 / 1e3), "unit": UNIT,
+                "ms_per_step": ms32 / args.steps, "dtype": "f32",
+                "gpu_launches": int(round(t32["launches_per_step"] * args.steps)),
+                "roofline": annotate_sms(roofline_entry(t32["prof"], t32["prof_steps"],
+                                                        ms32 / args.steps, w, nx, nss),
+                                         K, t32["h"], K.KS_FP32, w.batch, dev)}
+        t32["h"].close()
+
+    batched = None
+    if not args.no_batched and ws == 1 and args.workload != "ragged256_64xNs":
+        batched = batched_line(args, dev, flush, K)
 
     to_tol = None
     if not args.no_to_tol and ws == 1:
-        to_tol = run_to_tol(args, w, dev)
+        to_tol = run_to_tol(args, w, dev, K)
 
-    fp32 = None
-    if not args.no_fp32 and mode == K.KS_FP64:
-        fp32 = throughput_fp32(args, w, dev, flush, K)
-
-    launch_shape = {"path": K.ks_get_option(h.handle, "path"),
-                    "cluster": K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64"),
-                    "threads": K.ks_get_option(h.handle, "cluster_threads"),
-                    "autotuned": bool(args.autotune)}
-    h.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if mode == K.KS_FP32 else "f64", "data": "synthetic",
-            "config": {"workload": w.name, "L": w.L, "nx": nx, "ns": nss[:8], "batch": w.batch,
-                       "scheme": "imex" if w.scheme else "explicit", "dtau": w.dtau,
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "gridpoints": gp,
-                       "launch": launch_shape},
+            "config": workload_config(w),
+            "timing": {"l2": "flushed (256 MiB write) before every timed launch",
+                       "tau_steps_per_launch": min(args.chunk, args.steps),
+                       "launch": shape},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
-            "kernels_profiled_pass": {"steps": PROFILE_STEPS,
-                                      **{k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}},
+            "kernels_profiled_pass": {k: {"ms": v[0], "launches": v[1]} for k, v in tp["prof"].items()},
         }
-        if to_tol:
-            if cpu and cpu.get("value"):
-                # the oracle at the measured per-step rate for the same step counts (FP64 runs)
-                for key in ("fp64", "fp64_extrapolated"):
-                    if key in to_tol:
-                        n = sum(to_tol[key]["steps"]) if w.batch == 1 else to_tol[key]["steps"][0]
-                        to_tol[key]["cpu_oracle_seconds_extrapolated"] = n * w.gridpoints / cpu["value"]
-            # the whole descent against the roofline: algorithmic flops of its steps over its
-            # wall time (read-backs, monitors and extrapolations included); FP64 runs against
-            # the FP64 peak, mixed runs (mostly FP32 steps) reported as achieved only
-            # flops per loop-step (mean over the batch; exact for a single loop or equal Ns)
-            fl = step_flops(nx, nss) / w.batch
-            for key, v in to_tol.items():
-                if isinstance(v, dict) and v.get("seconds") and len(set(nss)) == 1:
-                    ach = fl * v["total_steps"] / v["seconds"] / 1e12
-                    v["achieved_tflops"] = ach
-                    if key.startswith("fp64"):
-                        v["frac_of_fp64_peak"] = ach / PEAK_TFLOPS["f64"]
-            line["time_to_tol"] = to_tol
+        for entry in (roof, (fp32 or {}).get("roofline"), (batched or {}).get("roofline"),
+                      tp.get("latency", {}).get("roofline")):
+            add_probe(entry, probe)
+        if "latency" in tp:
+            line["latency"] = tp["latency"]
         if fp32:
             line["fp32"] = fp32
+        if batched:
+            line["batched"] = batched
+        if to_tol:
+            attach_cpu_extrapolation(to_tol, cpu, w)
+            line["time_to_tol"] = to_tol
+            line["time_to_tol_summary"] = summarize(to_tol)
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
 
 
-PROFILE_STEPS = 20
-
-
-def profile_pass(K, h, args, flush, stream, dev, nsteps: int = PROFILE_STEPS):
-    """An untimed pass of nsteps bench steps (same pattern: flush, one ks_step) with the
-    library's per-kernel event timing on.  Returns ({kind: (ms, launches)}, launches per step).
-    The timed region runs without the library's own events, which would add device work to
-    every step."""
-    import torch
-    K.ks_profile(h.handle, True)
-    K.ks_profile_read(h.handle, reset=True)
-    for _ in range(nsteps):
-        if not args.no_flush:
-            flush.zero_()
-        K.ks_step(h.handle, 1, 0.0, stream)
-    torch.cuda.synchronize(dev)
-    prof, launches = K.ks_profile_read(h.handle, reset=True)
-    K.ks_profile(h.handle, False)
-    return prof, launches / nsteps
-
-
-def roofline_entry(prof, ms_per_step, w, nx, nss):
-    """Roofline of the dominant kernel: its launch duration is the timed region's mean step time
-    (CUDA events on the launch stream) times the kernel's share of the library's device time in
-    the profiled pass, per launch."""
-    dname = max(prof, key=lambda k: prof[k][0]) if prof else None
-    if not dname:
-        return None
-    ms_k, cnt = prof[dname]
-    tot = max(sum(v[0] for v in prof.values()), 1e-30)
-    share = ms_k / tot
-    launches_per_step = cnt / PROFILE_STEPS
-    ms_launch = ms_per_step * share / max(launches_per_step, 1e-30)
-    fl = kernel_flops(dname, nx, nss)
-    ach = fl / (ms_launch / 1e3) / 1e12 if ms_launch > 0 else 0.0
-    pk = PEAK_TFLOPS["f32" if dname.endswith("f32") else "f64"]
-    return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-            "frac": ach / pk, "traffic": measured_traffic(w.name, dname), "kernel": dname,
-            "flops_per_launch": fl, "ms_per_launch": ms_launch,
-            "ms_per_launch_profiled": ms_k / cnt, "share": share,
-            "peak_source": ("nominal GB300 FP64 rate (1.25 TFLOP/s)" if not dname.endswith("f32")
-                            else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")}
-
-
-def annotate_sms(roof, K, h, mode, batch, dev):
-    """For the cluster-resident kernel: the SMs a launch occupies (one CTA per SM; C CTAs per
-    loop) and the roofline fraction against the peak of those SMs alone."""
-    import torch
-    if not roof or K.ks_get_option(h.handle, "path") != 0:
-        return roof
-    C = K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64")
-    if C <= 0:
-        return roof
-    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    used = min(n_sms, C * batch)
-    roof["sms_used"] = used
-    roof["frac_of_sms_used"] = roof["frac"] * n_sms / used
-    return roof
-
-
-def throughput_fp32(args, w, dev, flush, K):
-    """Same timed loop on an FP32 handle (the bulk phase of a mixed descent)."""
-    import torch
-    stream = torch.cuda.current_stream(dev)
-    u = torch.from_numpy(w.packed()).to(dev, torch.float32)
-    T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
-    h = K.KSLoop(w.L, w.nx, w.ns, K.KS_FP32, w.scheme, w.dtau, autotune=int(args.autotune))
-    K.ks_set_state(h.handle, u, T, stream)
-    for _ in range(args.warmup):
-        K.ks_step(h.handle, 1, 0.0, stream)
-    torch.cuda.synchronize(dev)
-    prof, per_step = profile_pass(K, h, args, flush, stream, dev)
-    evs = []
-    for _ in range(args.steps):
-        if not args.no_flush:
-            flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        K.ks_step(h.handle, 1, 0.0, stream)
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize(dev)
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    out = {"value": w.gridpoints * args.steps / (total_ms / 1e3), "unit": UNIT,
-           "ms_per_step": total_ms / args.steps, "dtype": "f32",
-           "gpu_launches": int(round(per_step * args.steps))}
-    roof = annotate_sms(roofline_entry(prof, total_ms / args.steps, w, w.nx, w.ns), K, h,
-                        K.KS_FP32, w.batch, dev)
-    h.close()
-    if roof:
-        out["roofline"] = roof
+def batched_line(args, dev, flush, K):
+    """Throughput of the ragged batch of 256 loops (Nx = 64, Ns from {32, 64, 128, 256}) in
+    FP64 on the launch shape the autotuner picks, with its own roofline entry."""
+    from paper_2007_06427_gb300.inputs import workload
+    w = workload("ragged256_64xNs")
+    n = max(20, min(args.steps, 200))
+    t = throughput(args, w, K.KS_FP64, dev, flush, K, n, autotune=True)
+    ms = sum(m for m, _ in t["events"])
+    out = {"workload": w.name, "value": w.gridpoints * n / (ms / 1e3), "unit": UNIT,
+           "ms_per_step": ms / n, "steps": n, "dtype": "f64",
+           "launch": launch_shape(K, t["h"], K.KS_FP64, True),
+           "roofline": roofline_entry(t["prof"], t["prof_steps"], ms / n, w, w.nx, w.ns)}
+    t["h"].close()
     return out
 
 
@@ -557,73 +646,162 @@ def outcome_counts(K, st):
     return out
 
 
-def run_to_tol(args, w, dev):
-    """Plain FP64 descent vs FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol;
-    then both again with the extrapolation of App. C inside ks_descend."""
+def descend_variant(K, w, dev, mode, tol, cap, *, switch_tol=0.0, extrapolate=False,
+                    f32_adjoint=None, symmetry=False, chunk=None, u_override=None):
+    """One descent of the whole batch from its initial loops to sqrt(J) < tol or the cap; returns
+    a record with the wall time, per-loop outcomes and the classes reached."""
     import numpy as np
     import torch
-    from paper_2007_06427_gb300 import ks_loop as K
+    from paper_2007_06427_gb300.orbits import classify
+    ck = chunk or (1000 if extrapolate else 2000)
+    h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, tol=tol, switch_tol=switch_tol,
+                 max_steps=cap, chunk=ck)
+    if extrapolate:
+        K.ks_set_option(h.handle, "extrapolate", 1)
+    if symmetry:
+        K.ks_set_option(h.handle, "symmetry", 1)
+    if f32_adjoint is not None:
+        K.ks_set_option(h.handle, "finish_f32_adjoint", int(f32_adjoint))
+    packed = w.packed() if u_override is None else u_override
+    u = torch.from_numpy(packed).to(dev, torch.float64)
+    T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
+    steps = torch.zeros(w.batch, dtype=torch.int64, device=dev)
+    sq = torch.zeros(w.batch, dtype=torch.float64, device=dev)
+    st = torch.zeros(w.batch, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    K.ks_descend(h.handle, u, T, cap, tol, steps, sq, st)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    hs, hq, hp = K.ks_get_history(h.handle, 0)
+    uo = u.cpu().numpy()
+    kinds, off = {}, 0
+    conv = []
+    for b, n in enumerate(w.ns):
+        kind, _, _ = classify(uo[off:off + n * w.nx].reshape(n, w.nx), w.L)
+        off += n * w.nx
+        if int(st[b]) == K.KS_CONVERGED:
+            kinds[kind] = kinds.get(kind, 0) + 1
+            conv.append(b)
+    rec = {"seconds": el, "total_steps": int(steps.sum().item()),
+           "outcomes": outcome_counts(K, st), "converged_classes": kinds,
+           "converged_loops": conv if len(conv) <= 16 else len(conv),
+           "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8], "T": T.tolist()[:8],
+           "switch_tol": switch_tol, "extrapolate": bool(extrapolate), "cap": cap,
+           "gridpoint_steps": int(sum(int(a) * n * w.nx for a, n in zip(steps.tolist(), w.ns)))}
+    if mode == K.KS_MIXED:
+        rec["finish_f32_adjoint"] = K.ks_get_option(h.handle, "finish_f32_adjoint")
+        rec["loop0_switch_step"] = int(hs[np.nonzero(hp == 0)[0][0]]) if (hp == 0).any() else None
+    if extrapolate:
+        rec["extrapolations"] = K.ks_get_option(h.handle, "extrapolations")
+        rec["rejected"] = K.ks_get_option(h.handle, "extrapolations_rejected")
+    marks = {}
+    for target in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
+        idx = np.nonzero(hq < target)[0]
+        if idx.size:
+            marks[f"{target:.0e}"] = int(hs[idx[0]])
+    rec["loop0_first_step_below"] = marks
+    rec["_st"] = st.cpu().numpy()
+    h.close()
+    return rec
+
+
+def run_to_tol(args, w, dev, K):
+    """Plain FP64 descent against FP32 bulk + FP64 finish, from the same loops, to sqrt(J) < tol,
+    with and without the extrapolation of App. C, on: the bench workload; a recurrence loop at
+    the paper's setting that reaches a periodic orbit; the ragged batch of 256 loops; the eight
+    256 x 1024 loops (FP32 to 1e-5, then FP64).  Batched runs stop at a stated step cap."""
+    from paper_2007_06427_gb300.inputs import orbit_guess, workload
     out = {}
     clk = ClockSampler(dev.index if dev.index is not None else 0)
     clk.start()
-    for name, mode in (("fp64", K.KS_FP64), ("mixed", K.KS_MIXED)):
-        h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, tol=args.tol,
-                     switch_tol=args.switch_tol, max_steps=args.to_tol_max_steps, chunk=2000)
-        u = torch.from_numpy(w.packed()).to(dev, torch.float64)
-        T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
-        steps = torch.zeros(w.batch, dtype=torch.int64, device=dev)
-        sq = torch.zeros(w.batch, dtype=torch.float64, device=dev)
-        st = torch.zeros(w.batch, dtype=torch.int32, device=dev)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        K.ks_descend(h.handle, u, T, args.to_tol_max_steps, args.tol, steps, sq, st)
-        torch.cuda.synchronize(dev)
-        el = time.perf_counter() - t0
-        hs, hq, hp = K.ks_get_history(h.handle, 0)
-        marks = {}
-        for target in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
-            idx = np.nonzero(hq < target)[0]
-            if idx.size:
-                marks[f"{target:.0e}"] = int(hs[idx[0]])
-        switch = int(hs[np.nonzero(hp == 0)[0][0]]) if (name == "mixed" and (hp == 0).any()) else None
-        out[name] = {"seconds": el, "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8],
-                     "status": [K.STATUS_NAMES.get(int(s), str(int(s))) for s in st.tolist()[:8]],
-                     "outcomes": outcome_counts(K, st), "total_steps": int(steps.sum().item()),
-                     "T": T.tolist()[:8], "loop0_first_step_below": marks,
-                     "loop0_switch_step": switch,
-                     "loop0_history": [[int(a), float(c)] for a, c in zip(hs[::max(1, len(hs) // 40)], hq[::max(1, len(hq) // 40)])]}
-        h.close()
-    # the same two descents with the extrapolation of App. C inside ks_descend
-    # (the extrapolated mixed run switches to double at sqrt(J) = 1e-5, about the float floor of
-    # this loop: the jumps of the extrapolation restart the stall window the plain run waits on)
-    for name, mode in (("fp64_extrapolated", K.KS_FP64), ("mixed_extrapolated", K.KS_MIXED)):
-        sw = max(args.switch_tol, 1e-5) if mode == K.KS_MIXED else 0.0
-        h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, tol=args.tol,
-                     switch_tol=sw, max_steps=args.to_tol_max_steps, chunk=1000)
-        K.ks_set_option(h.handle, "extrapolate", 1)
-        u = torch.from_numpy(w.packed()).to(dev, torch.float64)
-        T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
-        steps = torch.zeros(w.batch, dtype=torch.int64, device=dev)
-        sq = torch.zeros(w.batch, dtype=torch.float64, device=dev)
-        st = torch.zeros(w.batch, dtype=torch.int32, device=dev)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        K.ks_descend(h.handle, u, T, args.to_tol_max_steps, args.tol, steps, sq, st)
-        torch.cuda.synchronize(dev)
-        el = time.perf_counter() - t0
-        hs, hq, hp = K.ks_get_history(h.handle, 0)
-        switch = int(hs[np.nonzero(hp == 0)[0][0]]) if (mode == K.KS_MIXED and (hp == 0).any()) else None
-        out[name] = {"seconds": el, "steps": steps.tolist()[:8], "sqrtJ": sq.tolist()[:8],
-                     "status": [K.STATUS_NAMES.get(int(v), str(int(v))) for v in st.tolist()[:8]],
-                     "outcomes": outcome_counts(K, st), "total_steps": int(steps.sum().item()),
-                     "T": T.tolist()[:8],
-                     "extrapolations": K.ks_get_option(h.handle, "extrapolations"),
-                     "rejected": K.ks_get_option(h.handle, "extrapolations_rejected"),
-                     "loop0_switch_step": switch, "switch_tol": sw,
-                     "note": "App. C inside ks_descend: from sqrt(J) = 1e-3, geometric extrapolation "
-                             "each time sqrt(J) (evaluated in double every 1000 steps) halves"}
-        h.close()
+    cap, tol = args.to_tol_max_steps, args.tol
+    single = {}
+    single["fp64"] = descend_variant(K, w, dev, K.KS_FP64, tol, cap)
+    single["mixed"] = descend_variant(K, w, dev, K.KS_MIXED, tol, cap, switch_tol=args.switch_tol)
+    single["mixed_f64_finish"] = descend_variant(K, w, dev, K.KS_MIXED, tol, cap,
+                                                 switch_tol=args.switch_tol, f32_adjoint=0)
+    single["fp64_extrapolated"] = descend_variant(K, w, dev, K.KS_FP64, tol, cap, extrapolate=True)
+    # the extrapolated mixed run switches to double at sqrt(J) = 1e-5, about the float floor of
+    # this loop: the jumps of the extrapolation restart the stall window the plain run waits on
+    single["mixed_extrapolated"] = descend_variant(K, w, dev, K.KS_MIXED, tol, cap,
+                                                   switch_tol=max(args.switch_tol, 1e-5),
+                                                   extrapolate=True)
+    out[w.name] = single
+    if args.orbit_max_steps > 0:
+        g = orbit_guess()
+        oc = args.orbit_max_steps
+        orb = {"note": "centre-symmetric recurrence loop of a chaotic run at L = 39 (T0 = %.2f), "
+                       "descended with the symmetry knob; the paper lists a periodic orbit of "
+                       "period 25.37 at this setting (Sec. 4.4)" % g.T0[0]}
+        for name, mode, ext in (("fp64", K.KS_FP64, False), ("mixed", K.KS_MIXED, False),
+                                ("fp64_extrapolated", K.KS_FP64, True),
+                                ("mixed_extrapolated", K.KS_MIXED, True)):
+            orb[name] = descend_variant(K, g, dev, mode, tol, oc, extrapolate=ext, symmetry=True,
+                                        switch_tol=1e-5 if (ext and mode == K.KS_MIXED) else 0.0)
+        out[g.name] = orb
+    if args.batched_max_steps > 0:
+        rg = workload("ragged256_64xNs")
+        bc = args.batched_max_steps
+        bt = {}
+        for name, mode, ext in (("fp64_extrapolated", K.KS_FP64, True),
+                                ("mixed_extrapolated", K.KS_MIXED, True)):
+            bt[name] = descend_variant(K, rg, dev, mode, tol, bc, extrapolate=ext,
+                                       switch_tol=1e-5 if mode == K.KS_MIXED else 0.0)
+        out[rg.name] = bt
+    if args.large_max_steps > 0:
+        lg = workload("large8_256x1024")
+        lc = args.large_max_steps
+        lt = {"fp64": descend_variant(K, lg, dev, K.KS_FP64, tol, lc),
+              "fp32_then_fp64": descend_variant(K, lg, dev, K.KS_MIXED, tol, lc, switch_tol=1e-5)}
+        out[lg.name] = lt
+    for grp in out.values():
+        common = None
+        for k, v in grp.items():
+            if isinstance(v, dict) and "_st" in v:
+                conv = set(int(i) for i in (v["_st"] == K.KS_CONVERGED).nonzero()[0])
+                common = conv if common is None else common & conv
+        for k, v in list(grp.items()):
+            if isinstance(v, dict) and "_st" in v:
+                del v["_st"]
+        if common is not None:
+            grp["converged_in_every_variant"] = len(common)
     out["clocks"] = clk.stop()
+    return out
+
+
+def attach_cpu_extrapolation(to_tol, cpu, w):
+    """The oracle at its measured per-step rate for the step counts of the FP64 descents of the
+    bench workload (labelled as extrapolated), and each variant's achieved flop rate."""
+    grp = to_tol.get(w.name, {})
+    for key, v in grp.items():
+        if not isinstance(v, dict) or "seconds" not in v:
+            continue
+        if cpu and cpu.get("value") and key.startswith("fp64"):
+            v["cpu_oracle_seconds_extrapolated"] = v["gridpoint_steps"] / cpu["value"]
+        if v["seconds"] > 0:
+            ach = survey_step_flops(w.nx, w.ns) / w.gridpoints * v["gridpoint_steps"] / v["seconds"] / 1e12
+            v["achieved_tflops"] = ach
+            if key.startswith("fp64"):
+                v["frac_of_fp64_peak"] = ach / PEAK_TFLOPS["f64"]
+
+
+def summarize(to_tol) -> dict:
+    """Compact record of every time-to-tolerance variant: [seconds, total tau-steps of the batch,
+    loops converged / batch]."""
+    out = {}
+    for wl, grp in to_tol.items():
+        if not isinstance(grp, dict) or wl == "clocks":
+            continue
+        row = {}
+        for k, v in grp.items():
+            if isinstance(v, dict) and "seconds" in v:
+                n = sum(v["outcomes"].values())
+                row[k] = [round(v["seconds"], 3), v["total_steps"],
+                          f"{v['outcomes'].get('converged', 0)}/{n}"]
+        if "converged_in_every_variant" in grp:
+            row["common"] = grp["converged_in_every_variant"]
+        out[wl] = row
     return out
 
 
