@@ -26,7 +26,7 @@ _EXPORTS = ("ks_loop_create", "ks_destroy", "ks_residual", "ks_adjoint_grad", "k
             "ks_set_state", "ks_step", "ks_get_state", "ks_last_error", "ks_version",
             "ks_config_sizeof", "ks_profile", "ks_profile_read", "ks_set_option", "ks_get_option",
             "ks_residual_noalloc", "ks_get_history", "ks_autotune", "ks_band_size",
-            "ks_get_band", "ks_set_band")
+            "ks_get_band", "ks_set_band", "ks_probe_peak")
 
 
 class KsError(RuntimeError):
@@ -83,10 +83,11 @@ def load_library(path: str = LIB_PATH):
     lib.ks_get_band.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ks_set_band.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ks_profile_read.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    lib.ks_probe_peak.argtypes = [i32, i32, vp, vp]
     for f in ("ks_loop_create", "ks_destroy", "ks_residual", "ks_adjoint_grad", "ks_descend",
               "ks_set_state", "ks_step", "ks_get_state", "ks_profile", "ks_profile_read",
               "ks_set_option", "ks_get_option", "ks_residual_noalloc", "ks_get_history",
-              "ks_autotune", "ks_get_band", "ks_set_band"):
+              "ks_autotune", "ks_get_band", "ks_set_band", "ks_probe_peak"):
         getattr(lib, f).restype = i32
     lib.ks_last_error.restype = ctypes.c_char_p
     lib.ks_version.restype = ctypes.c_char_p
@@ -231,6 +232,15 @@ def ks_get_history(h, b: int):
     if n:
         lib.ks_get_history(h, int(b), st.ctypes.data, sq.ctypes.data, pr.ctypes.data, n)
     return st, sq, pr
+
+
+def ks_probe_peak(precision: int, iters: int = 0, stream=None) -> float:
+    """Measured FMA peak of the current device in TFLOP/s (KS_FP64 or KS_FP32)."""
+    if iters <= 0:
+        iters = 500 if precision == KS_FP64 else 10000   # ~2 ms and ~0.7 ms per launch on GB300
+    v = ctypes.c_double()
+    _check(load_library().ks_probe_peak(int(precision), int(iters), ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def ks_profile(h, enable: bool) -> None:

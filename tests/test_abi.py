@@ -72,3 +72,15 @@ def test_no_cpu_fallback_without_gpu(lib):
     with pytest.raises(K.KsError) as e:
         K.ks_loop_create(22.0, 32, [32])
     assert e.value.code == K.KS_ERR_CUDA
+
+
+def test_probe_rejects_bad_arguments_and_needs_a_device(lib):
+    import ctypes
+    v = ctypes.c_double(0.0)
+    assert lib.ks_probe_peak(7, 10, ctypes.byref(v), None) == K.KS_ERR_ARG
+    assert lib.ks_probe_peak(K.KS_FP64, 0, ctypes.byref(v), None) == K.KS_ERR_ARG
+    assert lib.ks_probe_peak(K.KS_FP64, 10, None, None) == K.KS_ERR_ARG
+    import torch
+    if not torch.cuda.is_available():
+        assert lib.ks_probe_peak(K.KS_FP64, 10, ctypes.byref(v), None) == K.KS_ERR_CUDA
+        assert v.value == 0.0
