@@ -1,13 +1,22 @@
 """Checkpoint and resume of a descent (host side).
 
 A checkpoint is an .npz file holding the handle's configuration (L, Nx, the Ns list, mode,
-scheme, dtau, tolerances), the band state of every loop (ks_get_band: the Fourier
-coefficients u_hat of Eq. 2D_Fourier, widened to double), T, the step counters, the
-precision each loop descends in, and each loop's convergence history.  Resuming creates a
-handle with the same configuration and installs the band with ks_set_band, so the continued
-descent is bit-identical to an uninterrupted one.  (With the "extrapolate" knob the anchors of
-the extrapolation are not saved: a resumed descent takes new anchors at its first read-back, so
-its later extrapolations can differ from an uninterrupted run's.)
+scheme, dtau, tolerances), its descent knobs (``KNOBS``: symmetry, extrapolation, stall window
+and threshold, mixed finish, chunk, launch path), the band state of every loop (ks_get_band: the
+Fourier coefficients u_hat of Eq. 2D_Fourier, widened to double), T, the step counters, the
+precision each loop descends in, each loop's status and its convergence history.
+
+Resuming creates a handle with the same configuration and knobs and installs the band with
+ks_set_band.  What is and is not restored:
+* every loop that was running continues bit for bit as in an uninterrupted descent (same
+  band, T, counters, precision and knobs);
+* ks_set_band restarts every loop as running, so the saved statuses and histories are returned
+  to the caller (``resume(..., info=True)``) rather than reinstalled: a converged loop freezes
+  again before its next step (its sqrt(J) is below tol), a stalled or diverged one steps on
+  unless the caller leaves it out;
+* with the "extrapolate" knob the anchors of the extrapolation are not saved: a resumed descent
+  takes new anchors at its first read-back, so its later extrapolations can differ from an
+  uninterrupted run's.
 """
 from __future__ import annotations
 
@@ -16,8 +25,12 @@ import numpy as np
 from . import ks_loop as K
 
 _KEYS = ("L", "nx", "ns", "mode", "scheme", "dtau", "tol", "switch_tol", "band", "T", "prec",
-         "steps", "version")
-VERSION = 1
+         "steps", "status", "version")
+VERSION = 2
+# knobs of ks_set_option that change how the descent proceeds (saved and restored)
+KNOBS = ("symmetry", "extrapolate", "extrapolate_start_ppm", "extrapolate_drop_ppm",
+         "stall_window", "stall_drop_ppm", "finish_f32_adjoint", "switch_probe",
+         "switch_probe_steps", "chunk", "path")
 
 
 def save(loop: "K.KSLoop", path: str, tol: float = 1e-10, switch_tol: float = 0.0) -> None:
@@ -27,6 +40,9 @@ def save(loop: "K.KSLoop", path: str, tol: float = 1e-10, switch_tol: float = 0.
     prec = np.zeros(loop.batch, dtype=np.int32)
     steps = np.zeros(loop.batch, dtype=np.int64)
     K.ks_get_band(loop.handle, band, T, prec, steps)
+    status = np.zeros(loop.batch, dtype=np.int32)
+    K.ks_get_state(loop.handle, None, None, None, None, status)
+    knobs = {f"knob_{k}": K.ks_get_option(loop.handle, k) for k in KNOBS}
     hist = {}
     for b in range(loop.batch):
         hs, hq, hp = K.ks_get_history(loop.handle, b)
@@ -35,11 +51,13 @@ def save(loop: "K.KSLoop", path: str, tol: float = 1e-10, switch_tol: float = 0.
         hist[f"hist_prec_{b}"] = hp
     np.savez(path, L=loop.L, nx=loop.nx, ns=np.asarray(loop.ns, dtype=np.int64), mode=loop.mode,
              scheme=loop.scheme, dtau=loop.dtau, tol=tol, switch_tol=switch_tol, band=band, T=T,
-             prec=prec, steps=steps, version=VERSION, **hist)
+             prec=prec, steps=steps, status=status, version=VERSION, **knobs, **hist)
 
 
-def resume(path: str, **create_kw) -> "K.KSLoop":
-    """A new handle holding the checkpointed descent (raises ValueError on a bad file)."""
+def resume(path: str, info: bool = False, **create_kw):
+    """A new handle holding the checkpointed descent, its knobs restored (raises ValueError on a
+    bad file).  With info, returns (handle, {"status": [...], "history": {b: (steps, sqrtJ,
+    prec)}}) as saved."""
     with np.load(path) as z:
         missing = [k for k in _KEYS if k not in z.files]
         if missing:
@@ -54,7 +72,13 @@ def resume(path: str, **create_kw) -> "K.KSLoop":
         if band.size != 2 * K.ks_band_size(loop.handle) or z["T"].size != loop.batch:
             loop.close()
             raise ValueError(f"checkpoint {path} does not match its own configuration")
+        for k in KNOBS:
+            if f"knob_{k}" in z.files:
+                K.ks_set_option(loop.handle, k, int(z[f"knob_{k}"]))
         K.ks_set_band(loop.handle, band, np.ascontiguousarray(z["T"], dtype=np.float64),
                       np.ascontiguousarray(z["prec"], dtype=np.int32),
                       np.ascontiguousarray(z["steps"], dtype=np.int64))
-    return loop
+        saved = {"status": [int(v) for v in z["status"]],
+                 "history": {b: (z[f"hist_steps_{b}"], z[f"hist_sqrtJ_{b}"], z[f"hist_prec_{b}"])
+                             for b in range(loop.batch) if f"hist_steps_{b}" in z.files}}
+    return (loop, saved) if info else loop

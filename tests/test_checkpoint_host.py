@@ -10,12 +10,12 @@ def _fields(**over):
     f = dict(L=22.0, nx=32, ns=np.array([32], dtype=np.int64), mode=0, scheme=1, dtau=0.15,
              tol=1e-10, switch_tol=0.0, band=np.zeros(2 * 11 * 21), T=np.array([40.0]),
              prec=np.zeros(1, dtype=np.int32), steps=np.zeros(1, dtype=np.int64),
-             version=C.VERSION)
+             status=np.zeros(1, dtype=np.int32), version=C.VERSION)
     f.update(over)
     return f
 
 
-@pytest.mark.parametrize("drop", ["band", "T", "version", "ns"])
+@pytest.mark.parametrize("drop", ["band", "T", "version", "ns", "status"])
 def test_missing_field_is_refused(tmp_path, drop):
     f = _fields()
     del f[drop]

@@ -70,3 +70,34 @@ def test_corrupt_checkpoint_rejected(tmp_path):
     np.savez(tmp_path / "bad2.npz", **z)
     with pytest.raises(ValueError):
         checkpoint.resume(str(tmp_path / "bad2.npz"))
+
+
+def test_knobs_status_and_history_travel_with_the_checkpoint(tmp_path):
+    """The descent knobs are restored on resume; statuses and histories come back to the caller
+    as saved (a loop that converged before the checkpoint freezes again before its next step)."""
+    L, nx, nss = 22.0, 32, [32, 32]
+    u, T = _state(K.KS_FP64, nx, nss, L)
+    u[: 32 * nx] = 0.0                              # loop 0: u = 0, converged at once
+    knobs = {"symmetry": 1, "extrapolate": 1, "extrapolate_start_ppm": 2000,
+             "extrapolate_drop_ppm": 400000, "stall_window": 12345, "stall_drop_ppm": 77,
+             "chunk": 50}
+    with K.KSLoop(L, nx, nss, K.KS_FP64, K.KS_IMEX, 0.15) as h:
+        for k, v in knobs.items():
+            K.ks_set_option(h.handle, k, v)
+        K.ks_descend(h.handle, u, T, 100, 1e-10)
+        checkpoint.save(h, str(tmp_path / "ck.npz"))
+        hs0, hq0, _ = K.ks_get_history(h.handle, 1)
+    h2, saved = checkpoint.resume(str(tmp_path / "ck.npz"), info=True)
+    try:
+        for k, v in knobs.items():
+            assert K.ks_get_option(h2.handle, k) == v, k
+        assert saved["status"] == [K.KS_CONVERGED, K.KS_STEP_CAP]
+        np.testing.assert_array_equal(saved["history"][1][0], hs0)
+        np.testing.assert_array_equal(saved["history"][1][1], hq0)
+        steps = torch.zeros(2, dtype=torch.int64, device="cuda")
+        st = torch.zeros(2, dtype=torch.int32, device="cuda")
+        K.ks_step(h2.handle, 5, 1e-10)
+        K.ks_get_state(h2.handle, None, None, steps, None, st)
+        assert steps.tolist() == [0, 105] and st.tolist()[0] == K.KS_CONVERGED
+    finally:
+        h2.close()
