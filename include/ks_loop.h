@@ -59,6 +59,8 @@ enum {
     KS_MIXED = 2   /* ks_descend: float steps while sqrt(J), evaluated in double at every
                       read-back, exceeds switch_tol and keeps falling; then double steps to the
                       end (the adjoint half of each in float unless "finish_f32_adjoint" is 0).
+                      "Keeps falling" is decided by a probe (knob "switch_probe") once the
+                      float phase's rate bends, with the stall window as a fallback.
                       A loop whose float rounding alone more than doubles sqrt(J) (one that
                       starts below the float floor) takes double steps from the start.
                       Other calls compute in double */
@@ -231,15 +233,32 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *   "test_barrier_timeout" test hook: 1 makes every grid barrier of the path-1 kernel wait
  *                    for one arrival that never comes, so each wait runs out (about a second)
  *                    and the next read-back returns KS_ERR_TIMEOUT; 0 (default) restores it
+ *   "switch_probe"   KS_MIXED handles: 1 (default): the float phase of each loop is watched
+ *                    in windows of stall_window / 4 steps; when its rate (decades of sqrt(J),
+ *                    evaluated in double, per step) falls below an eighth of the best rate over
+ *                    windows below sqrt(J) = 1e-2, a copy of the loop takes "switch_probe_steps"
+ *                    double steps (a polish).  If the polish removes a fifth or more of sqrt(J)
+ *                    beyond what its steps give at the best rate, the float value is mostly
+ *                    rounding noise and the float steps keep converging beneath it: the loop
+ *                    stays in float until the stall window ends the phase.  If it removes less
+ *                    and descends at least four times faster than the float phase now does, the
+ *                    float arithmetic holds the descent back: the loop switches to double at once
+ *                    and continues from the polished copy (its step counter includes the
+ *                    polish's steps).  Otherwise the bend was the loop's own dynamics; it stays
+ *                    in float and may be probed again after stall_window steps.  0: switch only
+ *                    on switch_tol or the stall window.
+ *   "switch_probe_steps"  double steps of a probe, 1 .. 1e6 (default 1000)
  *   "finish_f32_adjoint"  KS_MIXED handles: 1 (default): the finishing steps keep the state,
  *                    the residual, J, dJ/dT and the update in double and form only the descent
  *                    direction G (the adjoint half of a step) in float; 0: all-double finish */
 KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
 
-/* Read a knob or a derived launch parameter: "path", "finish_f32_adjoint", "cluster_f64",
+/* Read a knob or a derived launch parameter: "path", "finish_f32_adjoint", "switch_probe",
+ * "switch_probe_steps", "cluster_f64",
  * "cluster_f32", "cluster_mixed_finish" (cluster
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
- * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "chunk", "symmetry",
+ * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "stall_drop_ppm",
+ * "chunk", "symmetry",
  * "extrapolate", "extrapolate_start_ppm", "extrapolate_drop_ppm", "extrapolations",
  * "extrapolations_rejected". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);
@@ -284,6 +303,15 @@ KS_API int ks_residual_noalloc(double L, int nx, int ns, const double* u, double
  * Clears the resident state (call ks_set_state afterwards).  All candidates give the same
  * results bit for bit; only the time differs. */
 KS_API int ks_autotune(ks_loop_t h);
+
+/* Measured arithmetic peak of the current device for the roofline of the hot path, which is
+ * bound by the FP64 pipe (double steps) or the FP32 pipe (float steps), not by HBM.  The paper
+ * has no counterpart: this is a measurement utility.  Launches a grid of (SMs x resident blocks
+ * of 256 threads), each thread running iters rounds of 8 independent fused multiply-add chains
+ * in the given precision (KS_FP64 or KS_FP32) with no memory traffic, once to warm up and once
+ * timed with CUDA events on `stream`; *tflops = 2 x FMAs / time in TFLOP/s.  Synchronises
+ * `stream`.  KS_ERR_ARG for another precision, iters < 1 or a null tflops. */
+KS_API int ks_probe_peak(int precision, int iters, double* tflops, void* stream);
 
 /* Message for the last non-zero return on the calling thread ("" if none). */
 KS_API const char* ks_last_error(void);

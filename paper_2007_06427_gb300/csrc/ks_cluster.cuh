@@ -3,7 +3,10 @@
 // A loop's whole working set lives in the distributed shared memory of one cluster of C CTAs
 // (1 <= C <= 16) for a chunk of tau-steps:
 //   * column j (retained x-mode, 0..Kx) is owned by rank j % C, slot j / C: its band values
-//     u_hat, r_hat and its mixed-array column M[j][n] (n = 0..Ns-1) sit in that rank's SMEM;
+//     u_hat, r_hat and its mixed-array column M[j][n] (n = 0..Ns-1) sit in that rank's SMEM.  In
+//     the centre-symmetric subspace (p.xi) the columns go by pairs (2p + 1, 2p + 2): pair p is
+//     owned by rank p % C, slots 2 (p / C) and 2 (p / C) + 1, and each pair shares one complex
+//     s-transform (see col_pair_item in ks_items.cuh); column 0 is zero and owned by no rank;
 //   * rows n are split in contiguous blocks of an even number of rows per rank; a rank keeps
 //     the grid values of u for its rows between the two row phases (in SMEM, or in the global
 //     U array when the plan cannot hold them).
@@ -17,6 +20,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "ks_items.cuh"
 
@@ -51,8 +55,8 @@ __host__ __device__ inline int cluster_rows_per_rank(int ns, int C) {
 template <typename R>
 __device__ __forceinline__ void col_fft_inplace(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                                 const cpx<R>* tw, int nthr = 0) {
-    cpx<R>* r = nthr > 0 ? fft_batch<R, true>(a, b, lg, cnt, dir, tw, nthr)
-                         : fft_warp<R, true>(a, b, lg, cnt, dir, tw);
+    cpx<R>* r = nthr > 0 ? fft_col<R, true>(a, b, lg, cnt, dir, tw, nthr)
+                         : fft_col_warp<R, true>(a, b, lg, cnt, dir, tw);
     if (r != a) {
         const int n = cnt << lg;
         const int NT = nthr > 0 ? nthr : (int)blockDim.x;
@@ -107,6 +111,10 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nx = d.nx, lgnx = d.lgnx, kx = d.kx, nkx = d.nkx, B = d.B;
     const int rmax = cp.rmax;
+    const bool xi = p.xi != 0;
+    // owner rank and slot of x-mode j (j >= 1 in the subspace)
+    auto own_rank = [&](int j) { return xi ? ((j - 1) >> 1) % C : j % C; };
+    auto own_slot = [&](int j) { return xi ? 2 * (((j - 1) >> 1) / C) + ((j - 1) & 1) : j / C; };
     cpx<R>* Mloc = reinterpret_cast<cpx<R>*>(smem + cp.off_M);   // owned columns: P / W
     cpx<R>* Rin = reinterpret_cast<cpx<R>*>(smem + cp.off_rin);  // own rows: v / rho, [j][r]
     cpx<R>* uhl = reinterpret_cast<cpx<R>*>(smem + cp.off_uh);
@@ -141,6 +149,10 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         cp_async<sizeof(R)>(s_cq + i, p.cq + i);
         cp_async<sizeof(RA)>(s_lina + i, ta.lin + i);
     }
+    if (xi && tid == 0) {  // column 0 is zero in the subspace and owned by no rank
+        part[0] = Part{};
+        part[nkx] = Part{};
+    }
     const int nm = max(nx, cp.nsmax);  // longest transform of the launch
     load_twiddles(tws, p.tw, nm);
     if (!kSame) load_twiddles(tws_a, ta.tw, nm);
@@ -159,7 +171,12 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         const long long moff_b = one ? 0 : p.moff[b], goff_b = one ? 0 : p.goff[b];
         double T = p.T[(size_t)par0 * B + b];
         double wT = p.wT[(size_t)par0 * B + b];
-        const int ncol = (rank < nkx) ? (nkx - rank + C - 1) / C : 0;
+        // local column q <-> x-mode j (in the subspace by pairs; a second column past Kx is a
+        // ghost that holds zeros and is never stored)
+        const int npr = (kx + 1) >> 1;
+        const int ncol = xi ? ((rank < npr) ? 2 * ((npr - rank + C - 1) / C) : 0)
+                            : ((rank < nkx) ? (nkx - rank + C - 1) / C : 0);
+        auto colj = [&](int q) { return xi ? 2 * (rank + (q >> 1) * C) + 1 + (q & 1) : rank + q * C; };
         const int rpr = cluster_rows_per_rank(ns, C);
         const int row0 = rank * rpr;
         const int nrow = (row0 < ns) ? min(rpr, ns - row0) : 0;
@@ -170,13 +187,18 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         auto load_state = [&]() {
             for (int i = tid; i < ncol * nk; i += nt) {
                 const int q = i / nk, kk = i - q * nk;
-                cp_async<sizeof(cpx<R>)>(uhl + i, p.uh + bo + (size_t)(rank + q * C) * nk + kk);
+                const int j = colj(q);
+                if (j <= kx) cp_async<sizeof(cpx<R>)>(uhl + i, p.uh + bo + (size_t)j * nk + kk);
+                else uhl[i] = mk<R>(0, 0);
             }
             if (use_M) {
                 for (int i = tid; i < nkx * nrow; i += nt) {
                     const int j = i / nrow, r = i - j * nrow;
-                    cp_async<sizeof(cpx<R>)>(Rin + (size_t)j * rmax + r, Mg + (size_t)j * ns + row0 + r);
+                    if (xi && j == 0) Rin[r] = mk<R>(0, 0);  // the zero column of the subspace
+                    else cp_async<sizeof(cpx<R>)>(Rin + (size_t)j * rmax + r, Mg + (size_t)j * ns + row0 + r);
                 }
+            } else if (xi) {
+                for (int r = tid; r < nrow; r += nt) Rin[r] = mk<R>(0, 0);
             }
         };
         if (one) load_state();  // its addresses need no load: issued with the scalars
@@ -198,7 +220,26 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const int q = (2 * i) >> lg, n = (2 * i) & (ns - 1);
                 const int owner = n / rpr;
                 auto* dst = cl.map_shared_rank(RinT, owner);
-                store_pair(dst + (size_t)(rank + q * C) * rmax + (n - owner * rpr), X[2 * i], X[2 * i + 1]);
+                store_pair(dst + (size_t)colj(q) * rmax + (n - owner * rpr), X[2 * i], X[2 * i + 1]);
+            }
+        };
+        // push the s-inverse c of each column pair: column 2p+1 gets Re c, column 2p+2 Im c, as
+        // the imaginary parts (imag = true: u, v) or the real parts (rho)
+        auto push_pairs = [&](const auto* Cp, auto* RinT, bool imag) {
+            typedef typename std::remove_pointer<decltype(RinT)>::type CT;
+            typedef decltype(CT{}.x) X;
+            for (int i = tid; i < (ncol << lg) >> 2; i += nt) {
+                const int pp = (2 * i) >> lg, n = (2 * i) & (ns - 1);
+                const int owner = n / rpr;
+                auto* dst = cl.map_shared_rank(RinT, owner) + (n - owner * rpr);
+                const auto c0 = Cp[2 * i], c1 = Cp[2 * i + 1];
+                const int ja = colj(2 * pp), jb = ja + 1;
+                if (imag) store_pair(dst + (size_t)ja * rmax, mk<X>(0, c0.x), mk<X>(0, c1.x));
+                else store_pair(dst + (size_t)ja * rmax, mk<X>(c0.x, 0), mk<X>(c1.x, 0));
+                if (jb <= kx) {
+                    if (imag) store_pair(dst + (size_t)jb * rmax, mk<X>(0, c0.y), mk<X>(0, c1.y));
+                    else store_pair(dst + (size_t)jb * rmax, mk<X>(c0.y, 0), mk<X>(c1.y, 0));
+                }
             }
         };
 
@@ -206,14 +247,27 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         __syncthreads();
         if (!use_M) {
             // no valid mixed values: prime them from the band (s-inverse of the owned columns)
-            for (int i = tid; i < ncol << lg; i += nt) {
-                const int q = i >> lg, n = i & (ns - 1);
-                const int k = (n < (ns >> 1)) ? n : n - ns;
-                Mloc[i] = (k >= -ks && k <= ks) ? uhl[q * nk + k + ks] : mk<R>(0, 0);
+            if (xi) {
+                for (int i = tid; i < (ncol >> 1) << lg; i += nt) {
+                    const int pp = i >> lg, n = i & (ns - 1);
+                    const int k = (n < (ns >> 1)) ? n : n - ns;
+                    Mloc[i] = (k >= -ks && k <= ks)
+                                  ? xi_join_imag(uhl[(2 * pp) * nk + k + ks], uhl[(2 * pp + 1) * nk + k + ks])
+                                  : mk<R>(0, 0);
+                }
+                __syncthreads();
+                col_fft_inplace(Mloc, scr, lg, ncol >> 1, +1, tws);
+                push_pairs(Mloc, Rin, true);
+            } else {
+                for (int i = tid; i < ncol << lg; i += nt) {
+                    const int q = i >> lg, n = i & (ns - 1);
+                    const int k = (n < (ns >> 1)) ? n : n - ns;
+                    Mloc[i] = (k >= -ks && k <= ks) ? uhl[q * nk + k + ks] : mk<R>(0, 0);
+                }
+                __syncthreads();
+                col_fft_inplace(Mloc, scr, lg, ncol, +1, tws);
+                push_columns(Mloc, Rin);
             }
-            __syncthreads();
-            col_fft_inplace(Mloc, scr, lg, ncol, +1, tws);
-            push_columns(Mloc, Rin);
         }
         cl.sync();
 
@@ -251,14 +305,15 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
                 }
                 __syncthreads();
-                cpx<R>* F = fft_warp<R, true>(Y, z, lgnx, np, -1, tws);
+                cpx<R>* F = fft_pair_warp<R, true>(Y, z, lgnx, np, -1, tws);
                 const int lgp = lgnr - 1;
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
+                    if (xi && j == 0) continue;  // the zero column of the subspace
                     const cpx<R> yj = F[(size_t)pr * nx + j];
                     const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<R> sm = yj + ym, df = yj - ym;
-                    cpx<R>* dst = cl.map_shared_rank(Mloc, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
+                    cpx<R>* dst = cl.map_shared_rank(Mloc, own_rank(j)) + (size_t)own_slot(j) * ns + n0 + 2 * pr;
                     store_pair(dst, scale(sm, h), mk<R>(df.y * h, -df.x * h));
                 }
                 __syncthreads();
@@ -267,12 +322,71 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             cl.sync();
 
             // ======== phase B: columns, r_hat, partials, rho = s-inverse of i q r_hat ========
-            if (ncol > 0) {
+            if (ncol > 0 && xi) {
+                // centre-symmetric subspace: one s-transform per column pair (col_pair_item)
+                const int npair = ncol >> 1;
+                for (int i = tid; i < npair << lg; i += nt) {
+                    const int pp = i >> lg, n = i & (ns - 1);
+                    // a ghost second column (past Kx) holds no data: it packs zeros
+                    const bool hasb = colj(2 * pp + 1) <= kx;
+                    scr[i] = mk<R>(Mloc[((2 * pp) << lg) + n].y, hasb ? Mloc[((2 * pp + 1) << lg) + n].y : (R)0);
+                }
+                __syncthreads();
+                col_fft_inplace(scr, Mloc, lg, npair, -1, tws);
+                const R wTr = (R)wT;
+                for (int pp = 0; pp < npair; ++pp) {
+                    const int ja = colj(2 * pp), jb = ja + 1;
+                    const bool hasb = jb <= kx;
+                    ColAcc<R> acc[2];
+                    if (tid < COL_ACC_LANES) {
+                        const R lin_a = s_lin[ja], q_a = s_qv[ja];
+                        const R lin_b = hasb ? s_lin[jb] : (R)0, q_b = hasb ? s_qv[jb] : (R)0;
+                        const cpx<R>* Cp = scr + (pp << lg);
+                        for (int n = tid; n < ns; n += COL_ACC_LANES) {
+                            const int k = (n < (ns >> 1)) ? n : n - ns;
+                            cpx<R> x = mk<R>(0, 0);
+                            if (k >= -ks && k <= ks) {
+                                const cpx<R> ck = Cp[n], cm = Cp[(ns - n) & (ns - 1)];
+                                const R bk = -(R)k * wTr;
+                                const cpx<R> pa = scale(xi_split_a(ck, cm), ins);
+                                const cpx<R> ua = uhl[(2 * pp) * nk + k + ks];
+                                const cpx<R> ra = mk<R>(lin_a * ua.x - bk * ua.y - pa.x, lin_a * ua.y + bk * ua.x - pa.y);
+                                rhl[(2 * pp) * nk + k + ks] = ra;
+                                acc[0].add(ua, ra, k);
+                                cpx<R> xb = mk<R>(0, 0);
+                                if (hasb) {
+                                    const cpx<R> pb = scale(xi_split_b(ck, cm), ins);
+                                    const cpx<R> ub = uhl[(2 * pp + 1) * nk + k + ks];
+                                    const cpx<R> rb = mk<R>(lin_b * ub.x - bk * ub.y - pb.x, lin_b * ub.y + bk * ub.x - pb.y);
+                                    rhl[(2 * pp + 1) * nk + k + ks] = rb;
+                                    acc[1].add(ub, rb, k);
+                                    xb = mk<R>(-q_b * rb.y, q_b * rb.x);
+                                }
+                                x = xi_join_real(mk<R>(-q_a * ra.y, q_a * ra.x), xb);
+                            }
+                            Mloc_a[(pp << lg) + n] = mk<RA>((RA)x.x, (RA)x.y);
+                        }
+                    }
+                    block_reduce2(acc[0], acc[1], red);
+                    if (tid < C) {
+                        Part* dstp = cl.map_shared_rank(part, tid);
+                        dstp[ja] = acc[0].part_J(2.0);
+                        dstp[nkx + ja] = acc[0].part_L(2.0);
+                        if (hasb) {
+                            dstp[jb] = acc[1].part_J(2.0);
+                            dstp[nkx + jb] = acc[1].part_L(2.0);
+                        }
+                    }
+                }
+                __syncthreads();
+                // inverse of the pairs of i q r_hat (Mloc holds the spectra, scr is scratch)
+                push_pairs(fft_col_warp<RA, true>(Mloc_a, scr_a, lg, npair, +1, tws_a), Rin_a, false);
+            } else if (ncol > 0) {
                 col_fft_inplace(Mloc, scr, lg, ncol, -1, tws);
                 const R wTr = (R)wT;
-                // columns in pairs: one block reduction for two columns' partials.  Element n
-                // of a column is accumulated by thread n mod COL_ACC_LANES, as in the item
-                // kernels, so the partials do not depend on the block size.
+                // columns in pairs: one block reduction for two columns' partials.  Element n of a
+                // column is accumulated by thread n mod COL_ACC_LANES, as in the item kernels, so
+                // the partials do not depend on the block size.
                 for (int q0 = 0; q0 < ncol; q0 += 2) {
                     const bool two = q0 + 1 < ncol;
                     ColAcc<R> acc[2];
@@ -315,7 +429,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 }
                 __syncthreads();
                 // inverse of i q r_hat (scr holds the spectra, Mloc is scratch), then push rho
-                push_columns(fft_warp<RA, true>(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a);
+                push_columns(fft_col_warp<RA, true>(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a);
             }
             cl.sync();
 
@@ -343,7 +457,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     A[(size_t)pr * nx + J] = z;
                 }
                 __syncthreads();
-                cpx<RA>* z = fft_warp<RA, true>(A, Bf, lgnx, np, +1, tws_a);
+                cpx<RA>* z = fft_pair_warp<RA, true>(A, Bf, lgnx, np, +1, tws_a);
                 cpx<RA>* Y = (z == A) ? Bf : A;
                 for (int i = tid; i < np * nx; i += nt) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
@@ -352,13 +466,14 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                                   (RA)Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
                 }
                 __syncthreads();
-                cpx<RA>* F = fft_warp<RA, true>(Y, z, lgnx, np, -1, tws_a);
+                cpx<RA>* F = fft_pair_warp<RA, true>(Y, z, lgnx, np, -1, tws_a);
                 for (int i = tid; i < (nkx << lgp); i += nt) {
                     const int j = i >> lgp, pr = i & (np - 1);
+                    if (xi && j == 0) continue;
                     const cpx<RA> yj = F[(size_t)pr * nx + j];
                     const cpx<RA> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<RA> sm = yj + ym, df = yj - ym;
-                    cpx<RA>* dst = cl.map_shared_rank(Mloc_a, j % C) + (size_t)(j / C) * ns + n0 + 2 * pr;
+                    cpx<RA>* dst = cl.map_shared_rank(Mloc_a, own_rank(j)) + (size_t)own_slot(j) * ns + n0 + 2 * pr;
                     store_pair(dst, scale(sm, h_a), mk<RA>(df.y * h_a, -df.x * h_a));
                 }
                 __syncthreads();
@@ -392,16 +507,82 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     reinterpret_cast<int*>(red + 3)[0] = sv;
                 }
             } else if constexpr (!kFloatAdj) {
-                if (ncol > 0) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a, nt - 32);
+                if (ncol > 0 && xi) {
+                    // pairs: the imaginary columns of W packed two to a transform
+                    for (int i = tid; i < (ncol >> 1) << lg; i += nt - 32) {
+                        const int pp = i >> lg, n = i & (ns - 1);
+                        const bool hasb = colj(2 * pp + 1) <= kx;
+                        scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
+                                          hasb ? Mloc_a[((2 * pp + 1) << lg) + n].y : (RA)0);
+                    }
+                    part_sync(nt - 32);
+                    col_fft_inplace(scr_a, Mloc_a, lg, ncol >> 1, -1, tws_a, nt - 32);
+                } else if (ncol > 0) {
+                    col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a, nt - 32);
+                }
             }
-            if (kFloatAdj && ncol > 0) col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
+            if (kFloatAdj && ncol > 0) {
+                if (xi) {
+                    for (int i = tid; i < (ncol >> 1) << lg; i += nt) {
+                        const int pp = i >> lg, n = i & (ns - 1);
+                        const bool hasb = colj(2 * pp + 1) <= kx;
+                        scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
+                                          hasb ? Mloc_a[((2 * pp + 1) << lg) + n].y : (RA)0);
+                    }
+                    __syncthreads();
+                    col_fft_inplace(scr_a, Mloc_a, lg, ncol >> 1, -1, tws_a);
+                } else {
+                    col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
+                }
+            }
             __syncthreads();
             const double J = red[0], Tnext = red[1], wTnext = red[2];
             st = reinterpret_cast<const int*>(red + 3)[0];
             __syncthreads();
             Jlast = J;
             if (st != ST_RUNNING) break;  // uniform: every rank computed the same J and T
-            if (ncol > 0) {
+            if (ncol > 0 && xi) {
+                // pairs (col_pair_item): G_hat of both columns from the packed transform in scr,
+                // no projection needed (the split keeps the symmetry exactly); the new u_hat of
+                // both packed into Mloc for one inverse transform
+                const int npair = ncol >> 1;
+                const R wTr = (R)wT;
+                const R dt = (R)d.dtau;
+                const R wT2 = wTr * wTr;
+                const RA wTa = (RA)wT;
+                const RA ins_a = (RA)ins;
+                for (int i = tid; i < npair << lg; i += nt) {
+                    const int pp = i >> lg, n = i & (ns - 1);
+                    const int k = (n < (ns >> 1)) ? n : n - ns;
+                    cpx<R> x = mk<R>(0, 0);
+                    if (k >= -ks && k <= ks) {
+                        const int ja = colj(2 * pp), jb = ja + 1;
+                        const cpx<RA> ck = scr_a[i], cm = scr_a[(pp << lg) + ((ns - n) & (ns - 1))];
+                        const RA bk = (RA)k * wTa;
+                        const R kk2 = (R)k * (R)k;
+                        auto update = [&](int q, int j, cpx<RA> whs) {
+                            const cpx<RA> wh = scale(whs, ins_a);
+                            const RA a_lin = s_lina[j];
+                            const cpx<R> rr = rhl[q * nk + k + ks];
+                            const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
+                            const cpx<RA> Ga = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+                            const cpx<R> G = mk<R>((R)Ga.x, (R)Ga.y);
+                            R f = dt;
+                            if (d.scheme == 1) f = dt / ((R)1 + dt * (kk2 * wT2 + s_cq[j]));
+                            cpx<R> u = uhl[q * nk + k + ks];
+                            u = u - scale(G, f);
+                            uhl[q * nk + k + ks] = u;
+                            return u;
+                        };
+                        const cpx<R> ua = update(2 * pp, ja, xi_split_a(ck, cm));
+                        const cpx<R> ub = (jb <= kx) ? update(2 * pp + 1, jb, xi_split_b(ck, cm)) : mk<R>(0, 0);
+                        x = xi_join_imag(ua, ub);
+                    }
+                    Mloc[i] = x;
+                }
+                __syncthreads();
+                push_pairs(fft_col_warp<R, true>(Mloc, scr, lg, npair, +1, tws), Rin, true);
+            } else if (ncol > 0) {
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;
@@ -417,29 +598,13 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     const cpx<RA> G = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
                     return mk<R>((R)G.x, (R)G.y);
                 };
-                if (p.xi) {
-                    // Xi subspace: G_hat of every k into scr first; the update takes the
-                    // projected pair (j, k), (j, -k) from there and writes the new u_hat to Mloc
-                    for (int i = tid; i < ncol << lg; i += nt) {
-                        const int q = i >> lg, n = i & (ns - 1);
-                        const int k = (n < (ns >> 1)) ? n : n - ns;
-                        if (k >= -ks && k <= ks) scr[i] = g_hat(i, q, k);
-                    }
-                    __syncthreads();
-                }
-                cpx<R>* Y = p.xi ? Mloc : scr;
                 for (int i = tid; i < ncol << lg; i += nt) {
                     const int q = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
                     cpx<R> x = mk<R>(0, 0);
                     if (k >= -ks && k <= ks) {
                         const int j = rank + q * C;
-                        cpx<R> G;
-                        if (p.xi)
-                            G = (j == 0) ? mk<R>(0, 0)
-                                         : xi_pair(scr[i], scr[(q << lg) + ((ns - n) & (ns - 1))]);
-                        else
-                            G = g_hat(i, q, k);
+                        const cpx<R> G = g_hat(i, q, k);
                         R f = dt;
                         if (d.scheme == 1) {
                             const R kk2 = (R)k * (R)k;
@@ -450,10 +615,10 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                         uhl[q * nk + k + ks] = u;
                         x = u;
                     }
-                    Y[i] = x;
+                    scr[i] = x;
                 }
                 __syncthreads();
-                push_columns(fft_warp<R, true>(Y, p.xi ? scr : Mloc, lg, ncol, +1, tws), Rin);
+                push_columns(fft_col_warp<R, true>(scr, Mloc, lg, ncol, +1, tws), Rin);
             }
             T = Tnext;
             wT = wTnext;
@@ -464,7 +629,8 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         // ---- write the loop back: band of the owned columns, mixed values of the own rows
         for (int i = tid; i < ncol * nk; i += nt) {
             const int q = i / nk, kk = i - q * nk;
-            p.uh[bo + (size_t)(rank + q * C) * nk + kk] = uhl[i];
+            const int j = colj(q);
+            if (j <= kx) p.uh[bo + (size_t)j * nk + kk] = uhl[i];
         }
         for (int i = tid; i < nkx * nrow; i += nt) {
             const int j = i / nrow, r = i - j * nrow;

@@ -32,11 +32,13 @@
 #include <cmath>
 
 #ifdef KS_HOST_EMULATION
+#define KS_HDX inline
 #define KS_HD inline
 #define KS_TID 0
 #define KS_NT 1
 #define KS_SYNC() ((void)0)
 #else
+#define KS_HDX __host__ __device__ inline  // also called by the host code that sizes launches
 #define KS_HD __device__ __forceinline__
 #define KS_TID ((int)threadIdx.x)
 #define KS_NT ((int)blockDim.x)
@@ -83,6 +85,41 @@ KS_HD cpx<R> scale(cpx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
 // multiply by i*sgn (sgn = +1 or -1)
 template <typename R>
 KS_HD cpx<R> mul_i(cpx<R> a, int sgn) { return sgn > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
+
+// fused multiply-add a * b + c with one rounding, in either precision
+KS_HD double fmx(double a, double b, double c) { return fma(a, b, c); }
+KS_HD float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+
+// v0 + w v (complex) as four fused multiply-adds
+template <typename R>
+KS_HD cpx<R> cfma(cpx<R> v0, cpx<R> w, cpx<R> v) {
+    return mk<R>(fmx(w.x, v.x, fmx(-w.y, v.y, v0.x)), fmx(w.x, v.y, fmx(w.y, v.x, v0.y)));
+}
+
+// 2 a - b (complex) as two fused multiply-adds
+template <typename R>
+KS_HD cpx<R> twice_minus(cpx<R> a, cpx<R> b) {
+    return mk<R>(fmx((R)2, a.x, -b.x), fmx((R)2, a.y, -b.y));
+}
+
+// Radix-4 butterfly of a decimation-in-time pass with twiddles w1, w2, w3 on v1, v2, v3
+// (dir: sign of the exponent).  The twiddle products are fused into the additions that follow
+// them: t0 = v0 + w2 v2 and t2 = w1 v1 + w3 v3 as fused multiply-adds, t1 = v0 - w2 v2 and
+// w1 v1 - w3 v3 as 2 v0 - t0 and 2 w1 v1 - t2: 24 floating-point operations for the butterfly
+// where separate products and additions take 28 (the FP64 pipe bounds the double path).
+template <typename R>
+KS_HD void bfly4_tw(cpx<R> v0, cpx<R> v1, cpx<R> v2, cpx<R> v3, cpx<R> w1, cpx<R> w2, cpx<R> w3,
+                    int dir, cpx<R>& o0, cpx<R>& o1, cpx<R>& o2, cpx<R>& o3) {
+    const cpx<R> a1 = cmul(v1, w1);
+    const cpx<R> t0 = cfma(v0, w2, v2);
+    const cpx<R> t1 = twice_minus(v0, t0);
+    const cpx<R> t2 = cfma(a1, w3, v3);
+    const cpx<R> t3 = mul_i(twice_minus(a1, t2), dir);
+    o0 = t0 + t2;
+    o1 = t1 + t3;
+    o2 = t0 - t2;
+    o3 = t1 - t3;
+}
 
 // ---- compensated float arithmetic (error-free transformations) -----------------------------
 // A float-float value hi + lo (|lo| <= ulp(hi) / 2).  Sums use Knuth's TwoSum, products use an
@@ -314,21 +351,22 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
             const int j = i & (nb - 1);
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+            const cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
             const int jm = j & (span - 1);
+            const int od = ((j - jm) << 2) + jm;
             if (span > 1) {
                 const int t = jm * tu;
-                v1 = cmul(v1, twid<R, SWZ>(tw, t, dir, twsh));
-                v2 = cmul(v2, twid<R, SWZ>(tw, 2 * t, dir, twsh));
-                v3 = cmul(v3, twid<R, SWZ>(tw, 3 * t, dir, twsh));
+                bfly4_tw(v0, v1, v2, v3, twid<R, SWZ>(tw, t, dir, twsh),
+                         twid<R, SWZ>(tw, 2 * t, dir, twsh), twid<R, SWZ>(tw, 3 * t, dir, twsh),
+                         dir, d[od], d[od + span], d[od + 2 * span], d[od + 3 * span]);
+            } else {
+                const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
+                const cpx<R> t3 = mul_i(v1 - v3, dir);
+                d[od] = t0 + t2;
+                d[od + 1] = t1 + t3;
+                d[od + 2] = t0 - t2;
+                d[od + 3] = t1 - t3;
             }
-            const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
-            const cpx<R> t3 = mul_i(v1 - v3, dir);
-            const int od = ((j - jm) << 2) + jm;
-            d[od] = t0 + t2;
-            d[od + span] = t1 + t3;
-            d[od + 2 * span] = t0 - t2;
-            d[od + 3 * span] = t1 - t3;
         }
         if (nthr > 0) part_sync(nthr);
         else KS_SYNC();
@@ -339,6 +377,79 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
         p -= 2;
     }
     return a;
+}
+
+// Radix-2 variant of fft_batch (every pass a radix-2 pass, natural order in and out, same
+// conventions).  A pass has twice the butterflies of a radix-4 pass, so a double transform of
+// a single column keeps twice as many warps busy; with the twiddle product fused into the
+// additions (v0 + w v1 as four fused multiply-adds, v0 - w v1 as 2 v0 minus that) it costs 3
+// floating-point operations per point per radix-2 stage, as the fused radix-4 butterfly does.
+template <typename R, bool SWZ = false>
+KS_HD cpx<R>* fft_batch_r2(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
+                           int nthr = 0, int twsh = 0) {
+#ifdef KS_HOST_EMULATION
+    const int NT = KS_NT;
+#else
+    const int NT = nthr > 0 ? nthr : KS_NT;
+#endif
+    const int n = 1 << lg;
+    const int nb = n >> 1;
+    const int total = cnt * nb;
+    for (int span = 1; span < n; span <<= 1) {
+        const int tu = NMAX / (span * 2);
+        for (int i = KS_TID; i < total; i += NT) {
+            const int f = i >> (lg - 1);
+            const int j = i & (nb - 1);
+            const cpx<R>* s = a + (size_t)f * n;
+            cpx<R>* d = b + (size_t)f * n;
+            const cpx<R> v0 = s[j], v1 = s[j + nb];
+            const int jm = j & (span - 1);
+            const int od = ((j - jm) << 1) + jm;
+            if (span > 1) {
+                const cpx<R> t = cfma(v0, twid<R, SWZ>(tw, jm * tu, dir, twsh), v1);
+                d[od] = t;
+                d[od + span] = twice_minus(v0, t);
+            } else {
+                d[od] = v0 + v1;
+                d[od + 1] = v0 - v1;
+            }
+        }
+        if (nthr > 0) part_sync(nthr);
+        else KS_SYNC();
+        cpx<R>* t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// The s-transforms (columns of the mixed array): in double, radix-2 passes (see fft_batch_r2)
+// unless the library is built with KS_COL_RADIX2=0; in float the radix-4 passes of fft_batch.
+// Every launch form calls this for its s-transforms, so they keep computing the same bits.
+#ifndef KS_COL_RADIX2
+#define KS_COL_RADIX2 1
+#endif
+template <typename R, bool SWZ = false>
+KS_HD cpx<R>* fft_col(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
+                      int nthr = 0, int twsh = 0) {
+    if constexpr (sizeof(R) == 8 && KS_COL_RADIX2) return fft_batch_r2<R, SWZ>(a, b, lg, cnt, dir, tw, nthr, twsh);
+    else return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw, nthr, twsh);
+}
+
+// The x-transforms of row pairs (two real rows packed as one complex row: the forward
+// transforms of the products and of the analysis, the inverse ones of r_x and of the synthesis)
+// have half as many transforms as the batch has rows; in double they take radix-2 passes
+// unless the library is built with KS_PAIR_RADIX2=0.  The transform of z = u + i u_x, one per
+// row, keeps the radix-4 passes.  The choice depends on the transform's role only, so every
+// launch form computes the same bits.
+#ifndef KS_PAIR_RADIX2
+#define KS_PAIR_RADIX2 1
+#endif
+template <typename R, bool SWZ = false>
+KS_HD cpx<R>* fft_pair(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
+                       int nthr = 0, int twsh = 0) {
+    if constexpr (sizeof(R) == 8 && KS_PAIR_RADIX2) return fft_batch_r2<R, SWZ>(a, b, lg, cnt, dir, tw, nthr, twsh);
+    else return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw, nthr, twsh);
 }
 
 // ------------------------------------------------------------------------------------
@@ -387,21 +498,22 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
             const int f = w + (i >> (lg - 2)) * nw, j = i & (nb - 1);
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+            const cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
             const int jm = j & (span - 1);
+            const int od = ((j - jm) << 2) + jm;
             if (span > 1) {
                 const int t = jm * tu;
-                v1 = cmul(v1, twid<R, SWZ>(tw, t, dir));
-                v2 = cmul(v2, twid<R, SWZ>(tw, 2 * t, dir));
-                v3 = cmul(v3, twid<R, SWZ>(tw, 3 * t, dir));
+                bfly4_tw(v0, v1, v2, v3, twid<R, SWZ>(tw, t, dir), twid<R, SWZ>(tw, 2 * t, dir),
+                         twid<R, SWZ>(tw, 3 * t, dir), dir, d[od], d[od + span],
+                         d[od + 2 * span], d[od + 3 * span]);
+            } else {
+                const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
+                const cpx<R> t3 = mul_i(v1 - v3, dir);
+                d[od] = t0 + t2;
+                d[od + 1] = t1 + t3;
+                d[od + 2] = t0 - t2;
+                d[od + 3] = t1 - t3;
             }
-            const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
-            const cpx<R> t3 = mul_i(v1 - v3, dir);
-            const int od = ((j - jm) << 2) + jm;
-            d[od] = t0 + t2;
-            d[od + span] = t1 + t3;
-            d[od + 2 * span] = t0 - t2;
-            d[od + 3 * span] = t1 - t3;
         }
         __syncwarp();
         cpx<R>* t = a;
@@ -455,6 +567,24 @@ template <typename R, bool SWZ = false>
 __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                             const cpx<R>* tw) {
     if constexpr (sizeof(R) == 8) return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw);
+    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw);
+}
+
+// row-pair x-transforms of the cluster kernel: the double ones as fft_pair (block-wide), the float
+// ones warp-owned (the same arithmetic as fft_pair's radix-4 passes)
+template <typename R, bool SWZ = false>
+__device__ __forceinline__ cpx<R>* fft_pair_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
+                                                 const cpx<R>* tw) {
+    if constexpr (sizeof(R) == 8) return fft_pair<R, SWZ>(a, b, lg, cnt, dir, tw);
+    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw);
+}
+
+// s-transforms of the cluster kernel: the double ones as fft_col (block-wide), the float ones
+// warp-owned (the same arithmetic as fft_col's radix-4 passes)
+template <typename R, bool SWZ = false>
+__device__ __forceinline__ cpx<R>* fft_col_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
+                                                const cpx<R>* tw) {
+    if constexpr (sizeof(R) == 8) return fft_col<R, SWZ>(a, b, lg, cnt, dir, tw);
     else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw);
 }
 #endif
@@ -822,13 +952,13 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = mk<R>(ra[m], ra[nx + m]);
         }
         KS_SYNC();
-        cpx<R>* Y = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, -1, p.tw, 0, p.twsh);
+        cpx<R>* Y = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, Y, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_SYNTH) {
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
+        cpx<R>* z = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
         const int total = npairs * nx;
         for (int i = KS_TID; i < total; i += KS_NT) {
             const int pr = i >> lgnx;
@@ -869,14 +999,14 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
         }
         KS_SYNC();
-        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
+        cpx<R>* F = fft_pair<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_ADJ) {
         // r_x rows from the column pass output rho = s-inverse of i q_j r_hat   (a7)
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
+        cpx<R>* z = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
         cpx<R>* Y = (z == A) ? Bf : A;
         const int tp = npairs * nx;
         for (int i = KS_TID; i < tp; i += KS_NT) {
@@ -887,7 +1017,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(ua[m] * rx.x, ua[nx + m] * rx.y);  // w = u r_x  (a8)
         }
         KS_SYNC();
-        cpx<R>* F = fft_batch<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
+        cpx<R>* F = fft_pair<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     }
@@ -918,8 +1048,272 @@ constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
 // cluster kernel of 128 or 256 threads.
 constexpr int COL_ACC_LANES = 128;
 
+// ---- centre-symmetric (Xi) subspace: columns in pairs --------------------------------------
+// In the subspace u_hat_{j,-k} = -conj(u_hat_{j,k}) and the j = 0 column is zero, so the s-series
+// of every retained x-mode j >= 1 is purely imaginary (u, the products u u_x and u r_x, all odd
+// in x) or purely real (r_x, even in x).  Two such columns share one complex s-transform: the
+// canonical pairs are (2p + 1, 2p + 2), p = 0 .. ceil(Kx / 2) - 1, the second column absent when
+// 2p + 2 > Kx.  Forward, of imaginary columns x_a = i xi_a, x_b = i xi_b: C = F[xi_a + i xi_b],
+// X_a(k) = i (C(k) + conj C(-k)) / 2, X_b(k) = (C(k) - conj C(-k)) / 2.  Inverse to imaginary
+// columns: c = F^-1[-i X_a + X_b], x_a = i Re c, x_b = i Im c; to real columns:
+// c = F^-1[X_a + i X_b], x_a = Re c, x_b = Im c.  The split gives X(-k) = -conj X(k) bit for bit
+// (IEEE negation is exact, addition commutes), so the band keeps the subspace's symmetry exactly
+// without a projection, and the x-mode j = 0 needs no transform at all.  Every launch form pairs
+// the same columns, so they compute the same bits.
+KS_HDX int xi_npairs(const Dims& d) { return (d.kx + 1) / 2; }
+
+// the column modes that run on pairs in the subspace
+KS_HDX constexpr bool col_paired(int MODE) {
+    return MODE == COL_SYNTH_U || MODE == COL_RESID || MODE == COL_UPDATE || MODE == COL_GRAD;
+}
+
+// number of work items of a column phase
+KS_HDX int col_item_count(const Dims& d, int xi, int MODE) {
+    return d.B * ((xi && col_paired(MODE)) ? xi_npairs(d) : d.nkx);
+}
+
+template <typename R>
+KS_HD cpx<R> xi_split_a(cpx<R> ck, cpx<R> cm) {  // X_a(k) from C(k), C(-k)
+    return mk<R>((R)0.5 * (cm.y - ck.y), (R)0.5 * (ck.x + cm.x));
+}
+template <typename R>
+KS_HD cpx<R> xi_split_b(cpx<R> ck, cpx<R> cm) {  // X_b(k)
+    return mk<R>((R)0.5 * (ck.x - cm.x), (R)0.5 * (ck.y + cm.y));
+}
+template <typename R>
+KS_HD cpx<R> xi_join_imag(cpx<R> xa, cpx<R> xb) {  // -i X_a + X_b
+    return mk<R>(xa.y + xb.x, xb.y - xa.x);
+}
+template <typename R>
+KS_HD cpx<R> xi_join_real(cpx<R> xa, cpx<R> xb) {  // X_a + i X_b
+    return mk<R>(xa.x - xb.y, xa.y + xb.x);
+}
+template <typename P>
+KS_HD P zero_part() { return P{}; }
+
+// One pair of columns (ja, jb) of one loop; the modes of col_item that run on pairs.  Pair 0
+// also writes the zero column j = 0 (M and the partials) and takes the per-loop duties that
+// column 0 has in col_item (T, status, sqrt(J), the step counter).
+template <typename R, int MODE, bool SWZ = false>
+KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem, int par) {
+    typedef typename PartT<R>::type Part;
+    const int nkx = d.nkx, np = xi_npairs(d);
+    const int b = p.colorder[item / np];
+    const int pp = item - (item / np) * np;
+    const int ja = 2 * pp + 1, jb = 2 * pp + 2;
+    const bool hasb = jb <= d.kx;
+    const int ns = p.ns[b], lg = p.lgns[b], ks = p.ks[b];
+    const int nk = 2 * ks + 1;
+    cpx<R>* A = reinterpret_cast<cpx<R>*>(smem);
+    cpx<R>* Bf = A + ns;
+    double* red = reinterpret_cast<double*>(Bf + ns);
+    cpx<R>* const M0 = p.M + p.moff[b];
+    cpx<R>* const cola = M0 + (size_t)ja * ns;
+    cpx<R>* const colb = M0 + (size_t)jb * ns;   // used only when hasb
+    const size_t ba = (size_t)p.boff[b] + (size_t)ja * nk;
+    const size_t bb = (size_t)p.boff[b] + (size_t)jb * nk;
+    const int B = d.B;
+    const double* Tc = p.T + (size_t)par * B;
+    double* Tn = p.T + (size_t)(par ^ 1) * B;
+    const double* wTc = p.wT + (size_t)par * B;
+    double* wTn = p.wT + (size_t)(par ^ 1) * B;
+    const cpx<R> zero = mk<R>(0, 0);
+
+    if constexpr (MODE == COL_RESID || MODE == COL_GRAD) {
+        if (!loop_live(p, b)) return;
+    }
+    if constexpr (MODE == COL_UPDATE) {
+        if (p.check_active && p.prec[b] != p.myprec) return;
+        if (p.check_active && p.status[b] != ST_RUNNING) {
+            if (pp == 0 && KS_TID == 0) {
+                Tn[b] = Tc[b];
+                wTn[b] = wTc[b];
+            }
+            return;
+        }
+    }
+
+    if constexpr (MODE == COL_SYNTH_U) {
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            const int k = (i < (ns >> 1)) ? i : i - ns;
+            cpx<R> x = zero;
+            if (k >= -ks && k <= ks) x = xi_join_imag(p.uh[ba + (k + ks)], hasb ? p.uh[bb + (k + ks)] : zero);
+            A[i] = x;
+        }
+        KS_SYNC();
+        const cpx<R>* v = fft_col<R, SWZ>(A, Bf, lg, 1, +1, p.tw, 0, p.twsh);
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            cola[i] = mk<R>(0, v[i].x);
+            if (hasb) colb[i] = mk<R>(0, v[i].y);
+            if (pp == 0) M0[i] = zero;
+        }
+        KS_SYNC();
+        return;
+    }
+
+    // RESID, UPDATE, GRAD: forward s-transform of the imaginary columns P or W of M, in one
+    for (int i = KS_TID; i < ns; i += KS_NT) A[i] = mk<R>(cola[i].y, hasb ? colb[i].y : (R)0);
+    KS_SYNC();
+    cpx<R>* F = fft_col<R, SWZ>(A, Bf, lg, 1, -1, p.tw, 0, p.twsh);
+    cpx<R>* X = (F == A) ? Bf : A;
+    const R ins = p.insv[b];
+    const R w_over_T = (R)wTc[b];
+    const R lin_a = p.lin[ja], lin_b = hasb ? p.lin[jb] : (R)0;
+    const R q_a = p.qv[ja], q_b = hasb ? p.qv[jb] : (R)0;
+
+    if constexpr (MODE == COL_RESID) {
+        ColAcc<R> acc[2];
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            const int k = (i < (ns >> 1)) ? i : i - ns;
+            cpx<R> x = zero;
+            if (k >= -ks && k <= ks) {
+                const cpx<R> ck = F[i], cm = F[(ns - i) & (ns - 1)];
+                const R bk = -(R)k * w_over_T;            // -omega_k / T
+                // r_hat = (a + i bk) u_hat - p_hat for both columns                     (a5)
+                const cpx<R> pa = scale(xi_split_a(ck, cm), ins);
+                const cpx<R> ua = p.uh[ba + (k + ks)];
+                const cpx<R> ra = mk<R>(lin_a * ua.x - bk * ua.y - pa.x, lin_a * ua.y + bk * ua.x - pa.y);
+                p.rh[ba + (k + ks)] = ra;
+                acc[0].add(ua, ra, k);                    // a6
+                cpx<R> xb = zero;
+                if (hasb) {
+                    const cpx<R> pb = scale(xi_split_b(ck, cm), ins);
+                    const cpx<R> ub = p.uh[bb + (k + ks)];
+                    const cpx<R> rb = mk<R>(lin_b * ub.x - bk * ub.y - pb.x, lin_b * ub.y + bk * ub.x - pb.y);
+                    p.rh[bb + (k + ks)] = rb;
+                    acc[1].add(ub, rb, k);
+                    xb = mk<R>(-q_b * rb.y, q_b * rb.x);   // i q_j r_hat                 (a7)
+                }
+                x = xi_join_real(mk<R>(-q_a * ra.y, q_a * ra.x), xb);
+            }
+            X[i] = x;
+        }
+        KS_SYNC();
+        const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            cola[i] = mk<R>(v[i].x, 0);
+            if (hasb) colb[i] = mk<R>(v[i].y, 0);
+            if (pp == 0) M0[i] = zero;
+        }
+        block_reduce2(acc[0], acc[1], red);
+        if (KS_TID == 0) {
+            p.Jpart[(size_t)b * nkx + ja] = acc[0].part_J(2.0);
+            p.L2part[(size_t)b * nkx + ja] = acc[0].part_L(2.0);
+            if (hasb) {
+                p.Jpart[(size_t)b * nkx + jb] = acc[1].part_J(2.0);
+                p.L2part[(size_t)b * nkx + jb] = acc[1].part_L(2.0);
+            }
+            if (pp == 0) {
+                p.Jpart[(size_t)b * nkx] = zero_part<Part>();
+                p.L2part[(size_t)b * nkx] = zero_part<Part>();
+            }
+        }
+        KS_SYNC();
+        return;
+    }
+
+    // G_hat = (a + i omega/T) r_hat + F[P(u r_x)] for both columns at mode k              (a9)
+    auto g_at = [&](int i, int k, bool second) {
+        const cpx<R> ck = F[i], cm = F[(ns - i) & (ns - 1)];
+        const cpx<R> wh = scale(second ? xi_split_b(ck, cm) : xi_split_a(ck, cm), ins);
+        const cpx<R> r = p.rh[(second ? bb : ba) + (k + ks)];
+        const R a_lin = second ? lin_b : lin_a;
+        const R bk = (R)k * w_over_T;
+        return mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+    };
+
+    if constexpr (MODE == COL_GRAD) {
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            const int k = (i < (ns >> 1)) ? i : i - ns;
+            if (k >= -ks && k <= ks) {
+                p.gh[ba + (k + ks)] = g_at(i, k, false);
+                if (hasb) p.gh[bb + (k + ks)] = g_at(i, k, true);
+            }
+        }
+        if (pp == 0)  // the j = 0 column of G is zero in the subspace
+            for (int kk = KS_TID; kk < nk; kk += KS_NT) p.gh[(size_t)p.boff[b] + kk] = zero;
+        KS_SYNC();
+        return;
+    }
+
+    if constexpr (MODE == COL_UPDATE) {
+        const double T = Tc[b];
+        if (KS_TID < 32) {
+            double sJ, sL;
+            sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
+            if (KS_TID == 0) {
+                red[0] = sJ * d.L;
+                red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
+            }
+        }
+        KS_SYNC();
+        const double J = red[0], L2 = red[1];
+        int st = ST_RUNNING;
+        if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
+        else if (J < p.tol * p.tol) st = ST_CONVERGED;
+        else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
+        if (pp == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
+        if (st != ST_RUNNING) {
+            if (pp == 0 && KS_TID == 0) {
+                p.status[b] = st;
+                Tn[b] = T;
+                wTn[b] = wTc[b];
+            }
+            KS_SYNC();
+            return;
+        }
+        const R dt = (R)d.dtau;
+        const R wT2 = w_over_T * w_over_T;
+        const R cq_a = p.cq[ja], cq_b = hasb ? p.cq[jb] : (R)0;
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            const int k = (i < (ns >> 1)) ? i : i - ns;
+            cpx<R> x = zero;
+            if (k >= -ks && k <= ks) {
+                R fa = dt, fb = dt;
+                if (d.scheme == 1) {
+                    // IMEX: dtau / (1 - dtau Lambda), Lambda = -(omega/T)^2 - q^4 (q^2-1)^2  (a10)
+                    const R kk2 = (R)k * (R)k;
+                    fa = dt / ((R)1 + dt * (kk2 * wT2 + cq_a));
+                    fb = dt / ((R)1 + dt * (kk2 * wT2 + cq_b));
+                }
+                cpx<R> ua = p.uh[ba + (k + ks)];
+                ua = ua - scale(g_at(i, k, false), fa);
+                p.uh[ba + (k + ks)] = ua;
+                cpx<R> ub = zero;
+                if (hasb) {
+                    ub = p.uh[bb + (k + ks)];
+                    ub = ub - scale(g_at(i, k, true), fb);
+                    p.uh[bb + (k + ks)] = ub;
+                }
+                x = xi_join_imag(ua, ub);
+            }
+            X[i] = x;
+        }
+        KS_SYNC();
+        const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
+        for (int i = KS_TID; i < ns; i += KS_NT) {
+            cola[i] = mk<R>(0, v[i].x);
+            if (hasb) colb[i] = mk<R>(0, v[i].y);
+            if (pp == 0) M0[i] = zero;
+        }
+        if (pp == 0 && KS_TID == 0) {
+            const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
+            Tn[b] = Tnew;
+            wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
+            p.steps[b] += 1;
+        }
+        KS_SYNC();
+    }
+}
+
 template <typename R, int MODE, bool SWZ = false>
 KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem, int par) {
+    if constexpr (col_paired(MODE)) {
+        if (p.xi) {
+            col_pair_item<R, MODE, SWZ>(d, p, item, smem, par);
+            return;
+        }
+    }
     const int nkx = d.nkx;
     const int b = p.colorder[item / nkx];
     const int j = item - (item / nkx) * nkx;
@@ -957,14 +1351,14 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = (k >= -ks && k <= ks) ? src[bo + (k + ks)] : mk<R>(0, 0);
         }
         KS_SYNC();
-        cpx<R>* v = fft_batch<R, SWZ>(A, Bf, lg, 1, +1, p.tw, 0, p.twsh);
+        cpx<R>* v = fft_col<R, SWZ>(A, Bf, lg, 1, +1, p.tw, 0, p.twsh);
         for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
         KS_SYNC();
     } else {
         // the remaining modes start with a forward s-transform of the column of M
         for (int i = KS_TID; i < ns; i += KS_NT) A[i] = col[i];
         KS_SYNC();
-        cpx<R>* F = fft_batch<R, SWZ>(A, Bf, lg, 1, -1, p.tw, 0, p.twsh);
+        cpx<R>* F = fft_col<R, SWZ>(A, Bf, lg, 1, -1, p.tw, 0, p.twsh);
         cpx<R>* X = (F == A) ? Bf : A;
         const R ins = p.insv[b];
 
@@ -1002,7 +1396,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 X[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
+            cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             block_reduce(acc, red);
             if (KS_TID == 0) {
@@ -1108,7 +1502,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 Y[i] = x;
             }
             KS_SYNC();
-            cpx<R>* v = fft_batch<R, SWZ>(Y, p.xi ? X : F, lg, 1, +1, p.tw, 0, p.twsh);
+            cpx<R>* v = fft_col<R, SWZ>(Y, p.xi ? X : F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             if (j == 0 && KS_TID == 0) {
                 const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)

@@ -154,15 +154,19 @@ __global__ void __launch_bounds__(128, 6) k_persist(Dims d, Bufs<R> p, int nstep
     __syncthreads();
     Bufs<R> q = p;
     q.tw = tws;
+    // column items per phase (pairs of columns in the centre-symmetric subspace); ncol, the
+    // launch's upper bound, is the count of single columns
+    const int ncol_r = min(ncol, col_item_count(d, p.xi, COL_RESID));
+    const int ncol_u = min(ncol, col_item_count(d, p.xi, COL_UPDATE));
     for (int s = 0; s < nsteps; ++s) {
         const int par = (par0 + s) & 1;
         for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_NONLIN, true>(d, q, it, smem);
         if (!grid_sync(bar)) return;
-        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_RESID, true>(d, q, it, smem, par);
+        for (int it = blockIdx.x; it < ncol_r; it += gridDim.x) col_item<R, COL_RESID, true>(d, q, it, smem, par);
         if (!grid_sync(bar)) return;
         for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ, true>(d, q, it, smem);
         if (!grid_sync(bar)) return;
-        for (int it = blockIdx.x; it < ncol; it += gridDim.x) col_item<R, COL_UPDATE, true>(d, q, it, smem, par);
+        for (int it = blockIdx.x; it < ncol_u; it += gridDim.x) col_item<R, COL_UPDATE, true>(d, q, it, smem, par);
         if (s + 1 < nsteps && !grid_sync(bar)) return;
     }
 }
@@ -303,6 +307,9 @@ struct ks_loop {
     int cthreads = 128;
     int cgrid[3] = {0, 0, 0};
     int finish_f32_adjoint = 1;     // mixed descents: finishing steps form the adjoint in float
+    // mixed descents: probe of the float floor (knobs "switch_probe", "switch_probe_steps")
+    int switch_probe = 1;
+    long long probe_steps = 1000;
     int xi = 0;                     // 1: loads, gradients and updates projected onto the Xi subspace
     // ks_descend with the extrapolation of App. C (knob "extrapolate")
     int extrapolate = 0;
@@ -559,7 +566,7 @@ template <typename R, int MODE>
 int launch_cols(ks_loop* h, const Bufs<R>& p, cudaStream_t s) {
     const int pr = std::is_same<R, double>::value ? P64 : P32;
     const Launch& l = h->lcol[pr];
-    const int n = h->d.B * h->d.nkx;
+    const int n = col_item_count(h->d, h->xi, MODE);
     LaunchScope ls(h, s, std::string(kColNames[MODE]) + prec_suffix(pr));
     k_cols<R, MODE><<<std::min(n, l.grid), l.threads, l.smem, s>>>(h->d, p, n, (int)l.tw_off,
                                                                      std::max(h->d.nx, h->nsmax));
@@ -615,7 +622,10 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     const size_t cs = sizeof(cpx<R>), rs = sizeof(R);
     const int nx = h->d.nx, nkx = h->d.nkx;
     cp.C = C;
-    cp.ncmax = (nkx + C - 1) / C;
+    // columns per rank: single columns, or pairs of columns in the centre-symmetric subspace
+    // (the knob can change after the plan is made, so the plan holds either)
+    const int npr = (h->d.kx + 1) / 2;
+    cp.ncmax = std::max((nkx + C - 1) / C, 2 * ((npr + C - 1) / C));
     cp.nsmax = h->nsmax;
     cp.nkmax = 2 * (h->nsmax / 3) + 1;
     int nsmin = h->nsmax;
@@ -1427,6 +1437,93 @@ int monitor_f64(ks_loop* h, cudaStream_t s, std::vector<double>& out, bool doubl
     return KS_OK;
 }
 
+// Probe of the float floor of a mixed descent.  The loops flagged in sel take n double steps from
+// their current state (the float band widened exactly) on the API workspace; the resident state
+// is not touched.  out[b] gets sqrt(J) of each probed loop after those steps, evaluated in
+// double, and Tout[b] its period.  A float state carries rounding noise that the double steps
+// remove within a few hundred steps; what remains is the part of the residual the float steps
+// can still reduce, so comparing it with sqrt(J) of the float state tells a float phase that
+// still converges (beneath its noise) from one that has stalled.
+int polish_probe(ks_loop* h, cudaStream_t s, const std::vector<int>& sel, long long n,
+                 std::vector<double>& out, std::vector<double>& Tout) {
+    Work& w = h->st;
+    Work& a = h->api;
+    const int B = h->d.B;
+    dim3 g(8, B);
+    k_band_merge<<<g, 256, 0, s>>>((const cpx<float>*)w.uh[P32], (const cpx<double>*)w.uh[P64],
+                                   (cpx<double>*)a.uh[P64], h->d_boff, w.prec, B, h->d.nkx, h->d_ks);
+    KS_CUDA(cudaGetLastError());
+    KS_CUDA(cudaMemcpyAsync(a.T, w.T + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    a.par = 0;
+    k_prep_wT<<<(B + 127) / 128, 128, 0, s>>>(a.T, a.wT, B);
+    KS_CUDA(cudaGetLastError());
+    std::vector<int> st(B), pr(B, P64);
+    for (int b = 0; b < B; ++b) st[b] = sel[b] ? KS_RUNNING : KS_STEP_CAP;
+    KS_CUDA(cudaMemcpyAsync(a.status, st.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemcpyAsync(a.prec, pr.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemsetAsync(a.steps, 0, B * sizeof(long long), s));
+    a.mix_valid[P64] = false;
+    const bool clus = h->path == 0 && h->cplan[P64].bytes > 0;
+    const bool pers = h->path <= 1 && h->pgrid[P64] > 0;
+    const long long kMaxPerLaunch = 1 << 14;
+    for (long long done = 0; done < n;) {
+        const long long c = (clus || pers) ? std::min(kMaxPerLaunch, n - done) : 1;
+        if (clus) {
+            KS_TRY((run_cluster<double, double>(h, a, P64, c, 0.0, 0.0, s)));
+        } else if (pers) {
+            KS_TRY(run_persist<double>(h, a, P64, c, 0.0, 0.0, s));
+        } else {
+            if (!a.mix_valid[P64]) KS_TRY(run_prime<double>(h, a, P64, s));
+            KS_TRY(run_step<double>(h, a, P64, 0.0, 0.0, s));
+        }
+        if (c & 1) a.par ^= 1;
+        done += c;
+    }
+    const double* Tc = a.T + (size_t)a.par * B;
+    KS_TRY(run_residual<double>(h, a, P64, s));
+    KS_TRY(run_finalize(h, a, Tc, P64, 0, s));
+    out.resize(B);
+    Tout.resize(B);
+    KS_CUDA(cudaMemcpyAsync(out.data(), a.sqrtJ, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(Tout.data(), Tc, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    return KS_OK;
+}
+
+// The loops flagged in sel continue in double from the state the last polish_probe left in the
+// API workspace (band, T after n more steps, step counters advanced by n).
+int switch_polished(ks_loop* h, cudaStream_t s, const std::vector<int>& sel, long long n,
+                    const std::vector<double>& Tp) {
+    Work& w = h->st;
+    Work& a = h->api;
+    const int B = h->d.B;
+    dim3 g(8, B);
+    KS_CUDA(cudaMemcpyAsync(w.sel, sel.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_band_copy_sel<<<g, 256, 0, s>>>((const cpx<double>*)a.uh[P64], (cpx<double>*)w.uh[P64],
+                                      h->d_boff, w.sel, B, h->d.nkx, h->d_ks);
+    KS_CUDA(cudaGetLastError());
+    std::vector<double> Tcur(B), wTcur(B);
+    KS_CUDA(cudaMemcpyAsync(Tcur.data(), w.T + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(wTcur.data(), w.wT + (size_t)w.par * B, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b)
+        if (sel[b]) {
+            Tcur[b] = Tp[b];
+            wTcur[b] = 2.0 * 3.14159265358979323846 / Tp[b];
+            h->h_prec[b] = P64;
+            h->h_status[b] = KS_RUNNING;
+            h->h_steps[b] += n;
+            h->anc_sq[b] = -1.0;  // an extrapolation anchor from the float phase no longer applies
+        }
+    KS_CUDA(cudaMemcpyAsync(w.T + (size_t)w.par * B, Tcur.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemcpyAsync(w.wT + (size_t)w.par * B, wTcur.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemcpyAsync(w.prec, h->h_prec.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemcpyAsync(w.status, h->h_status.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    KS_CUDA(cudaMemcpyAsync(w.steps, h->h_steps.data(), B * sizeof(long long), cudaMemcpyHostToDevice, s));
+    w.mix_valid[P64] = false;
+    return KS_OK;
+}
+
 // One extrapolation round of App. C over the running loops, from sqrt(J) of the current states
 // (val, evaluated in double).  A loop below extrap_start without an anchor takes its current
 // state as the anchor; a loop whose sqrt(J) has fallen to half its anchor's is extrapolated
@@ -1651,6 +1748,13 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
     // from sqrt(J) evaluated in double, which keeps falling after the float value has reached
     // its noise floor
     const bool monitor = (h->mode == KS_MIXED);
+    // float-floor probe (knob "switch_probe"): the rate of the float phase in decades of sqrt(J)
+    // per step over windows of stall_window / 4 steps, the best rate over windows that lie in the
+    // tail (sqrt(J) < 1e-2 at their start), and the probe schedule.  When the rate falls below an
+    // eighth of the best, a probe polishes a copy of the loop in double (polish_probe) and the
+    // loop stays in float or switches from the polished copy (see the decision below).
+    std::vector<double> rv0(B, -1.0), rbest(B, 0.0), rlast(B, 0.0);
+    std::vector<long long> rs0(B, 0), pnext(B, 0);
     if (monitor) {
         // a loop whose float rounding alone already doubles sqrt(J) (it starts below the float
         // floor, e.g. a nearly converged loop) descends in double from the start
@@ -1685,8 +1789,8 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
             h->hist_sqrtJ[b].push_back(val[b]);
             h->hist_prec[b].push_back(h->h_prec[b]);
         }
-        std::vector<int> sel(B, 0);
-        bool any_switch = false, any_live = false, status_dirty = false;
+        std::vector<int> sel(B, 0), psel(B, 0);
+        bool any_switch = false, any_live = false, status_dirty = false, any_probe = false;
         for (int b = 0; b < B; ++b) {
             int& stb = h->h_status[b];
             if (stb == ST_SWITCH) {
@@ -1712,6 +1816,25 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
                     any_switch = true;
                     continue;
                 }
+                if (h->switch_probe) {
+                    const long long wr = std::max<long long>(1, h->stall_window / 4);
+                    if (rv0[b] < 0.0) {
+                        rv0[b] = v;
+                        rs0[b] = h->h_steps[b];
+                    } else if (h->h_steps[b] - rs0[b] >= wr) {
+                        const double rate = std::log10(rv0[b] / v) / (double)(h->h_steps[b] - rs0[b]);
+                        const bool tail = rv0[b] < 1e-2;  // the whole window in the tail
+                        const bool bent = tail && rbest[b] > 0.0 && rate < 0.125 * rbest[b];
+                        if (tail && rate > rbest[b]) rbest[b] = rate;
+                        rlast[b] = rate;
+                        rv0[b] = v;
+                        rs0[b] = h->h_steps[b];
+                        if (bent && h->h_steps[b] >= pnext[b]) {
+                            psel[b] = 1;
+                            any_probe = true;
+                        }
+                    }
+                }
             }
             // no-progress test over a window of stall_window steps
             if (win_val[b] < 0.0) {
@@ -1731,6 +1854,42 @@ extern "C" int ks_descend(ks_loop_t h, void* u, double* T, long long max_steps, 
                 win_step[b] = h->h_steps[b];
             }
             if (stb == KS_RUNNING && !sel[b]) any_live = true;
+        }
+        if (any_probe) {
+            std::vector<double> pv, pT;
+            KS_TRY(polish_probe(h, s, psel, h->probe_steps, pv, pT));
+            std::vector<int> ssel(B, 0);
+            bool any_polished = false;
+            for (int b = 0; b < B; ++b) {
+                if (!psel[b]) continue;
+                // The polish removes the float rounding noise.  Against what its steps would
+                // give at the best tail rate: if it removes a fifth or more of sqrt(J), the float
+                // state's value is mostly that noise and the float steps keep converging beneath
+                // it (the stall window ends the float phase, no further probe); if it removes
+                // less and descends at least four times faster than the float phase does now,
+                // the float arithmetic holds the descent back: switch from the polished copy;
+                // otherwise the bend was the loop's own dynamics (probe again at a later bend).
+                const double expect = val[b] * std::pow(10.0, -rbest[b] * (double)h->probe_steps);
+                const double removed = 1.0 - pv[b] / expect;
+                const double rp = std::log10(val[b] / pv[b]) / (double)h->probe_steps;
+                const bool go = removed < 0.2 && rp > 4.0 * std::max(rlast[b], 0.0);
+                const long long wait = removed >= 0.2 ? (1LL << 62) : h->stall_window;
+                if (go && pv[b] == pv[b] && pT[b] > 0.0) {
+                    ssel[b] = 1;
+                    sel[b] = 0;
+                    any_polished = true;
+                } else {
+                    pnext[b] = h->h_steps[b] + wait;
+                }
+            }
+            if (any_polished) {
+                KS_TRY(switch_polished(h, s, ssel, h->probe_steps, pT));
+                for (int b = 0; b < B; ++b)
+                    if (ssel[b]) {
+                        win_val[b] = -1.0;
+                        any_live = true;
+                    }
+            }
         }
         if (any_switch) {
             KS_TRY(switch_to_double(h, sel, s));
@@ -1830,6 +1989,11 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         h->test_barrier_extra = value ? 1 : 0;
     } else if (k == "finish_f32_adjoint") {
         h->finish_f32_adjoint = value != 0;
+    } else if (k == "switch_probe") {
+        h->switch_probe = value ? 1 : 0;
+    } else if (k == "switch_probe_steps") {
+        if (value < 1 || value > 1000000) return fail(KS_ERR_ARG, "switch_probe_steps in [1, 1e6]");
+        h->probe_steps = value;
     } else if (k == "extrapolate") {
         h->extrapolate = value ? 1 : 0;
     } else if (k == "extrapolate_start_ppm") {
@@ -1868,9 +2032,12 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "cluster_smem_f32") *value = h->cplan[1].bytes;
     else if (k == "rows_per_tile") *value = h->rows_per_tile;
     else if (k == "finish_f32_adjoint") *value = h->finish_f32_adjoint;
+    else if (k == "switch_probe") *value = h->switch_probe;
+    else if (k == "switch_probe_steps") *value = h->probe_steps;
     else if (k == "cluster_threads") *value = h->cthreads;
     else if (k == "cluster_mixed_finish") *value = h->cplan[2].bytes ? h->cplan[2].C : 0;
     else if (k == "stall_window") *value = h->stall_window;
+    else if (k == "stall_drop_ppm") *value = std::llround(h->stall_drop * 1e6);
     else if (k == "chunk") *value = h->chunk;
     else if (k == "symmetry") *value = h->xi;
     else if (k == "extrapolate") *value = h->extrapolate;

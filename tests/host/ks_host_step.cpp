@@ -155,7 +155,7 @@ void rows_pass(const Dims& d, HostBatch<R>& h, int mode) {
 template <typename R, int MODE>
 void cols_pass(const Dims& d, HostBatch<R>& h, int par) {
     unsigned char* smem = reinterpret_cast<unsigned char*>(g_smem.data());
-    for (int it = 0; it < d.B * d.nkx; ++it) col_item<R, MODE>(d, h.p, it, smem, par);
+    for (int it = 0; it < col_item_count(d, h.p.xi, MODE); ++it) col_item<R, MODE>(d, h.p, it, smem, par);
 }
 
 template <typename R>

@@ -343,3 +343,41 @@ def test_mixed_batch_concurrent_precisions_equal_sequential():
         assert mixed_phase
     for a, b in zip(outs[0], outs[1]):
         assert torch.equal(a, b)
+
+
+def test_mixed_switch_probe_on_a_periodic_orbit():
+    """The float-floor probe of a mixed descent (knob "switch_probe") on the stored recurrence
+    loop at L = 39: the float phase of this loop stalls at sqrt(J) ~ 3e-5 with nothing converging
+    beneath its noise, so the probe switches it to double soon after its rate bends and the loop
+    converges below 1e-10 to the periodic orbit (T = 25.3708).  With the stall window alone the
+    float phase runs on far longer (measured: switch at 524k steps, or 1.72M with the paired
+    column transforms of the subspace), so within 600k steps it has switched much later or not
+    at all, and has not converged."""
+    from paper_2007_06427_gb300.inputs import orbit_guess
+    w = orbit_guess()
+    out = {}
+    for probe, cap in ((1, 2_000_000), (0, 600_000)):
+        u = torch.tensor(w.u[0].ravel(), device="cuda")
+        T = torch.tensor(w.T0, dtype=torch.float64, device="cuda")
+        steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sq = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        with K.KSLoop(w.L, w.nx, w.ns, K.KS_MIXED, K.KS_IMEX, 0.15, chunk=2000) as h:
+            K.ks_set_option(h.handle, "symmetry", 1)
+            assert K.ks_get_option(h.handle, "switch_probe") == 1
+            assert K.ks_get_option(h.handle, "switch_probe_steps") == 1000
+            K.ks_set_option(h.handle, "switch_probe", probe)
+            K.ks_descend(h.handle, u, T, cap, 1e-10, steps, sq, st)
+            hs, hq, hp = K.ks_get_history(h.handle, 0)
+        sw = int(hs[np.nonzero(hp == 0)[0][0]]) if (hp == 0).any() else None
+        out[probe] = (int(steps.item()), float(sq.item()), int(st.item()), float(T.item()), sw)
+    n1, sq1, st1, T1, sw1 = out[1]
+    assert st1 == K.KS_CONVERGED and sq1 < 1e-10 and abs(T1 - 25.3708) < 1e-3, out
+    assert sw1 is not None and sw1 < 300_000, out
+    n0, sq0, st0, T0, sw0 = out[0]
+    assert st0 != K.KS_CONVERGED, out
+    assert sw0 is None or sw0 > 2 * sw1, out
+    with K.KSLoop(w.L, w.nx, w.ns, K.KS_MIXED) as h:
+        for bad in (0, 1000001):
+            with pytest.raises(K.KsError):
+                K.ks_set_option(h.handle, "switch_probe_steps", bad)

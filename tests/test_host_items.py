@@ -194,3 +194,19 @@ def test_items_float_switch_rule():
                         status=True, switch_tol=float(sw))
     assert st[0] == (5, 0) and res[0][1] == float(np.float64(T0))   # switched at once, T kept
     assert st[1] == (0, 2)
+
+
+def test_items_xi_pairs_descent_matches_oracle():
+    """In the centre-symmetric subspace the column items work on column pairs (2p+1, 2p+2): a
+    ragged batch of odd-in-x loops (Kx = 10, even, and Kx = 5, odd: the last pair has no second
+    column) against the oracle's descent in the subspace, five IMEX steps, FP64."""
+    for nx, nss in ((32, [32, 8, 64]), (16, [16, 128])):
+        loops = []
+        for i, n in enumerate(nss):
+            u, T, _ = spectral_loop(20 + i, nx, 39.0, ns=n, T_range=(30.0, 50.0), symmetric=True)
+            loops.append((u, T))
+        res = run_batch(harness_exe(), loops, 39.0, 0.15, ko.IMEX, 5, xi=1)
+        for (u, T), (a, c, g) in zip(loops, res):
+            ref = ko.descend(u, T, 39.0, 0.15, ko.IMEX, 5, xi=True)
+            assert rel(g, ref["u"]) <= 1e-12 and abs(c - ref["T"]) <= 1e-12 * ref["T"]
+            assert abs(a - np.sqrt(ko.residual(u, T, 39.0, xi=True)["J"])) <= 1e-12 * a
