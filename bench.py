@@ -83,6 +83,8 @@ def parse(argv=None):
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case: load the workload, run 3 x K tau-steps, no timing")
+    ap.add_argument("--path", type=int, default=-1,
+                    help="profiling case: launch path (0 cluster, 1 persistent, 2 per-phase)")
     return ap.parse_args(argv)
 
 
@@ -828,6 +830,8 @@ def ncu_case(args):
     u = torch.from_numpy(w.packed()).cuda().to(dt)
     T = torch.tensor(w.T0, dtype=torch.float64, device="cuda")
     with K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau) as h:
+        if args.path >= 0:
+            K.ks_set_option(h.handle, "path", args.path)
         K.ks_set_state(h.handle, u, T)
         for _ in range(3):
             K.ks_step(h.handle, args.ncu_case, 0.0)

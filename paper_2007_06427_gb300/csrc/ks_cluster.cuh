@@ -97,7 +97,9 @@ struct AdjTables {
 // stores and reloads reached L2 and DRAM after a flush; with both it uses ~150 registers and
 // spills nothing.  The single loop runs one block per SM anyway, and the batched workloads
 // (64x64 batch, ragged, 256x1024) measured no slower with the fewer resident blocks.
-template <typename R, typename RA>
+// XI: the centre-symmetric subspace (p.xi set), a separate instantiation so that each kernel
+// carries only the code of its own column scheme.
+template <typename R, typename RA, bool XI>
 __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables<RA> ta,
                                                  ClusterPlan cp, int nsteps, int par0, int use_M) {
     typedef typename PartT<R>::type Part;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nx = d.nx, lgnx = d.lgnx, kx = d.kx, nkx = d.nkx, B = d.B;
     const int rmax = cp.rmax;
-    const bool xi = p.xi != 0;
+    constexpr bool xi = XI;
     // owner rank and slot of x-mode j (j >= 1 in the subspace)
     auto own_rank = [&](int j) { return xi ? ((j - 1) >> 1) % C : j % C; };
     auto own_slot = [&](int j) { return xi ? 2 * (((j - 1) >> 1) / C) + ((j - 1) & 1) : j / C; };

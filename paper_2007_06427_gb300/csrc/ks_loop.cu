@@ -676,7 +676,8 @@ int setup_cluster(ks_loop* h) {
     KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
     int target = 16;
     while (target > 1 && (long long)target * h->d.B > 2LL * sms) target >>= 1;
-    KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     // candidate sizes: powers of two from the target down.  (A size that only balances the
     // columns, e.g. 11 ranks of 2 columns for 22, gives each rank 12 rows in two x-batches and
     // measured slower than 16 ranks with one row batch each.)
@@ -690,7 +691,8 @@ int setup_cluster(ks_loop* h) {
         for (int ug = 0; ug < 2; ++ug) {
             ClusterPlan cp = make_cluster_plan<R, RA>(h, C, ug, limit);
             if (!cp.bytes) continue;
-            KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
+            KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
+            KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);
             cfg.blockDim = dim3(h->cthreads);
@@ -703,7 +705,7 @@ int setup_cluster(ks_loop* h) {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int ncl = 0;
-            if (cudaOccupancyMaxActiveClusters(&ncl, k_cluster<R, RA>, &cfg) != cudaSuccess) {
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_cluster<R, RA, false>, &cfg) != cudaSuccess) {
                 cudaGetLastError();
                 ncl = 0;
             }
@@ -739,7 +741,8 @@ int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     cfg.attrs = at;
     cfg.numAttrs = 1;
     LaunchScope ls(h, s, std::string("cluster") + prec_suffix(pr) + (slot == 2 ? "_adj_f32" : ""));
-    KS_CUDA(cudaLaunchKernelEx(&cfg, k_cluster<R, RA>, h->d, p, ta, cp, (int)nsteps, w.par,
+    KS_CUDA(cudaLaunchKernelEx(&cfg, h->xi ? k_cluster<R, RA, true> : k_cluster<R, RA, false>, h->d, p,
+                               ta, cp, (int)nsteps, w.par,
                                w.mix_valid[pr] ? 1 : 0));
     ls.done();
     w.mix_valid[pr] = true;
