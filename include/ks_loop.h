@@ -193,12 +193,15 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
                            long long* total_launches, int reset);
 
 /* Tuning knobs of a handle (KS_ERR_ARG for an unknown key or a bad value):
- *   "path"           launch shape of ks_step / descent chunks: 0 (default) cluster-resident
- *                    kernel (one thread-block cluster per loop, state in shared memory for the
- *                    whole chunk, falls back to 1 where the loop does not fit); 1 one
- *                    cooperative launch per chunk with grid-wide barriers between the four
- *                    phases of a step; 2 four launches per tau-step.  All three give bit-identical
- *                    results.
+ *   "path"           launch shape of ks_step / descent chunks: 0 cluster-resident kernel (one
+ *                    thread-block cluster per loop, state in shared memory for the whole chunk,
+ *                    falls back to 1 where the loop does not fit); 1 one cooperative launch per
+ *                    chunk with grid-wide barriers between the four phases of a step; 2 four
+ *                    launches per tau-step.  All three give bit-identical results.  Default at
+ *                    create: 2 for ragged batches (unequal Ns) of 64 or more loops and for
+ *                    KS_FP64 batches whose cluster plan has 1 or 2 CTAs per loop on loops of
+ *                    Nx Ns >= 4096 points, else 0 (the faster form in measurements on GB300;
+ *                    ks_autotune chooses by timing instead).
  *   "persistent"     1: path 1, 0: path 2 (older spelling of "path")
  *   "cluster"        0 (default): cluster size chosen per precision; 1..16: force this size
  *                    (KS_ERR_ARG when no plan of that size fits the batch)

@@ -1148,161 +1148,161 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
             if (pp == 0) M0[i] = zero;
         }
         KS_SYNC();
-        return;
-    }
+    } else {
 
-    // RESID, UPDATE, GRAD: forward s-transform of the imaginary columns P or W of M, in one
-    for (int i = KS_TID; i < ns; i += KS_NT) A[i] = mk<R>(cola[i].y, hasb ? colb[i].y : (R)0);
-    KS_SYNC();
-    cpx<R>* F = fft_col<R, SWZ>(A, Bf, lg, 1, -1, p.tw, 0, p.twsh);
-    cpx<R>* X = (F == A) ? Bf : A;
-    const R ins = p.insv[b];
-    const R w_over_T = (R)wTc[b];
-    const R lin_a = p.lin[ja], lin_b = hasb ? p.lin[jb] : (R)0;
-    const R q_a = p.qv[ja], q_b = hasb ? p.qv[jb] : (R)0;
+        // RESID, UPDATE, GRAD: forward s-transform of the imaginary columns P or W of M, in one
+        for (int i = KS_TID; i < ns; i += KS_NT) A[i] = mk<R>(cola[i].y, hasb ? colb[i].y : (R)0);
+        KS_SYNC();
+        cpx<R>* F = fft_col<R, SWZ>(A, Bf, lg, 1, -1, p.tw, 0, p.twsh);
+        cpx<R>* X = (F == A) ? Bf : A;
+        const R ins = p.insv[b];
+        const R w_over_T = (R)wTc[b];
+        const R lin_a = p.lin[ja], lin_b = hasb ? p.lin[jb] : (R)0;
+        const R q_a = p.qv[ja], q_b = hasb ? p.qv[jb] : (R)0;
 
-    if constexpr (MODE == COL_RESID) {
-        ColAcc<R> acc[2];
-        for (int i = KS_TID; i < ns; i += KS_NT) {
-            const int k = (i < (ns >> 1)) ? i : i - ns;
-            cpx<R> x = zero;
-            if (k >= -ks && k <= ks) {
-                const cpx<R> ck = F[i], cm = F[(ns - i) & (ns - 1)];
-                const R bk = -(R)k * w_over_T;            // -omega_k / T
-                // r_hat = (a + i bk) u_hat - p_hat for both columns                     (a5)
-                const cpx<R> pa = scale(xi_split_a(ck, cm), ins);
-                const cpx<R> ua = p.uh[ba + (k + ks)];
-                const cpx<R> ra = mk<R>(lin_a * ua.x - bk * ua.y - pa.x, lin_a * ua.y + bk * ua.x - pa.y);
-                p.rh[ba + (k + ks)] = ra;
-                acc[0].add(ua, ra, k);                    // a6
-                cpx<R> xb = zero;
-                if (hasb) {
-                    const cpx<R> pb = scale(xi_split_b(ck, cm), ins);
-                    const cpx<R> ub = p.uh[bb + (k + ks)];
-                    const cpx<R> rb = mk<R>(lin_b * ub.x - bk * ub.y - pb.x, lin_b * ub.y + bk * ub.x - pb.y);
-                    p.rh[bb + (k + ks)] = rb;
-                    acc[1].add(ub, rb, k);
-                    xb = mk<R>(-q_b * rb.y, q_b * rb.x);   // i q_j r_hat                 (a7)
+        if constexpr (MODE == COL_RESID) {
+            ColAcc<R> acc[2];
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                const int k = (i < (ns >> 1)) ? i : i - ns;
+                cpx<R> x = zero;
+                if (k >= -ks && k <= ks) {
+                    const cpx<R> ck = F[i], cm = F[(ns - i) & (ns - 1)];
+                    const R bk = -(R)k * w_over_T;            // -omega_k / T
+                    // r_hat = (a + i bk) u_hat - p_hat for both columns                     (a5)
+                    const cpx<R> pa = scale(xi_split_a(ck, cm), ins);
+                    const cpx<R> ua = p.uh[ba + (k + ks)];
+                    const cpx<R> ra = mk<R>(lin_a * ua.x - bk * ua.y - pa.x, lin_a * ua.y + bk * ua.x - pa.y);
+                    p.rh[ba + (k + ks)] = ra;
+                    acc[0].add(ua, ra, k);                    // a6
+                    cpx<R> xb = zero;
+                    if (hasb) {
+                        const cpx<R> pb = scale(xi_split_b(ck, cm), ins);
+                        const cpx<R> ub = p.uh[bb + (k + ks)];
+                        const cpx<R> rb = mk<R>(lin_b * ub.x - bk * ub.y - pb.x, lin_b * ub.y + bk * ub.x - pb.y);
+                        p.rh[bb + (k + ks)] = rb;
+                        acc[1].add(ub, rb, k);
+                        xb = mk<R>(-q_b * rb.y, q_b * rb.x);   // i q_j r_hat                 (a7)
+                    }
+                    x = xi_join_real(mk<R>(-q_a * ra.y, q_a * ra.x), xb);
                 }
-                x = xi_join_real(mk<R>(-q_a * ra.y, q_a * ra.x), xb);
+                X[i] = x;
             }
-            X[i] = x;
-        }
-        KS_SYNC();
-        const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
-        for (int i = KS_TID; i < ns; i += KS_NT) {
-            cola[i] = mk<R>(v[i].x, 0);
-            if (hasb) colb[i] = mk<R>(v[i].y, 0);
-            if (pp == 0) M0[i] = zero;
-        }
-        block_reduce2(acc[0], acc[1], red);
-        if (KS_TID == 0) {
-            p.Jpart[(size_t)b * nkx + ja] = acc[0].part_J(2.0);
-            p.L2part[(size_t)b * nkx + ja] = acc[0].part_L(2.0);
-            if (hasb) {
-                p.Jpart[(size_t)b * nkx + jb] = acc[1].part_J(2.0);
-                p.L2part[(size_t)b * nkx + jb] = acc[1].part_L(2.0);
+            KS_SYNC();
+            const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                cola[i] = mk<R>(v[i].x, 0);
+                if (hasb) colb[i] = mk<R>(v[i].y, 0);
+                if (pp == 0) M0[i] = zero;
             }
-            if (pp == 0) {
-                p.Jpart[(size_t)b * nkx] = zero_part<Part>();
-                p.L2part[(size_t)b * nkx] = zero_part<Part>();
-            }
-        }
-        KS_SYNC();
-        return;
-    }
-
-    // G_hat = (a + i omega/T) r_hat + F[P(u r_x)] for both columns at mode k              (a9)
-    auto g_at = [&](int i, int k, bool second) {
-        const cpx<R> ck = F[i], cm = F[(ns - i) & (ns - 1)];
-        const cpx<R> wh = scale(second ? xi_split_b(ck, cm) : xi_split_a(ck, cm), ins);
-        const cpx<R> r = p.rh[(second ? bb : ba) + (k + ks)];
-        const R a_lin = second ? lin_b : lin_a;
-        const R bk = (R)k * w_over_T;
-        return mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
-    };
-
-    if constexpr (MODE == COL_GRAD) {
-        for (int i = KS_TID; i < ns; i += KS_NT) {
-            const int k = (i < (ns >> 1)) ? i : i - ns;
-            if (k >= -ks && k <= ks) {
-                p.gh[ba + (k + ks)] = g_at(i, k, false);
-                if (hasb) p.gh[bb + (k + ks)] = g_at(i, k, true);
-            }
-        }
-        if (pp == 0)  // the j = 0 column of G is zero in the subspace
-            for (int kk = KS_TID; kk < nk; kk += KS_NT) p.gh[(size_t)p.boff[b] + kk] = zero;
-        KS_SYNC();
-        return;
-    }
-
-    if constexpr (MODE == COL_UPDATE) {
-        const double T = Tc[b];
-        if (KS_TID < 32) {
-            double sJ, sL;
-            sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
+            block_reduce2(acc[0], acc[1], red);
             if (KS_TID == 0) {
-                red[0] = sJ * d.L;
-                red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
-            }
-        }
-        KS_SYNC();
-        const double J = red[0], L2 = red[1];
-        int st = ST_RUNNING;
-        if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
-        else if (J < p.tol * p.tol) st = ST_CONVERGED;
-        else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
-        if (pp == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
-        if (st != ST_RUNNING) {
-            if (pp == 0 && KS_TID == 0) {
-                p.status[b] = st;
-                Tn[b] = T;
-                wTn[b] = wTc[b];
+                p.Jpart[(size_t)b * nkx + ja] = acc[0].part_J(2.0);
+                p.L2part[(size_t)b * nkx + ja] = acc[0].part_L(2.0);
+                if (hasb) {
+                    p.Jpart[(size_t)b * nkx + jb] = acc[1].part_J(2.0);
+                    p.L2part[(size_t)b * nkx + jb] = acc[1].part_L(2.0);
+                }
+                if (pp == 0) {
+                    p.Jpart[(size_t)b * nkx] = zero_part<Part>();
+                    p.L2part[(size_t)b * nkx] = zero_part<Part>();
+                }
             }
             KS_SYNC();
             return;
         }
-        const R dt = (R)d.dtau;
-        const R wT2 = w_over_T * w_over_T;
-        const R cq_a = p.cq[ja], cq_b = hasb ? p.cq[jb] : (R)0;
-        for (int i = KS_TID; i < ns; i += KS_NT) {
-            const int k = (i < (ns >> 1)) ? i : i - ns;
-            cpx<R> x = zero;
-            if (k >= -ks && k <= ks) {
-                R fa = dt, fb = dt;
-                if (d.scheme == 1) {
-                    // IMEX: dtau / (1 - dtau Lambda), Lambda = -(omega/T)^2 - q^4 (q^2-1)^2  (a10)
-                    const R kk2 = (R)k * (R)k;
-                    fa = dt / ((R)1 + dt * (kk2 * wT2 + cq_a));
-                    fb = dt / ((R)1 + dt * (kk2 * wT2 + cq_b));
+
+        // G_hat = (a + i omega/T) r_hat + F[P(u r_x)] for both columns at mode k              (a9)
+        auto g_at = [&](int i, int k, bool second) {
+            const cpx<R> ck = F[i], cm = F[(ns - i) & (ns - 1)];
+            const cpx<R> wh = scale(second ? xi_split_b(ck, cm) : xi_split_a(ck, cm), ins);
+            const cpx<R> r = p.rh[(second ? bb : ba) + (k + ks)];
+            const R a_lin = second ? lin_b : lin_a;
+            const R bk = (R)k * w_over_T;
+            return mk<R>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
+        };
+
+        if constexpr (MODE == COL_GRAD) {
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                const int k = (i < (ns >> 1)) ? i : i - ns;
+                if (k >= -ks && k <= ks) {
+                    p.gh[ba + (k + ks)] = g_at(i, k, false);
+                    if (hasb) p.gh[bb + (k + ks)] = g_at(i, k, true);
                 }
-                cpx<R> ua = p.uh[ba + (k + ks)];
-                ua = ua - scale(g_at(i, k, false), fa);
-                p.uh[ba + (k + ks)] = ua;
-                cpx<R> ub = zero;
-                if (hasb) {
-                    ub = p.uh[bb + (k + ks)];
-                    ub = ub - scale(g_at(i, k, true), fb);
-                    p.uh[bb + (k + ks)] = ub;
-                }
-                x = xi_join_imag(ua, ub);
             }
-            X[i] = x;
+            if (pp == 0)  // the j = 0 column of G is zero in the subspace
+                for (int kk = KS_TID; kk < nk; kk += KS_NT) p.gh[(size_t)p.boff[b] + kk] = zero;
+            KS_SYNC();
+            return;
         }
-        KS_SYNC();
-        const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
-        for (int i = KS_TID; i < ns; i += KS_NT) {
-            cola[i] = mk<R>(0, v[i].x);
-            if (hasb) colb[i] = mk<R>(0, v[i].y);
-            if (pp == 0) M0[i] = zero;
+
+        if constexpr (MODE == COL_UPDATE) {
+            const double T = Tc[b];
+            if (KS_TID < 32) {
+                double sJ, sL;
+                sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
+                if (KS_TID == 0) {
+                    red[0] = sJ * d.L;
+                    red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
+                }
+            }
+            KS_SYNC();
+            const double J = red[0], L2 = red[1];
+            int st = ST_RUNNING;
+            if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
+            else if (J < p.tol * p.tol) st = ST_CONVERGED;
+            else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
+            if (pp == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
+            if (st != ST_RUNNING) {
+                if (pp == 0 && KS_TID == 0) {
+                    p.status[b] = st;
+                    Tn[b] = T;
+                    wTn[b] = wTc[b];
+                }
+                KS_SYNC();
+                return;
+            }
+            const R dt = (R)d.dtau;
+            const R wT2 = w_over_T * w_over_T;
+            const R cq_a = p.cq[ja], cq_b = hasb ? p.cq[jb] : (R)0;
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                const int k = (i < (ns >> 1)) ? i : i - ns;
+                cpx<R> x = zero;
+                if (k >= -ks && k <= ks) {
+                    R fa = dt, fb = dt;
+                    if (d.scheme == 1) {
+                        // IMEX: dtau / (1 - dtau Lambda), Lambda = -(omega/T)^2 - q^4 (q^2-1)^2  (a10)
+                        const R kk2 = (R)k * (R)k;
+                        fa = dt / ((R)1 + dt * (kk2 * wT2 + cq_a));
+                        fb = dt / ((R)1 + dt * (kk2 * wT2 + cq_b));
+                    }
+                    cpx<R> ua = p.uh[ba + (k + ks)];
+                    ua = ua - scale(g_at(i, k, false), fa);
+                    p.uh[ba + (k + ks)] = ua;
+                    cpx<R> ub = zero;
+                    if (hasb) {
+                        ub = p.uh[bb + (k + ks)];
+                        ub = ub - scale(g_at(i, k, true), fb);
+                        p.uh[bb + (k + ks)] = ub;
+                    }
+                    x = xi_join_imag(ua, ub);
+                }
+                X[i] = x;
+            }
+            KS_SYNC();
+            const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
+            for (int i = KS_TID; i < ns; i += KS_NT) {
+                cola[i] = mk<R>(0, v[i].x);
+                if (hasb) colb[i] = mk<R>(0, v[i].y);
+                if (pp == 0) M0[i] = zero;
+            }
+            if (pp == 0 && KS_TID == 0) {
+                const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
+                Tn[b] = Tnew;
+                wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
+                p.steps[b] += 1;
+            }
+            KS_SYNC();
         }
-        if (pp == 0 && KS_TID == 0) {
-            const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
-            Tn[b] = Tnew;
-            wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
-            p.steps[b] += 1;
-        }
-        KS_SYNC();
     }
 }
 

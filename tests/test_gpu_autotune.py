@@ -59,3 +59,25 @@ def test_invalid_cache_entry_is_ignored(tmp_path, monkeypatch):
     lines = cache.read_text().strip().splitlines()
     assert len(lines) == 2 and lines[0].endswith(" 32")
     assert int(lines[1].split("|")[1].split()[2]) in (128, 256)
+
+
+def test_default_launch_path_rule():
+    """The launch form chosen at create without tuning: four launches per step for ragged batches
+    of 64 or more loops and for double batches whose cluster plan has 1 or 2 CTAs per loop on loops
+    of 4096 or more points; the cluster-resident kernel otherwise."""
+    from paper_2007_06427_gb300.inputs import workload
+    rg = workload("ragged256_64xNs", batch=64)
+    for mode in (K.KS_FP64, K.KS_FP32, K.KS_MIXED):
+        with K.KSLoop(rg.L, rg.nx, rg.ns, mode) as h:
+            assert K.ks_get_option(h.handle, "path") == 2, mode
+    with K.KSLoop(22.0, 64, [64] * 256, K.KS_FP64) as h:
+        assert K.ks_get_option(h.handle, "cluster_f64") in (1, 2)
+        assert K.ks_get_option(h.handle, "path") == 2
+    for mode in (K.KS_FP32, K.KS_MIXED):
+        with K.KSLoop(22.0, 64, [64] * 256, mode) as h:
+            assert K.ks_get_option(h.handle, "path") == 0, mode
+    with K.KSLoop(22.0, 32, [32] * 256, K.KS_FP64) as h:     # 1024-point loops
+        assert K.ks_get_option(h.handle, "path") == 0
+    with K.KSLoop(22.0, 64, [128], K.KS_FP64) as h:          # the single loop
+        assert K.ks_get_option(h.handle, "path") == 0
+        assert K.ks_get_option(h.handle, "cluster_f64") == 16
