@@ -426,6 +426,8 @@ def launch_shape(K, h, mode, autotuned):
     return {"path": K.ks_get_option(h.handle, "path"),
             "cluster": K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64"),
             "threads": K.ks_get_option(h.handle, "cluster_threads"),
+            "graph": K.ks_get_option(h.handle, "graph"),
+            "graph_replays": K.ks_get_option(h.handle, "graph_replays"),
             "autotuned": bool(autotuned)}
 
 

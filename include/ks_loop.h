@@ -233,6 +233,14 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *                    a window is stalled (default 1000): the float phase of a mixed descent
  *                    then switches to double, a double descent stops with KS_STALLED
  *   "chunk"          tau-steps between read-backs in ks_descend
+ *   "graph"          path 2: 1 (default): runs of up to 16 tau-steps (an even number) are
+ *                    captured once as a CUDA graph of their launches and replayed on the
+ *                    caller's stream (while loops are live in both precisions, the float and
+ *                    double chains of a step are parallel branches of the graph); an odd last
+ *                    step is launched directly.  Up to 8 graphs are kept per handle, keyed by
+ *                    the live precisions, tol, the switch threshold, the step parity, the
+ *                    symmetry knob and the run length.  Results are bit-identical to 0 (every
+ *                    launch separately).  Off while ks_profile is on.
  *   "test_barrier_timeout" test hook: 1 makes every grid barrier of the path-1 kernel wait
  *                    for one arrival that never comes, so each wait runs out (about a second)
  *                    and the next read-back returns KS_ERR_TIMEOUT; 0 (default) restores it
@@ -261,7 +269,7 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
  * "cluster_f32", "cluster_mixed_finish" (cluster
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "stall_drop_ppm",
- * "chunk", "symmetry",
+ * "chunk", "symmetry", "graph", "graph_replays" (graphs replayed since create),
  * "extrapolate", "extrapolate_start_ppm", "extrapolate_drop_ppm", "extrapolations",
  * "extrapolations_rejected". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);

@@ -347,6 +347,20 @@ struct ks_loop {
     // beside the float one (created on first use; non-blocking, ordered by the two events)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // four-launch form: runs of tau-steps captured once as CUDA graphs and replayed (knob
+    // "graph"); a graph is keyed by everything its launches read from the host side
+    int graph = 1;
+    cudaStream_t gcap = nullptr, gcap2 = nullptr;  // capture streams (never executed on)
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;
+    struct StepGraph {
+        cudaGraphExec_t exec;
+        bool live[2];
+        double tol, swt;
+        int par, xi, steps;
+        long long launches;  // kernel launches in one replay
+    };
+    std::vector<StepGraph> graphs;
+    long long graph_replays = 0;
     // convergence history recorded by ks_descend at every read-back: (steps, sqrtJ, prec)
     std::vector<std::vector<long long>> hist_steps;
     std::vector<std::vector<double>> hist_sqrtJ;
@@ -1147,6 +1161,11 @@ extern "C" int ks_destroy(ks_loop_t h) {
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     if (h->side) cudaStreamDestroy(h->side);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    if (h->gcap) cudaStreamDestroy(h->gcap);
+    if (h->gcap2) cudaStreamDestroy(h->gcap2);
+    if (h->gfork) cudaEventDestroy(h->gfork);
+    if (h->gjoin) cudaEventDestroy(h->gjoin);
     for (void* p : h->allocs) cudaFree(p);
     delete h;
     return KS_OK;
@@ -1301,6 +1320,83 @@ int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
     return KS_OK;
 }
 
+// ---- graphs of the four-launch form ----
+// The four launches of a tau-step depend on one another and on nothing the host computes between
+// steps, so a run of `steps` (even) steps is captured once and replayed; an even run leaves the
+// step parity where it found it.  While both precisions have live loops, the float and double
+// chains of each step are independent (they touch disjoint loops) and the graph holds them as
+// two parallel branches.
+constexpr int kGraphSteps = 16;
+constexpr size_t kGraphCache = 8;
+
+int step_graph(ks_loop* h, const bool* live, double tol, double swt, int steps,
+               const ks_loop::StepGraph** out) {
+    Work& w = h->st;
+    for (const auto& g : h->graphs)
+        if (g.live[0] == live[0] && g.live[1] == live[1] && g.tol == tol && g.swt == swt &&
+            g.par == w.par && g.xi == h->xi && g.steps == steps) {
+            *out = &g;
+            return KS_OK;
+        }
+    if (!h->gcap) {
+        KS_CUDA(cudaStreamCreateWithFlags(&h->gcap, cudaStreamNonBlocking));
+        KS_CUDA(cudaStreamCreateWithFlags(&h->gcap2, cudaStreamNonBlocking));
+        KS_CUDA(cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming));
+        KS_CUDA(cudaEventCreateWithFlags(&h->gjoin, cudaEventDisableTiming));
+    }
+    const bool both = live[P32] && live[P64];
+    const int par0 = w.par;
+    const long long l0 = h->launches;
+    KS_CUDA(cudaStreamBeginCapture(h->gcap, cudaStreamCaptureModeThreadLocal));
+    int rc = KS_OK;
+    for (int i = 0; i < steps && rc == KS_OK; ++i) {
+        cudaStream_t s64 = h->gcap;
+        if (both) {
+            if (cudaEventRecord(h->gfork, h->gcap) != cudaSuccess ||
+                cudaStreamWaitEvent(h->gcap2, h->gfork, 0) != cudaSuccess) {
+                rc = fail(KS_ERR_CUDA, "graph capture: fork failed");
+                break;
+            }
+            s64 = h->gcap2;
+        }
+        if (live[P32]) rc = run_step<float>(h, w, P32, tol, swt, h->gcap);
+        if (rc == KS_OK && live[P64]) rc = run_step<double>(h, w, P64, tol, 0.0, s64);
+        if (rc == KS_OK && both &&
+            (cudaEventRecord(h->gjoin, h->gcap2) != cudaSuccess ||
+             cudaStreamWaitEvent(h->gcap, h->gjoin, 0) != cudaSuccess))
+            rc = fail(KS_ERR_CUDA, "graph capture: join failed");
+        w.par ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->gcap, &graph);
+    w.par = par0;
+    ks_loop::StepGraph g{};
+    g.launches = h->launches - l0;
+    h->launches = l0;
+    if (rc != KS_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != KS_OK ? rc : fail(KS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    KS_CUDA(ei);
+    g.live[0] = live[0];
+    g.live[1] = live[1];
+    g.tol = tol;
+    g.swt = swt;
+    g.par = par0;
+    g.xi = h->xi;
+    g.steps = steps;
+    if (h->graphs.size() >= kGraphCache) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(g);
+    *out = &h->graphs.back();
+    return KS_OK;
+}
+
 // run n steps of the resident state on the precisions that have live loops
 int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_switch = true) {
     Work& w = h->st;
@@ -1365,7 +1461,20 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_
         }
         return KS_OK;
     }
-    for (long long i = 0; i < n; ++i) {
+    long long i = 0;
+    if (h->graph && !h->prof) {
+        while (n - i >= 2) {
+            const int G = (int)std::min<long long>(kGraphSteps, (n - i) & ~1LL);
+            const ks_loop::StepGraph* g = nullptr;
+            KS_TRY(step_graph(h, live, tol, swt, G, &g));
+            for (const long long end = i + (n - i) / G * G; i < end; i += G) {
+                KS_CUDA(cudaGraphLaunch(g->exec, s));
+                h->launches += g->launches;
+                h->graph_replays++;
+            }
+        }
+    }
+    for (; i < n; ++i) {
         if (live[P32]) KS_TRY(run_step<float>(h, w, P32, tol, swt, s));
         if (live[P64]) KS_TRY(run_step<double>(h, w, P64, tol, 0.0, s));
         w.par ^= 1;
@@ -2038,6 +2147,8 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
     } else if (k == "stall_drop_ppm") {
         if (value < 0 || value >= 1000000) return fail(KS_ERR_ARG, "stall_drop_ppm in [0, 1e6)");
         h->stall_drop = (double)value * 1e-6;
+    } else if (k == "graph") {
+        h->graph = value ? 1 : 0;
     } else if (k == "chunk") {
         if (value < 1) return fail(KS_ERR_ARG, "chunk must be >= 1");
         h->chunk = (int)std::min<long long>(value, 1 << 30);
@@ -2066,6 +2177,8 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "stall_window") *value = h->stall_window;
     else if (k == "stall_drop_ppm") *value = std::llround(h->stall_drop * 1e6);
     else if (k == "chunk") *value = h->chunk;
+    else if (k == "graph") *value = h->graph;
+    else if (k == "graph_replays") *value = h->graph_replays;
     else if (k == "symmetry") *value = h->xi;
     else if (k == "extrapolate") *value = h->extrapolate;
     else if (k == "extrapolate_start_ppm") *value = std::llround(h->extrap_start * 1e6);
