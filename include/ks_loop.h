@@ -193,15 +193,20 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
                            long long* total_launches, int reset);
 
 /* Tuning knobs of a handle (KS_ERR_ARG for an unknown key or a bad value):
- *   "path"           launch shape of ks_step / descent chunks: 0 cluster-resident kernel (one
- *                    thread-block cluster per loop, state in shared memory for the whole chunk,
- *                    falls back to 1 where the loop does not fit); 1 one cooperative launch per
- *                    chunk with grid-wide barriers between the four phases of a step; 2 four
- *                    launches per tau-step.  All three give bit-identical results.  Default at
- *                    create: 2 for ragged batches (unequal Ns) of 64 or more loops and for
- *                    KS_FP64 batches whose cluster plan has 1 or 2 CTAs per loop on loops of
- *                    Nx Ns >= 4096 points, else 0 (the faster form in measurements on GB300;
- *                    ks_autotune chooses by timing instead).
+ *   "path"           launch shape of ks_step / descent chunks, for both precisions: 0
+ *                    cluster-resident kernel (one thread-block cluster per loop, state in shared
+ *                    memory for the whole chunk, falls back to 1 where the loop does not fit);
+ *                    1 one cooperative launch per chunk with grid-wide barriers between the four
+ *                    phases of a step; 2 four launches per tau-step (replayed as CUDA graphs, see
+ *                    "graph").  All three give bit-identical results.
+ *   "path_f64", "path_f32"  the same for the double or the float steps alone (the loops of a
+ *                    KS_MIXED batch in each precision are stepped by their own precision's form).
+ *                    Default at create, with P = Nx * max Ns (the faster form in measurements on
+ *                    GB300): 2 for ragged batches (unequal Ns) of 64 or more loops; double: 2
+ *                    when P >= 16384, or P >= 8192 in batches of 8 or more, or when the cluster
+ *                    plan has 1 or 2 CTAs per loop on P >= 4096 in a batch; float: 2 when
+ *                    P >= 32768, or P >= 16384 in batches of 64 or more; else 0.  ks_autotune
+ *                    replaces the bulk precision's form (float for KS_MIXED) by timing.
  *   "persistent"     1: path 1, 0: path 2 (older spelling of "path")
  *   "cluster"        0 (default): cluster size chosen per precision; 1..16: force this size
  *                    (KS_ERR_ARG when no plan of that size fits the batch)
@@ -261,10 +266,13 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *   "switch_probe_steps"  double steps of a probe, 1 .. 1e6 (default 1000)
  *   "finish_f32_adjoint"  KS_MIXED handles: 1 (default): the finishing steps keep the state,
  *                    the residual, J, dJ/dT and the update in double and form only the descent
- *                    direction G (the adjoint half of a step) in float; 0: all-double finish */
+ *                    direction G (the adjoint half of a step) in float, in the cluster-resident
+ *                    form (the other forms finish all in double); 0: all-double finish.  With 0
+ *                    every launch form gives bit-identical mixed descents. */
 KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
 
-/* Read a knob or a derived launch parameter: "path", "finish_f32_adjoint", "switch_probe",
+/* Read a knob or a derived launch parameter: "path" (the bulk precision's: float for KS_FP32
+ * and KS_MIXED handles), "path_f64", "path_f32", "finish_f32_adjoint", "switch_probe",
  * "switch_probe_steps", "cluster_f64",
  * "cluster_f32", "cluster_mixed_finish" (cluster
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",

@@ -2,9 +2,10 @@
 
 A checkpoint is an .npz file holding the handle's configuration (L, Nx, the Ns list, mode,
 scheme, dtau, tolerances), its descent knobs (``KNOBS``: symmetry, extrapolation, stall window
-and threshold, mixed finish, chunk, launch path), the band state of every loop (ks_get_band: the
-Fourier coefficients u_hat of Eq. 2D_Fourier, widened to double), T, the step counters, the
-precision each loop descends in, each loop's status and its convergence history.
+and threshold, mixed finish, chunk, each precision's launch form, graph replay), the band state
+of every loop (ks_get_band: the Fourier coefficients u_hat of Eq. 2D_Fourier, widened to
+double), T, the step counters, the precision each loop descends in, each loop's status and its
+convergence history.
 
 Resuming creates a handle with the same configuration and knobs and installs the band with
 ks_set_band.  What is and is not restored:
@@ -30,7 +31,7 @@ VERSION = 2
 # knobs of ks_set_option that change how the descent proceeds (saved and restored)
 KNOBS = ("symmetry", "extrapolate", "extrapolate_start_ppm", "extrapolate_drop_ppm",
          "stall_window", "stall_drop_ppm", "finish_f32_adjoint", "switch_probe",
-         "switch_probe_steps", "chunk", "path")
+         "switch_probe_steps", "chunk", "path_f64", "path_f32", "graph")
 
 
 def save(loop: "K.KSLoop", path: str, tol: float = 1e-10, switch_tol: float = 0.0) -> None:

@@ -299,9 +299,9 @@ struct ks_loop {
     void* d_lin[2] = {nullptr, nullptr};
     void* d_cq[2] = {nullptr, nullptr};
     void* d_insv[2] = {nullptr, nullptr};
-    // launch path: 0 = cluster-resident kernel when its plan fits, else 1; 1 = grid-persistent
-    // cooperative kernel; 2 = four launches per tau-step
-    int path = 0;
+    // launch path of each precision (index P64, P32): 0 = cluster-resident kernel when its plan
+    // fits, else 1; 1 = grid-persistent cooperative kernel; 2 = four launches per tau-step
+    int path[2] = {0, 0};
     int force_cluster = 0;          // 0: choose the cluster size; else use this one
     ClusterPlan cplan[3] = {};      // double, float, double + float adjoint; bytes = 0: unavailable
     int cthreads = 128;
@@ -354,6 +354,7 @@ struct ks_loop {
     cudaEvent_t gfork = nullptr, gjoin = nullptr;
     struct StepGraph {
         cudaGraphExec_t exec;
+        const void* work;  // the workspace whose buffers the launches use
         bool live[2];
         double tol, swt;
         int par, xi, steps;
@@ -732,27 +733,45 @@ int setup_cluster(ks_loop* h) {
     return KS_OK;
 }
 
-// Default launch form of ks_step / descent chunks (the "path" knob), from steady-state timings of
-// the three forms on GB300 over uniform and ragged batches of 96-1024 loops (all three compute
-// the same bits, so this only sets the speed):
+// Default launch form of each precision's steps (the "path" knob, set per precision), from
+// steady-state step times on GB300 of the cluster-resident kernel against the four-launch form
+// replayed as graphs, over loops of 32x64 to 256x1024 points in batches of 1-128 (and ragged
+// batches of 64-1024 loops).  All forms compute the same bits, so this only sets the speed.
+// P = Nx * max Ns, the points of the longest loop:
 //   * ragged batches (loops of unequal Ns) of 64 or more loops: four launches per step.  One
-//     cluster per loop leaves the SMs that hold the long loops working while the rest idle
-//     (ragged 64 x {32..256}: FP64 1.1-2.0x, FP32 1.5-2.3x faster per step);
-//   * double batches whose cluster plan has 1 or 2 CTAs per loop, on loops of 4096 or more
-//     points: four launches per step (64 x 64, 96-1024 loops: 1.1-2.2x faster);
-//   * otherwise the cluster-resident kernel (float batches, small loops, single loops).
-// The bulk precision decides (float for KS_FP32 and KS_MIXED handles).  ks_autotune replaces the
-// choice by timing.
-int default_path(const ks_loop* h) {
+//     cluster per loop leaves the SMs that hold the long loops working while the rest idle;
+//   * double: four launches once P >= 16384, or P >= 8192 in batches of 8 or more, or when the
+//     cluster plan has 1 or 2 CTAs per loop on P >= 4096 in a batch.  A double loop of that size
+//     keeps each CTA of its cluster busy for long serial transforms (64x256 single loop: 54 us
+//     per step resident, 38 us in four launches; 256x256: 192 against 45);
+//   * float: four launches once P >= 32768, or P >= 16384 in batches of 64 or more (float
+//     transforms are short enough that the resident kernel's saved launches and round trips to
+//     memory win up to there: 64x256 x 32 loops 29.7 against 30.4 us; 256x1024 x 8 loops 305
+//     against 83);
+//   * otherwise the cluster-resident kernel.
+// ks_autotune replaces the choice of the handle's bulk precision by timing.
+int default_path(const ks_loop* h, int pr) {
     const int B = h->d.B;
     bool ragged = false;
     for (int b = 1; b < B; ++b) ragged |= (h->ns[b] != h->ns[0]);
     if (ragged && B >= 64) return 2;
-    if (h->mode == KS_FP64 && B > 1) {
+    const long long P = (long long)h->d.nx * h->nsmax;
+    if (pr == P64) {
+        if (P >= 16384 || (P >= 8192 && B >= 8)) return 2;
         const int C = h->cplan[0].bytes ? h->cplan[0].C : 0;
-        if ((C == 1 || C == 2) && (long long)h->d.nx * h->nsmax >= 4096) return 2;
+        if (B > 1 && (C == 1 || C == 2) && P >= 4096) return 2;
+        return 0;
     }
-    return 0;
+    return (P >= 32768 || (P >= 16384 && B >= 64)) ? 2 : 0;
+}
+
+// the launch form precision pr's steps take: 0 cluster-resident (where its plan fits), 1
+// grid-persistent (where its cooperative grid fits), 2 four launches per step
+int form_of(const ks_loop* h, int pr) {
+    const int p = h->path[pr];
+    if (p == 0 && h->cplan[pr].bytes > 0) return 0;
+    if (p <= 1 && h->pgrid[pr] > 0) return 1;
+    return 2;
 }
 
 // nsteps tau-steps of the live loops of precision pr, one cluster per loop
@@ -1141,7 +1160,8 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     h->h_prec.assign(B, 0);
     h->h_sqrtJ.assign(B, 0.0);
     h->h_steps.assign(B, 0);
-    h->path = default_path(h);
+    h->path[P64] = default_path(h, P64);
+    h->path[P32] = default_path(h, P32);
     if (h->autotune && (rc = ks_autotune_impl(h))) return cleanup(rc);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(fail(KS_ERR_CUDA, cudaGetErrorString(e)));
@@ -1329,12 +1349,11 @@ int set_state_full(ks_loop* h, const void* u, const double* T, cudaStream_t s) {
 constexpr int kGraphSteps = 16;
 constexpr size_t kGraphCache = 8;
 
-int step_graph(ks_loop* h, const bool* live, double tol, double swt, int steps,
+int step_graph(ks_loop* h, Work& w, const bool* live, double tol, double swt, int steps,
                const ks_loop::StepGraph** out) {
-    Work& w = h->st;
     for (const auto& g : h->graphs)
-        if (g.live[0] == live[0] && g.live[1] == live[1] && g.tol == tol && g.swt == swt &&
-            g.par == w.par && g.xi == h->xi && g.steps == steps) {
+        if (g.work == &w && g.live[0] == live[0] && g.live[1] == live[1] && g.tol == tol &&
+            g.swt == swt && g.par == w.par && g.xi == h->xi && g.steps == steps) {
             *out = &g;
             return KS_OK;
         }
@@ -1381,6 +1400,7 @@ int step_graph(ks_loop* h, const bool* live, double tol, double swt, int steps,
     const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     KS_CUDA(ei);
+    g.work = &w;
     g.live[0] = live[0];
     g.live[1] = live[1];
     g.tol = tol;
@@ -1397,76 +1417,16 @@ int step_graph(ks_loop* h, const bool* live, double tol, double swt, int steps,
     return KS_OK;
 }
 
-// run n steps of the resident state on the precisions that have live loops
-int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_switch = true) {
-    Work& w = h->st;
-    bool live[2] = {false, false};
-    for (int b = 0; b < h->d.B; ++b)
-        if (h->h_status[b] == KS_RUNNING) live[h->h_prec[b]] = true;
-    for (int pr = 0; pr < 2; ++pr) {
-        const bool clus_pr = h->path == 0 && h->cplan[pr].bytes > 0;
-        if (live[pr] && !w.mix_valid[pr] && !clus_pr) {
-            if (pr == P64) KS_TRY(run_prime<double>(h, w, pr, s));
-            else KS_TRY(run_prime<float>(h, w, pr, s));
-        }
-    }
-    const double swt = (h->mode == KS_MIXED && device_switch) ? h->switch_tol : 0.0;
-    const long long kMaxPerLaunch = 1 << 14;
-    const bool clus[2] = {h->path == 0 && h->cplan[P64].bytes > 0, h->path == 0 && h->cplan[P32].bytes > 0};
-    if ((!live[P32] || clus[P32]) && (!live[P64] || clus[P64])) {
-        // With loops live in both precisions (a mixed batch in mid-switch) the two launches
-        // touch disjoint loops: the double one runs on the side stream, concurrently, and each
-        // carries T forward only for the frozen loops of its own precision (a loop that
-        // freezes during the chunk is written by its own kernel alone).
-        const bool both = live[P32] && live[P64] && !h->prof;
-        if (both && !h->side) {
-            KS_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-            KS_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
-            KS_CUDA(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
-        }
-        for (long long done = 0; done < n;) {
-            const long long c = std::min(kMaxPerLaunch, n - done);
-            cudaStream_t s64 = s;
-            if (both) {
-                KS_CUDA(cudaEventRecord(h->fork, s));
-                KS_CUDA(cudaStreamWaitEvent(h->side, h->fork, 0));
-                s64 = h->side;
-            }
-            if (live[P32]) KS_TRY((run_cluster<float, float>(h, w, P32, c, tol, swt, s, both)));
-            if (live[P64]) {
-                if (h->mode == KS_MIXED && h->finish_f32_adjoint && h->cplan[2].bytes > 0)
-                    KS_TRY((run_cluster<double, float>(h, w, P64, c, tol, 0.0, s64, both)));
-                else
-                    KS_TRY((run_cluster<double, double>(h, w, P64, c, tol, 0.0, s64, both)));
-            }
-            if (both) {
-                KS_CUDA(cudaEventRecord(h->join, h->side));
-                KS_CUDA(cudaStreamWaitEvent(s, h->join, 0));
-            }
-            if (c & 1) w.par ^= 1;
-            done += c;
-        }
-        return KS_OK;
-    }
-    const bool pers[2] = {h->path <= 1 && h->pgrid[P64] > 0, h->path <= 1 && h->pgrid[P32] > 0};
-    if ((!live[P32] || pers[P32]) && (!live[P64] || pers[P64])) {
-        // loops are independent, so each precision's kernel may run all n steps in turn; both
-        // start from the same parity and frozen loops carry T forward in either kernel
-        for (long long done = 0; done < n;) {
-            const long long c = std::min(kMaxPerLaunch, n - done);
-            if (live[P32]) KS_TRY(run_persist<float>(h, w, P32, c, tol, swt, s));
-            if (live[P64]) KS_TRY(run_persist<double>(h, w, P64, c, tol, 0.0, s));
-            if (c & 1) w.par ^= 1;
-            done += c;
-        }
-        return KS_OK;
-    }
+// n tau-steps in the four-launch form of the precisions marked live (M primed): runs of even
+// length as graph replays unless the knob is off or profiling is on, the rest launch by launch
+int phase_steps(ks_loop* h, Work& w, const bool* live, long long n, double tol, double swt,
+                cudaStream_t s) {
     long long i = 0;
     if (h->graph && !h->prof) {
         while (n - i >= 2) {
             const int G = (int)std::min<long long>(kGraphSteps, (n - i) & ~1LL);
             const ks_loop::StepGraph* g = nullptr;
-            KS_TRY(step_graph(h, live, tol, swt, G, &g));
+            KS_TRY(step_graph(h, w, live, tol, swt, G, &g));
             for (const long long end = i + (n - i) / G * G; i < end; i += G) {
                 KS_CUDA(cudaGraphLaunch(g->exec, s));
                 h->launches += g->launches;
@@ -1479,6 +1439,99 @@ int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_
         if (live[P64]) KS_TRY(run_step<double>(h, w, P64, tol, 0.0, s));
         w.par ^= 1;
     }
+    return KS_OK;
+}
+
+constexpr long long kMaxPerLaunch = 1 << 14;
+
+// n tau-steps of the live loops of precision pr in launch form `form` (form_of), starting from
+// w.par and leaving it advanced by n.  adj32: a double cluster form of a KS_MIXED handle may
+// form the adjoint in float (the "finish_f32_adjoint" knob).
+int form_steps(ks_loop* h, Work& w, int pr, int form, long long n, double tol, double swt,
+               cudaStream_t s, bool adj32) {
+    if (form == 2) {
+        const bool live[2] = {pr == P64, pr == P32};
+        if (!w.mix_valid[pr]) {
+            if (pr == P64) KS_TRY(run_prime<double>(h, w, pr, s));
+            else KS_TRY(run_prime<float>(h, w, pr, s));
+        }
+        return phase_steps(h, w, live, n, tol, pr == P32 ? swt : 0.0, s);
+    }
+    for (long long done = 0; done < n;) {
+        const long long c = std::min(kMaxPerLaunch, n - done);
+        if (form == 0) {
+            if (pr == P32)
+                KS_TRY((run_cluster<float, float>(h, w, P32, c, tol, swt, s)));
+            else if (adj32 && h->mode == KS_MIXED && h->finish_f32_adjoint && h->cplan[2].bytes > 0)
+                KS_TRY((run_cluster<double, float>(h, w, P64, c, tol, 0.0, s)));
+            else
+                KS_TRY((run_cluster<double, double>(h, w, P64, c, tol, 0.0, s)));
+        } else {
+            if (!w.mix_valid[pr]) {
+                if (pr == P64) KS_TRY(run_prime<double>(h, w, pr, s));
+                else KS_TRY(run_prime<float>(h, w, pr, s));
+            }
+            if (pr == P32) KS_TRY(run_persist<float>(h, w, P32, c, tol, swt, s));
+            else KS_TRY(run_persist<double>(h, w, P64, c, tol, 0.0, s));
+        }
+        if (c & 1) w.par ^= 1;
+        done += c;
+    }
+    return KS_OK;
+}
+
+// run n steps of the resident state on the precisions that have live loops.  The loops of the
+// two precisions are disjoint and independent, so each precision may take its own launch form
+// and run its n steps from the same parity; where both take the cluster form (and profiling is
+// off) the double launch runs beside the float one on the side stream, where both take the
+// four-launch form their graphs hold the two chains as parallel branches.
+int steps_impl(ks_loop* h, long long n, double tol, cudaStream_t s, bool device_switch = true) {
+    Work& w = h->st;
+    bool live[2] = {false, false};
+    for (int b = 0; b < h->d.B; ++b)
+        if (h->h_status[b] == KS_RUNNING) live[h->h_prec[b]] = true;
+    const double swt = (h->mode == KS_MIXED && device_switch) ? h->switch_tol : 0.0;
+    const int form[2] = {form_of(h, P64), form_of(h, P32)};
+    if (live[P32] && live[P64] && form[P32] == 2 && form[P64] == 2) {
+        for (int pr = 0; pr < 2; ++pr)
+            if (!w.mix_valid[pr]) {
+                if (pr == P64) KS_TRY(run_prime<double>(h, w, pr, s));
+                else KS_TRY(run_prime<float>(h, w, pr, s));
+            }
+        return phase_steps(h, w, live, n, tol, swt, s);
+    }
+    if (live[P32] && live[P64] && form[P32] == 0 && form[P64] == 0 && !h->prof) {
+        // each launch carries T forward only for the frozen loops of its own precision (a loop
+        // that freezes during the chunk is written by its own kernel alone)
+        if (!h->side) {
+            KS_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+            KS_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+            KS_CUDA(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+        }
+        for (long long done = 0; done < n;) {
+            const long long c = std::min(kMaxPerLaunch, n - done);
+            KS_CUDA(cudaEventRecord(h->fork, s));
+            KS_CUDA(cudaStreamWaitEvent(h->side, h->fork, 0));
+            KS_TRY((run_cluster<float, float>(h, w, P32, c, tol, swt, s, true)));
+            if (h->mode == KS_MIXED && h->finish_f32_adjoint && h->cplan[2].bytes > 0)
+                KS_TRY((run_cluster<double, float>(h, w, P64, c, tol, 0.0, h->side, true)));
+            else
+                KS_TRY((run_cluster<double, double>(h, w, P64, c, tol, 0.0, h->side, true)));
+            KS_CUDA(cudaEventRecord(h->join, h->side));
+            KS_CUDA(cudaStreamWaitEvent(s, h->join, 0));
+            if (c & 1) w.par ^= 1;
+            done += c;
+        }
+        return KS_OK;
+    }
+    // one precision at a time, each from the same parity
+    const int par0 = w.par;
+    for (int pr : {P32, P64}) {
+        if (!live[pr]) continue;
+        w.par = par0;
+        KS_TRY(form_steps(h, w, pr, form[pr], n, tol, swt, s, true));
+    }
+    w.par = par0 ^ (int)(n & 1);
     return KS_OK;
 }
 
@@ -1599,22 +1652,7 @@ int polish_probe(ks_loop* h, cudaStream_t s, const std::vector<int>& sel, long l
     KS_CUDA(cudaMemcpyAsync(a.prec, pr.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
     KS_CUDA(cudaMemsetAsync(a.steps, 0, B * sizeof(long long), s));
     a.mix_valid[P64] = false;
-    const bool clus = h->path == 0 && h->cplan[P64].bytes > 0;
-    const bool pers = h->path <= 1 && h->pgrid[P64] > 0;
-    const long long kMaxPerLaunch = 1 << 14;
-    for (long long done = 0; done < n;) {
-        const long long c = (clus || pers) ? std::min(kMaxPerLaunch, n - done) : 1;
-        if (clus) {
-            KS_TRY((run_cluster<double, double>(h, a, P64, c, 0.0, 0.0, s)));
-        } else if (pers) {
-            KS_TRY(run_persist<double>(h, a, P64, c, 0.0, 0.0, s));
-        } else {
-            if (!a.mix_valid[P64]) KS_TRY(run_prime<double>(h, a, P64, s));
-            KS_TRY(run_step<double>(h, a, P64, 0.0, 0.0, s));
-        }
-        if (c & 1) a.par ^= 1;
-        done += c;
-    }
+    KS_TRY(form_steps(h, a, P64, form_of(h, P64), n, 0.0, 0.0, s, false));
     const double* Tc = a.T + (size_t)a.par * B;
     KS_TRY(run_residual<double>(h, a, P64, s));
     KS_TRY(run_finalize(h, a, Tc, P64, 0, s));
@@ -2109,10 +2147,11 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
     if (!key) return fail(KS_ERR_ARG, "null option name");
     const std::string k(key);
     if (k == "persistent") {
-        h->path = value ? 1 : 2;
-    } else if (k == "path") {
+        h->path[P64] = h->path[P32] = value ? 1 : 2;
+    } else if (k == "path" || k == "path_f64" || k == "path_f32") {
         if (value < 0 || value > 2) return fail(KS_ERR_ARG, "path must be 0, 1 or 2");
-        h->path = (int)value;
+        if (k != "path_f32") h->path[P64] = (int)value;
+        if (k != "path_f64") h->path[P32] = (int)value;
     } else if (k == "cluster") {
         if (value < 0 || value > 16) return fail(KS_ERR_ARG, "cluster must be 0 (auto) or 1..16");
         h->force_cluster = (int)value;
@@ -2163,7 +2202,9 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     KS_TRY(check_handle(h));
     if (!key || !value) return fail(KS_ERR_ARG, "null argument");
     const std::string k(key);
-    if (k == "path") *value = h->path;
+    if (k == "path") *value = h->path[h->mode == KS_FP64 ? P64 : P32];
+    else if (k == "path_f64") *value = h->path[P64];
+    else if (k == "path_f32") *value = h->path[P32];
     else if (k == "cluster_f64") *value = h->cplan[0].bytes ? h->cplan[0].C : 0;
     else if (k == "cluster_f32") *value = h->cplan[1].bytes ? h->cplan[1].C : 0;
     else if (k == "cluster_smem_f64") *value = h->cplan[0].bytes;
@@ -2264,8 +2305,11 @@ void cache_store(const std::string& key, const TuneChoice& c) {
     std::fclose(f);
 }
 
+// the tuned precision's launch form (both for single-precision handles; the float bulk of a
+// KS_MIXED handle, whose double finish keeps the default rule's form)
 int apply_choice(ks_loop* h, const TuneChoice& c) {
-    h->path = c.path;
+    h->path[P32] = c.path;
+    if (h->mode != KS_MIXED) h->path[P64] = c.path;
     h->force_cluster = c.cluster;
     h->cthreads = c.threads;
     KS_TRY((setup_cluster<double, double>(h)));

@@ -62,9 +62,11 @@ def test_invalid_cache_entry_is_ignored(tmp_path, monkeypatch):
 
 
 def test_default_launch_path_rule():
-    """The launch form chosen at create without tuning: four launches per step for ragged batches
-    of 64 or more loops and for double batches whose cluster plan has 1 or 2 CTAs per loop on loops
-    of 4096 or more points; the cluster-resident kernel otherwise."""
+    """The launch form chosen at create without tuning, per precision (P = Nx * max Ns): four
+    launches per step for ragged batches of 64 or more loops; in double once P >= 16384, or
+    P >= 8192 in batches of 8 or more, or with 1 or 2 CTAs per loop's cluster on P >= 4096; in
+    float once P >= 32768, or P >= 16384 in batches of 64 or more; the cluster-resident kernel
+    otherwise.  "path" reads the bulk precision's form (float for mixed handles)."""
     from paper_2007_06427_gb300.inputs import workload
     rg = workload("ragged256_64xNs", batch=64)
     for mode in (K.KS_FP64, K.KS_FP32, K.KS_MIXED):
@@ -81,3 +83,20 @@ def test_default_launch_path_rule():
     with K.KSLoop(22.0, 64, [128], K.KS_FP64) as h:          # the single loop
         assert K.ks_get_option(h.handle, "path") == 0
         assert K.ks_get_option(h.handle, "cluster_f64") == 16
+    with K.KSLoop(22.0, 64, [128] * 8, K.KS_FP64) as h:      # 8192 points, 8 loops
+        assert K.ks_get_option(h.handle, "path") == 2
+    with K.KSLoop(22.0, 64, [256], K.KS_MIXED) as h:         # 16384 points, one loop
+        assert K.ks_get_option(h.handle, "path") == 0
+        assert K.ks_get_option(h.handle, "path_f32") == 0
+        assert K.ks_get_option(h.handle, "path_f64") == 2
+    with K.KSLoop(44.0, 128, [128] * 64, K.KS_FP32) as h:    # 16384 points, 64 loops
+        assert K.ks_get_option(h.handle, "path") == 2
+    for mode in (K.KS_FP64, K.KS_FP32, K.KS_MIXED):          # the large domain, 8 loops
+        with K.KSLoop(100.0, 256, [1024] * 8, mode) as h:
+            assert K.ks_get_option(h.handle, "path_f64") == 2, mode
+            assert K.ks_get_option(h.handle, "path_f32") == 2, mode
+    with K.KSLoop(22.0, 64, [256], K.KS_MIXED) as h:
+        K.ks_set_option(h.handle, "path", 1)
+        assert (K.ks_get_option(h.handle, "path_f64"), K.ks_get_option(h.handle, "path_f32")) == (1, 1)
+        K.ks_set_option(h.handle, "path_f64", 0)
+        assert (K.ks_get_option(h.handle, "path_f64"), K.ks_get_option(h.handle, "path_f32")) == (0, 1)

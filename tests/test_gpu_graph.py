@@ -84,3 +84,27 @@ def test_graph_mixed_batch_in_both_precisions_equals_direct():
         assert (replays > 0) == bool(graph)
     for a, b in zip(outs[0], outs[1]):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("forms", [(0, 2), (2, 0), (1, 2), (2, 1), (2, 2)])
+def test_per_precision_launch_forms_equal_cluster_forms(forms):
+    """Each precision of a mixed batch stepped by its own launch form (float form, double form):
+    the descent through the switch, with loops live in both precisions at once, equals the one
+    with both precisions in the cluster-resident form bit for bit."""
+    L, nx, nss = 22.0, 32, [32, 32, 64, 32]
+    us, Ts = loops(nx, nss, L, T_range=(30.0, 50.0), scale=(1e-2, 3e-3, 1e-2, 1.0))
+    outs = []
+    for f32, f64 in ((0, 0), forms):
+        u, T = to_dev(us, Ts, K.KS_FP64)
+        steps = torch.zeros(4, dtype=torch.int64, device="cuda")
+        sq = torch.zeros(4, dtype=torch.float64, device="cuda")
+        st = torch.zeros(4, dtype=torch.int32, device="cuda")
+        with K.KSLoop(L, nx, nss, K.KS_MIXED, K.KS_IMEX, 0.15, tol=1e-10, switch_tol=1e-5,
+                      chunk=500) as h:
+            K.ks_set_option(h.handle, "finish_f32_adjoint", 0)
+            K.ks_set_option(h.handle, "path_f32", f32)
+            K.ks_set_option(h.handle, "path_f64", f64)
+            K.ks_descend(h.handle, u, T, 60000, 1e-10, steps, sq, st)
+        outs.append((u.cpu(), T.cpu(), steps.cpu(), st.cpu()))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
