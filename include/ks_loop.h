@@ -208,6 +208,12 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *                    P >= 32768, or P >= 16384 in batches of 64 or more; else 0.  ks_autotune
  *                    replaces the bulk precision's form (float for KS_MIXED) by timing.
  *   "persistent"     1: path 1, 0: path 2 (older spelling of "path")
+ *   "row_threads", "col_threads"  path 2: threads per block of the row and column items, 128
+ *                    or 256 (results are bit-identical: a column's partials of J and L^dag_2
+ *                    keep 128 accumulators at either size).  Default at create: 256-thread rows
+ *                    for Nx >= 256; 256-thread columns when the batch has fewer than 152 column
+ *                    items (loops x retained x-modes, one per SM of a GB300) and max Ns >= 256;
+ *                    else 128.
  *   "cluster"        0 (default): cluster size chosen per precision; 1..16: force this size
  *                    (KS_ERR_ARG when no plan of that size fits the batch)
  *   "symmetry"       1: restrict the descent to loops invariant under Xi: (x, s) -> (-x, s),
@@ -278,6 +284,7 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
  * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "stall_drop_ppm",
  * "chunk", "symmetry", "graph", "graph_replays" (graphs replayed since create),
+ * "row_threads", "col_threads",
  * "extrapolate", "extrapolate_start_ppm", "extrapolate_drop_ppm", "extrapolations",
  * "extrapolations_rejected". */
 KS_API int ks_get_option(ks_loop_t h, const char* key, long long* value);

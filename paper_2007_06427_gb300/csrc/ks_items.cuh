@@ -1037,7 +1037,7 @@ enum ColMode {
 };
 
 // Shared-memory bytes a column item needs beyond its two transform buffers.
-constexpr int COL_RED_DOUBLES = 4 * (256 / 32 + 1) + 4;
+constexpr int COL_RED_DOUBLES = 4 * (256 / 32 + 1) + 4;  // blocks of up to 256 threads
 
 // 1 / (2 pi), for L^dag_2 = (L / T^2) 2 pi S = L (2 pi / T)^2 S / (2 pi) from the stored 2 pi / T
 constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
@@ -1047,6 +1047,16 @@ constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
 // (and everything downstream of it) is the same bits in the item kernels (128 threads) and in a
 // cluster kernel of 128 or 256 threads.
 constexpr int COL_ACC_LANES = 128;
+
+// A column item of more than COL_ACC_LANES threads forms r_hat with all of them, then its first
+// COL_ACC_LANES threads accumulate the column from the stored band (the same values in the same
+// order per accumulator); with exactly COL_ACC_LANES threads the accumulation is fused into the
+// loop that forms r_hat.
+#ifdef KS_HOST_EMULATION
+#define KS_ACC_FUSED true
+#else
+#define KS_ACC_FUSED ((int)blockDim.x == COL_ACC_LANES)
+#endif
 
 // ---- centre-symmetric (Xi) subspace: columns in pairs --------------------------------------
 // In the subspace u_hat_{j,-k} = -conj(u_hat_{j,k}) and the j = 0 column is zero, so the s-series
@@ -1162,6 +1172,7 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
 
         if constexpr (MODE == COL_RESID) {
             ColAcc<R> acc[2];
+            const bool fused = KS_ACC_FUSED;
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
                 cpx<R> x = zero;
@@ -1173,14 +1184,14 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
                     const cpx<R> ua = p.uh[ba + (k + ks)];
                     const cpx<R> ra = mk<R>(lin_a * ua.x - bk * ua.y - pa.x, lin_a * ua.y + bk * ua.x - pa.y);
                     p.rh[ba + (k + ks)] = ra;
-                    acc[0].add(ua, ra, k);                    // a6
+                    if (fused) acc[0].add(ua, ra, k);         // a6
                     cpx<R> xb = zero;
                     if (hasb) {
                         const cpx<R> pb = scale(xi_split_b(ck, cm), ins);
                         const cpx<R> ub = p.uh[bb + (k + ks)];
                         const cpx<R> rb = mk<R>(lin_b * ub.x - bk * ub.y - pb.x, lin_b * ub.y + bk * ub.x - pb.y);
                         p.rh[bb + (k + ks)] = rb;
-                        acc[1].add(ub, rb, k);
+                        if (fused) acc[1].add(ub, rb, k);
                         xb = mk<R>(-q_b * rb.y, q_b * rb.x);   // i q_j r_hat                 (a7)
                     }
                     x = xi_join_real(mk<R>(-q_a * ra.y, q_a * ra.x), xb);
@@ -1188,6 +1199,14 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
                 X[i] = x;
             }
             KS_SYNC();
+            if (!fused && KS_TID < COL_ACC_LANES)
+                for (int i = KS_TID; i < ns; i += COL_ACC_LANES) {
+                    const int k = (i < (ns >> 1)) ? i : i - ns;
+                    if (k >= -ks && k <= ks) {
+                        acc[0].add(p.uh[ba + (k + ks)], p.rh[ba + (k + ks)], k);
+                        if (hasb) acc[1].add(p.uh[bb + (k + ks)], p.rh[bb + (k + ks)], k);
+                    }
+                }
             const cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 cola[i] = mk<R>(v[i].x, 0);
@@ -1380,6 +1399,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
 
         if constexpr (MODE == COL_RESID) {
             ColAcc<R> acc;
+            const bool fused = KS_ACC_FUSED;
             for (int i = KS_TID; i < ns; i += KS_NT) {
                 const int k = (i < (ns >> 1)) ? i : i - ns;
                 cpx<R> x = mk<R>(0, 0);
@@ -1390,12 +1410,17 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     // r_hat = (a + i bk) u_hat - p_hat                                    (a5)
                     const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
                     p.rh[bo + (k + ks)] = r;
-                    acc.add(u, r, k);                         // a6: |r|^2, k Im(conj(u) r)
+                    if (fused) acc.add(u, r, k);              // a6: |r|^2, k Im(conj(u) r)
                     x = mk<R>(-rq * r.y, rq * r.x);           // i q_j r_hat                 (a7)
                 }
                 X[i] = x;
             }
             KS_SYNC();
+            if (!fused && KS_TID < COL_ACC_LANES)
+                for (int i = KS_TID; i < ns; i += COL_ACC_LANES) {
+                    const int k = (i < (ns >> 1)) ? i : i - ns;
+                    if (k >= -ks && k <= ks) acc.add(p.uh[bo + (k + ks)], p.rh[bo + (k + ks)], k);
+                }
             cpx<R>* v = fft_col<R, SWZ>(X, F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
             block_reduce(acc, red);

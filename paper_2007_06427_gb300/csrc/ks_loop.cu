@@ -1136,17 +1136,22 @@ extern "C" int ks_loop_create(const ks_config* cfg, ks_loop_t* out) {
     bool api_need[2] = {true, h->api_prec == P32};
     if ((rc = alloc_work(h, h->st, st_need)) || (rc = alloc_work(h, h->api, api_need)))
         return cleanup(rc);
-    // launch shapes
+    // launch shapes.  Block sizes from step times of the four-launch form on GB300: 256-thread
+    // row items for rows of 256 points or more (256 x 1024, 8 loops: 505 against 546 us per
+    // double step), 256-thread column items only when the columns are fewer than the SMs and
+    // long (one 256 x 1024 loop: 102 against 113 us); batches with more column items run
+    // them faster at 128 threads (ragged 64 x {32..256}, 256 loops: 405 against 479 us).
+    const int ncolitems = B * h->d.nkx;
     for (int pr = 0; pr < 2; ++pr) {
         const size_t cs = pr == P64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
         const size_t tw_bytes = (size_t)std::max(h->d.nx, h->nsmax) * cs;  // compact table
         Launch& lr = h->lrow[pr];
-        lr.threads = 128;
+        lr.threads = h->d.nx >= 256 ? 256 : 128;
         lr.tw_off = (2 * (size_t)h->rows_per_tile * h->d.nx * cs + 15) & ~(size_t)15;
         lr.smem = lr.tw_off + tw_bytes;
         lr.grid = 152 * 16;
         Launch& lc = h->lcol[pr];
-        lc.threads = COL_ACC_LANES;  // the column partials' accumulation width (ks_items.cuh)
+        lc.threads = (ncolitems < 152 && h->nsmax >= 256) ? 256 : 128;
         lc.tw_off = (2 * (size_t)h->nsmax * cs + COL_RED_DOUBLES * sizeof(double) + 15) & ~(size_t)15;
         lc.smem = lc.tw_off + tw_bytes;
         lc.grid = 152 * 16;
@@ -1409,6 +1414,7 @@ int step_graph(ks_loop* h, Work& w, const bool* live, double tol, double swt, in
     g.xi = h->xi;
     g.steps = steps;
     if (h->graphs.size() >= kGraphCache) {
+        KS_CUDA(cudaDeviceSynchronize());  // the oldest graph may still be replaying
         cudaGraphExecDestroy(h->graphs.front().exec);
         h->graphs.erase(h->graphs.begin());
     }
@@ -1478,6 +1484,14 @@ int form_steps(ks_loop* h, Work& w, int pr, int form, long long n, double tol, d
         done += c;
     }
     return KS_OK;
+}
+
+// destroy the cached graphs once no replay of them can still be queued on any stream
+void drop_graphs(ks_loop* h) {
+    if (h->graphs.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
 }
 
 // run n steps of the resident state on the precisions that have live loops.  The loops of the
@@ -2188,6 +2202,10 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         h->stall_drop = (double)value * 1e-6;
     } else if (k == "graph") {
         h->graph = value ? 1 : 0;
+    } else if (k == "row_threads" || k == "col_threads") {
+        if (value != 128 && value != 256) return fail(KS_ERR_ARG, k + " must be 128 or 256");
+        for (int pr = 0; pr < 2; ++pr) (k == "row_threads" ? h->lrow : h->lcol)[pr].threads = (int)value;
+        drop_graphs(h);
     } else if (k == "chunk") {
         if (value < 1) return fail(KS_ERR_ARG, "chunk must be >= 1");
         h->chunk = (int)std::min<long long>(value, 1 << 30);
@@ -2219,6 +2237,8 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "stall_drop_ppm") *value = std::llround(h->stall_drop * 1e6);
     else if (k == "chunk") *value = h->chunk;
     else if (k == "graph") *value = h->graph;
+    else if (k == "row_threads") *value = h->lrow[P64].threads;
+    else if (k == "col_threads") *value = h->lcol[P64].threads;
     else if (k == "graph_replays") *value = h->graph_replays;
     else if (k == "symmetry") *value = h->xi;
     else if (k == "extrapolate") *value = h->extrapolate;

@@ -108,3 +108,31 @@ def test_per_precision_launch_forms_equal_cluster_forms(forms):
         outs.append((u.cpu(), T.cpu(), steps.cpu(), st.cpu()))
     for a, b in zip(outs[0], outs[1]):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("symmetry", [0, 1])
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+def test_item_block_sizes_give_the_same_bits(mode, symmetry):
+    """Row and column items of 256 threads (knobs "row_threads", "col_threads"): the column
+    partials of J and L^dag_2 keep their 128 accumulators, so the descent and the reported
+    sqrt(J) equal those of 128-thread items bit for bit."""
+    L, nx, nss = 22.0, 64, [32, 64, 128, 256, 64, 32]
+    us, Ts = loops(nx, nss, L)
+    out = []
+    for rt, ct in ((128, 128), (256, 128), (128, 256), (256, 256)):
+        u, T = to_dev(us, Ts, mode)
+        sq = torch.zeros(len(nss), dtype=torch.float64, device="cuda")
+        with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15) as h:
+            K.ks_set_option(h.handle, "path", 2)
+            K.ks_set_option(h.handle, "symmetry", symmetry)
+            K.ks_set_option(h.handle, "row_threads", rt)
+            K.ks_set_option(h.handle, "col_threads", ct)
+            assert (K.ks_get_option(h.handle, "row_threads"), K.ks_get_option(h.handle, "col_threads")) == (rt, ct)
+            K.ks_set_state(h.handle, u, T)
+            K.ks_step(h.handle, 9, 0.0)
+            K.ks_get_state(h.handle, u, T, None, sq)
+            torch.cuda.synchronize()
+        out.append((u.cpu(), T.cpu(), sq.cpu()))
+    for o in out[1:]:
+        for a, b in zip(out[0], o):
+            assert torch.equal(a, b)
