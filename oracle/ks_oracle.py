@@ -436,3 +436,114 @@ def adjoint_grad_batch(us, Ts, L, xi=False):
 
 def descend_batch(us, Ts, L, dtau, scheme, nsteps, tol=0.0, xi=False):
     return [descend(u, T, L, dtau, scheme, nsteps, tol, xi=xi) for u, T in zip(us, Ts)]
+
+
+# ---------------------------------------------------------------------------------------
+# Time integration of the KSE itself, for the initial guesses (Sec. 4.3)
+# ---------------------------------------------------------------------------------------
+# The paper takes its initial loops from a chaotic solution u(x, t) of u_t = -u u_x - u_xx
+# - u_xxxx on [0, L) (Sec. 4.3); it does not name the integrator.  Reading: a Fourier
+# pseudo-spectral discretisation with Nx points, 2/3-rule dealiasing of the product (as in the
+# descent, Sec. 4.2), and fourth-order exponential time differencing (ETDRK4 of Cox & Matthews,
+# J. Comput. Phys. 176, 2002), whose linear part is the exact diagonal symbol q^2 - q^4.  Here
+# everything is a dense DFT over the signed modes, and the phi-functions come from their power
+# series or closed forms (not a contour integral).  parity pins: a conserved mean, a constant
+# state, fourth-order convergence under dt halving, agreement with classical RK4 at a step far
+# inside its stability limit, and the centre-symmetric subspace kept exactly.
+
+def etd_phi(z: np.ndarray):
+    """phi_1, phi_2, phi_3 at real z: phi_k(z) = sum_{m >= 0} z^m / (m + k)!.
+
+    |z| < 1: the series (30 terms); otherwise phi_1 = (e^z - 1) / z, phi_2 = (phi_1 - 1) / z,
+    phi_3 = (phi_2 - 1/2) / z."""
+    z = np.asarray(z, dtype=np.float64)
+    p1 = np.empty_like(z)
+    p2 = np.empty_like(z)
+    p3 = np.empty_like(z)
+    small = np.abs(z) < 1.0
+    zs = z[small]
+    s1 = np.zeros_like(zs)
+    s2 = np.zeros_like(zs)
+    s3 = np.zeros_like(zs)
+    for m in range(29, -1, -1):                      # Horner from the smallest term
+        s1 = s1 * zs + 1.0 / math.factorial(m + 1)
+        s2 = s2 * zs + 1.0 / math.factorial(m + 2)
+        s3 = s3 * zs + 1.0 / math.factorial(m + 3)
+    p1[small], p2[small], p3[small] = s1, s2, s3
+    zl = z[~small]
+    q1 = np.expm1(zl) / zl
+    q2 = (q1 - 1.0) / zl
+    q3 = (q2 - 0.5) / zl
+    p1[~small], p2[~small], p3[~small] = q1, q2, q3
+    return p1, p2, p3
+
+
+def dns_coefficients(L: float, Nx: int, dt: float):
+    """Wavenumbers, dealiasing mask, and the ETDRK4 weights of each signed x-mode j:
+    E = e^z, E2 = e^(z/2), Q = (dt/2) phi_1(z/2), f1 = dt (phi_1 - 3 phi_2 + 4 phi_3)(z),
+    f2 = dt (phi_2 - 2 phi_3)(z), f3 = dt (4 phi_3 - phi_2)(z), with z = dt (q_j^2 - q_j^4)."""
+    j = signed_modes(Nx)
+    q = 2.0 * math.pi * j / L
+    keep = (np.abs(j) <= Nx // 3) & (np.abs(j) != Nx // 2)
+    z = dt * (q ** 2 - q ** 4)
+    a1, a2, a3 = etd_phi(z)
+    h1, _, _ = etd_phi(z / 2.0)
+    return dict(q=q, keep=keep, E=np.exp(z), E2=np.exp(z / 2.0), Q=0.5 * dt * h1,
+                f1=dt * (a1 - 3.0 * a2 + 4.0 * a3), f2=dt * (a2 - 2.0 * a3),
+                f3=dt * (4.0 * a3 - a2))
+
+
+def dns_nonlinear(vh: np.ndarray, q: np.ndarray, keep: np.ndarray, Ex: np.ndarray) -> np.ndarray:
+    """-(u u_x) = -(u^2 / 2)_x in spectral space, product on the grid, truncated to the 2/3 band.
+    vh: coefficients over the signed modes with u(x_m) = (1/Nx) sum_j vh_j e^(i q_j x_m)."""
+    Nx = vh.shape[0]
+    u = np.real(Ex @ vh) / Nx
+    W = Ex.conj().T @ (u * u)
+    return np.where(keep, -0.5j * q * W, 0.0)
+
+
+def dns(L: float, Nx: int, dt: float, nsteps: int, u0: np.ndarray, save_every: int = 1,
+        symmetric: bool = False):
+    """ETDRK4 integration of the KSE from the grid field u0 [Nx]; returns (t [nsave],
+    u [nsave, Nx]) every save_every steps, t = 0 first.  symmetric: the state is kept in the
+    centre-symmetric subspace u(-x) = -u(x) (purely imaginary coefficients), projected
+    initially and after every step."""
+    c = dns_coefficients(L, Nx, dt)
+    Ex = dft_matrix(Nx)
+    q, keep = c["q"], c["keep"]
+    sym = (lambda v: 1j * v.imag) if symmetric else (lambda v: v)  # noqa: E731
+    N = lambda v: dns_nonlinear(v, q, keep, Ex)  # noqa: E731
+    vh = sym(np.where(keep, Ex.conj().T @ np.asarray(u0, dtype=np.float64), 0.0))
+    ts, us = [0.0], [np.real(Ex @ vh) / Nx]
+    for n in range(1, nsteps + 1):
+        Nv = N(vh)
+        a = c["E2"] * vh + c["Q"] * Nv
+        Na = N(a)
+        b = c["E2"] * vh + c["Q"] * Na
+        Nb = N(b)
+        cc = c["E2"] * a + c["Q"] * (2.0 * Nb - Nv)
+        Nc = N(cc)
+        vh = sym(c["E"] * vh + c["f1"] * Nv + 2.0 * c["f2"] * (Na + Nb) + c["f3"] * Nc)
+        if n % save_every == 0:
+            ts.append(n * dt)
+            us.append(np.real(Ex @ vh) / Nx)
+    return np.asarray(ts), np.asarray(us)
+
+
+def dns_rk4(L: float, Nx: int, dt: float, nsteps: int, u0: np.ndarray) -> np.ndarray:
+    """Classical RK4 on the same dealiased Fourier system (v' = (q^2 - q^4) v + N(v)); an
+    independent integrator for pinning ``dns`` (stable only for dt below ~2.8 / max q^4)."""
+    j = signed_modes(Nx)
+    q = 2.0 * math.pi * j / L
+    keep = (np.abs(j) <= Nx // 3) & (np.abs(j) != Nx // 2)
+    lam = q ** 2 - q ** 4
+    Ex = dft_matrix(Nx)
+    f = lambda v: np.where(keep, lam * v, 0.0) + dns_nonlinear(v, q, keep, Ex)  # noqa: E731
+    vh = np.where(keep, Ex.conj().T @ np.asarray(u0, dtype=np.float64), 0.0)
+    for _ in range(nsteps):
+        k1 = f(vh)
+        k2 = f(vh + 0.5 * dt * k1)
+        k3 = f(vh + 0.5 * dt * k2)
+        k4 = f(vh + dt * k3)
+        vh = vh + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    return np.real(Ex @ vh) / Nx
