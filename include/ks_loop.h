@@ -339,6 +339,44 @@ KS_API int ks_autotune(ks_loop_t h);
  * `stream`.  KS_ERR_ARG for another precision, iters < 1 or a null tflops. */
 KS_API int ks_probe_peak(int precision, int iters, double* tflops, void* stream);
 
+/* Time integration of the KSE u_t = -u u_x - u_xx - u_xxxx on [0, L), periodic, the chaotic run
+ * from which the paper takes its initial loops (Sec. 4.3).  Fourier pseudo-spectral in x with Nx
+ * points and the product -(u^2/2)_x truncated to |j| <= Nx/3 (the 2/3 rule of Sec. 4.2; the
+ * Nyquist mode is zero), fourth-order exponential time differencing in t (ETDRK4 of Cox &
+ * Matthews, J. Comput. Phys. 176 (2002); the paper names no integrator).  `batch` independent
+ * trajectories share L, Nx and dt.
+ *   u0      : in,  [batch][nx] doubles, the initial grid fields (projected onto |j| <= Nx/3)
+ *   nsteps  : steps of size dt (>= 0); save_every (>= 1): the state is saved at steps
+ *             0, save_every, 2 save_every, ..., so nsave = nsteps / save_every + 1 instants
+ *   symmetric: nonzero keeps the run in the centre-symmetric subspace u(-x) = -u(x) (Sec. 4.4):
+ *             the real parts of the coefficients are zeroed initially and after every step
+ *   u_saved : out, [batch][nsave][nx] doubles, the grid fields at the saved instants, nullable
+ *   norms   : out, [batch][nsave] doubles, ||u||(t) = (int_0^L u^2 dx)^(1/2) at the saved
+ *             instants (Sec. 4.3), nullable
+ *   u_end   : out, [batch][nx] doubles, the field after the last step, nullable
+ * Pointers follow the conventions above (device or host).  Errors: KS_ERR_ARG for L or dt not
+ * finite and > 0, nx not a power of two in [8, 1024], batch < 1, nsteps < 0, save_every < 1 or a
+ * null u0; KS_ERR_OOM when a host buffer cannot be staged.  The run is one launch on `stream`
+ * (one block per two to eight trajectories); with device buffers only it is stream ordered. */
+KS_API int ks_dns(double L, int nx, int batch, double dt, long long nsteps, int save_every,
+                  int symmetric, const double* u0, double* u_saved, double* norms, double* u_end,
+                  void* stream);
+
+/* Initial loops from segments of one saved trajectory (Sec. 4.3): loop l is the field at the Ns_l
+ * instants t_a + T_l n / Ns_l (n = 0..Ns_l - 1), t_a the time of saved sample a_idx[l], by linear
+ * interpolation in time between saved samples.  The temporal low-pass of Sec. 4.3 is the
+ * projection onto the 2/3 band that every loop input receives (ks_set_state, ks_descend).
+ *   nx, nsave: the trajectory's [nsave][nx] layout in `us` (device or host doubles)
+ *   dts      : time between saved samples, > 0
+ *   a_idx, T, ns: HOST arrays [nloops]: first sample, period (> 0) and Ns (>= 1) of each loop
+ *   out      : out, ragged-packed loops [sum_l Ns_l * nx] doubles, layout [n][m] (device or host)
+ * KS_ERR_ARG for a null pointer, nsave < 2, dts not finite and > 0, nloops < 0, or a segment
+ * whose last instant needs a sample past the last saved one (the interpolation reads the samples
+ * on both sides of every instant). */
+KS_API int ks_dns_segments(int nx, long long nsave, double dts, const double* us, int nloops,
+                           const int* a_idx, const double* T, const int* ns, double* out,
+                           void* stream);
+
 /* Message for the last non-zero return on the calling thread ("" if none). */
 KS_API const char* ks_last_error(void);
 

@@ -547,3 +547,19 @@ def dns_rk4(L: float, Nx: int, dt: float, nsteps: int, u0: np.ndarray) -> np.nda
         k4 = f(vh + dt * k3)
         vh = vh + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
     return np.real(Ex @ vh) / Nx
+
+
+def norm_series(us: np.ndarray, L: float) -> np.ndarray:
+    """||u||(t) = (int_0^L u^2 dx)^(1/2) of each saved field u[i, m] (Sec. 4.3), the grid mean
+    of u^2 times L (exact for the dealiased fields of the run: u^2 has no aliased modes)."""
+    us = np.asarray(us, dtype=np.float64)
+    return np.sqrt(L * np.mean(us * us, axis=-1))
+
+
+def segment_loop(ts: np.ndarray, us: np.ndarray, a: int, T: float, Ns: int) -> np.ndarray:
+    """The field of a recurrence loop (Sec. 4.3) before its low-pass: the saved run u(x_m, t_i)
+    at the Ns instants t_a + T n / Ns, n = 0..Ns-1, by linear interpolation in time between the
+    saved instants (np.interp per grid point).  Returns [Ns, Nx]."""
+    us = np.asarray(us, dtype=np.float64)
+    s_t = ts[a] + T * np.arange(Ns) / Ns
+    return np.stack([np.interp(s_t, ts, us[:, m]) for m in range(us.shape[1])], axis=1)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libks_loop.so")
-SOURCES = ["ks_loop.cu", "ks_noalloc.cu", "ks_probe.cu"]
+SOURCES = ["ks_loop.cu", "ks_noalloc.cu", "ks_probe.cu", "ks_dns.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

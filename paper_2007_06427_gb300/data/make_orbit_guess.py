@@ -2,10 +2,11 @@
 centre-symmetric) taken from a close recurrence of a chaotic KS run (Sec. 4.3), stored as its
 band coefficients so that every machine starts from the same loop.
 
-A chaotic run is not reproducible across machines bit for bit (different FFT rounding grows
-exponentially along the trajectory), which is why the loop is stored rather than recomputed.
-The run and the extraction are those of ``paper_2007_06427_gb300.guesses`` with the arguments
-below; the recurrence is chosen by its start time in the run.
+A chaotic run is not reproducible bit for bit on other hardware or with other transforms
+(different rounding grows exponentially along the trajectory), which is why the loop is stored
+rather than recomputed.  The run and the extraction are those of ``paper_2007_06427_gb300.guesses``
+(on the GPU) with the arguments below; the recurrence is chosen by its start time in the run.
+Needs a CUDA device.
 
     python -m paper_2007_06427_gb300.data.make_orbit_guess [t0]
 """
@@ -24,10 +25,10 @@ RUN = {"t_end": 6000.0, "seed": 2, "symmetric": True}
 EXTRACT = {"T_range": [20.0, 32.0], "tol": 0.01, "t_min": 200.0, "max_loops": 8}
 
 
-def main(t0: float = 5225.5) -> str:
+def main(t0: float = 1515.0) -> str:
     from paper_2007_06427_gb300.guesses import chaotic_run, recurrence_loops
-    ts, us = chaotic_run(L, NX, RUN["t_end"], seed=RUN["seed"], symmetric=RUN["symmetric"])
-    gs = recurrence_loops(ts, us, L, NS, T_range=tuple(EXTRACT["T_range"]), tol=EXTRACT["tol"],
+    run = chaotic_run(L, NX, RUN["t_end"], seed=RUN["seed"], symmetric=RUN["symmetric"])
+    gs = recurrence_loops(run, L, NS, T_range=tuple(EXTRACT["T_range"]), tol=EXTRACT["tol"],
                           t_min=EXTRACT["t_min"], max_loops=EXTRACT["max_loops"])
     g = min(gs, key=lambda g: abs(g.t0 - t0))
     # c_jk of u(x_m, s_n) = sum_{j, k} c_jk exp(2 pi i (m j / Nx + n k / Ns)), j = 1..Kx, k = 0..Ks;

@@ -4,75 +4,60 @@ The paper extracts its initial guesses from a chaotic solution u(x, t) of the KS
 subsequent maxima of the spatial L2 norm ||u||(t) = (int_0^L u^2 dx)^(1/2) at which
 ||u||(t + T) ~ ||u||(t), uses the segment between them as the field of the loop and its length
 as the period, and removes the high temporal frequencies with a Fourier filter so that the
-loop closes smoothly.  This module provides both halves:
+loop closes smoothly.  Both halves run on the GPU through the C ABI:
 
-* ``ks_dns``: pseudo-spectral time integration of u_t = -u u_x - u_xx - u_xxxx on [0, L)
-  (periodic), 2/3-rule dealiasing, fourth-order exponential time differencing (ETDRK4 of Cox &
-  Matthews, J. Comput. Phys. 176, 2002, with the phi-functions evaluated by the contour-integral
-  average of Kassam & Trefethen, SIAM J. Sci. Comput. 26, 2005);
-* ``recurrence_loops``: the recurrence search, segment extraction, temporal low-pass onto the
-  descent's band and resampling to Ns points in s.
+* ``ks_dns``: the run itself (``ks_dns`` in the library: Fourier pseudo-spectral in x, 2/3-rule
+  dealiasing, fourth-order exponential time differencing), which also returns ||u||(t) at every
+  saved instant;
+* ``recurrence_loops``: the recurrence search over the norm series (``recurrence_pairs``, index
+  bookkeeping on the host), the segment cut to Ns instants by linear interpolation in time
+  (``ks_dns_segments``) and the temporal low-pass, which is the projection onto the descent's
+  2/3 band (|k| <= Ns/3, which also removes the jump at the closure, and |j| <= Nx/3) that a
+  loop handle applies to every input (``ks_set_state`` / ``ks_get_state``).
 
 The paper takes its initial loops from a chaotic run within the subspace of centre-symmetric
 fields, u(-x) = -u(x) (Sec. 4.4); ``symmetric=True`` keeps the run there (an odd real field
 has purely imaginary Fourier coefficients, and the KSE preserves that, so the projection after
 each step only removes rounding).  Every later step of the extraction is linear and acts the
 same at x and -x, so the loops it returns are centre-symmetric as well.
-
-Host-side preprocessing (NumPy); the loops it returns are inputs for the GPU descent.
 """
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import List, Optional
+from typing import List, NamedTuple, Optional
 
 import numpy as np
 
+from . import ks_loop as K
 
-def ks_dns(L: float, nx: int, dt: float, nsteps: int, u0: np.ndarray, save_every: int = 1,
-           symmetric: bool = False):
-    """Integrate the KSE; returns (t [nsave], u [nsave, nx]) sampled every save_every steps.
 
-    symmetric: stay in the centre-symmetric subspace (the real parts of the coefficients are
-    zeroed initially and after every step)."""
-    k = np.fft.rfftfreq(nx, d=1.0 / nx)                 # 0 .. nx/2
-    q = 2.0 * np.pi * k / L
-    lin = q ** 2 - q ** 4                               # symbol of -u_xx - u_xxxx
-    keep = k <= nx // 3                                 # 2/3 rule
-    g = -0.5j * q                                       # N(u) = -(u^2/2)_x
-    E = np.exp(dt * lin)
-    E2 = np.exp(dt * lin / 2.0)
-    # phi-function weights by a contour average around each dt*lin (M points on a circle)
-    M = 32
-    r = np.exp(1j * np.pi * (np.arange(1, M + 1) - 0.5) / M)
-    LR = dt * lin[:, None] + r[None, :]
-    Q = dt * np.real(np.mean((np.exp(LR / 2.0) - 1.0) / LR, axis=1))
-    f1 = dt * np.real(np.mean((-4.0 - LR + np.exp(LR) * (4.0 - 3.0 * LR + LR ** 2)) / LR ** 3, axis=1))
-    f2 = dt * np.real(np.mean((2.0 + LR + np.exp(LR) * (-2.0 + LR)) / LR ** 3, axis=1))
-    f3 = dt * np.real(np.mean((-4.0 - 3.0 * LR - LR ** 2 + np.exp(LR) * (4.0 - LR)) / LR ** 3, axis=1))
+class Run(NamedTuple):
+    ts: np.ndarray    # [nsave] saved instants, t = 0 first
+    us: "object"      # torch tensor on the device, [nsave, nx] (or [batch, nsave, nx])
+    norms: np.ndarray  # ||u||(t) at the saved instants, [nsave] (or [batch, nsave])
 
-    def N(vh):
-        u = np.fft.irfft(vh, n=nx)
-        return g * np.where(keep, np.fft.rfft(u * u), 0.0)
 
-    def sym(vh):
-        return 1j * vh.imag if symmetric else vh
-
-    vh = sym(np.where(keep, np.fft.rfft(np.asarray(u0, dtype=np.float64)), 0.0))
-    ts, us = [0.0], [np.fft.irfft(vh, n=nx)]
-    for n in range(1, nsteps + 1):
-        Nv = N(vh)
-        a = E2 * vh + Q * Nv
-        Na = N(a)
-        b = E2 * vh + Q * Na
-        Nb = N(b)
-        c = E2 * a + Q * (2.0 * Nb - Nv)
-        Nc = N(c)
-        vh = sym(E * vh + Nv * f1 + 2.0 * (Na + Nb) * f2 + Nc * f3)
-        if n % save_every == 0:
-            ts.append(n * dt)
-            us.append(np.fft.irfft(vh, n=nx))
-    return np.asarray(ts), np.asarray(us)
+def ks_dns(L: float, nx: int, dt: float, nsteps: int, u0, save_every: int = 1,
+           symmetric: bool = False, device: str = "cuda") -> Run:
+    """Integrate the KSE on the GPU from the grid field(s) u0 ([nx] or [batch, nx]); the state is
+    saved every save_every steps (t = 0 first).  symmetric: stay in the centre-symmetric
+    subspace (the real parts of the coefficients are zeroed initially and after every step)."""
+    import torch
+    u0 = torch.as_tensor(np.asarray(u0, dtype=np.float64)).to(device)
+    single = u0.dim() == 1
+    u0 = u0.reshape(-1, nx).contiguous()
+    batch = u0.shape[0]
+    nsave = nsteps // save_every + 1
+    us = torch.empty(batch, nsave, nx, dtype=torch.float64, device=device)
+    norms = torch.empty(batch, nsave, dtype=torch.float64, device=device)
+    with torch.cuda.device(u0.device):
+        K.ks_dns(L, nx, batch, dt, nsteps, save_every, symmetric, u0, us, norms,
+                 stream=torch.cuda.current_stream())
+    ts = dt * save_every * np.arange(nsave, dtype=np.float64)
+    nrm = norms.cpu().numpy()
+    if single:
+        return Run(ts, us[0], nrm[0])
+    return Run(ts, us, nrm)
 
 
 @dataclass
@@ -83,23 +68,12 @@ class Guess:
     mismatch: float    # | ||u||(t0 + T) - ||u||(t0) | / ||u||(t0)
 
 
-def norm_series(us: np.ndarray, L: float) -> np.ndarray:
-    """||u||(t) = (int_0^L u^2 dx)^(1/2) of each saved field (Sec. 4.3)."""
-    return np.sqrt(L * np.mean(us * us, axis=1))
-
-
-def recurrence_loops(ts: np.ndarray, us: np.ndarray, L: float, ns: int,
-                     T_range=(10.0, 100.0), tol: float = 0.01, t_min: float = 0.0,
-                     max_loops: Optional[int] = None) -> List[Guess]:
-    """Loops from subsequent maxima of ||u||(t) with ||u||(t + T) ~ ||u||(t) (Sec. 4.3).
-
-    For every local maximum t_a (after t_min) and every later maximum t_b with T = t_b - t_a in
-    T_range and a relative mismatch of the norms below tol, the segment u(., [t_a, t_b)) is
-    interpolated to Ns equispaced instants s = n/Ns, Fourier transformed in s, truncated to
-    |k| <= Ns/3 (the descent's 2/3 band, which also removes the jump at the closure) and
-    transformed back.  Sorted by mismatch, best first."""
-    nx = us.shape[1]
-    nrm = norm_series(us, L)
+def recurrence_pairs(ts: np.ndarray, norms: np.ndarray, T_range=(10.0, 100.0), tol: float = 0.01,
+                     t_min: float = 0.0):
+    """Close recurrences of a norm series (Sec. 4.3): every pair of local maxima t_a < t_b of
+    ||u||(t) (t_a >= t_min) with T = t_b - t_a in T_range and a relative mismatch
+    | ||u||(t_b) - ||u||(t_a) | / ||u||(t_a) below tol, as (mismatch, a, b) sorted best first."""
+    nrm = np.asarray(norms)
     idx = [i for i in range(1, len(nrm) - 1)
            if nrm[i] > nrm[i - 1] and nrm[i] >= nrm[i + 1] and ts[i] >= t_min]
     cands = []
@@ -112,34 +86,48 @@ def recurrence_loops(ts: np.ndarray, us: np.ndarray, L: float, ns: int,
                 break
             mis = abs(nrm[b] - nrm[a]) / nrm[a]
             if mis < tol:
-                cands.append((mis, a, b))
+                cands.append((float(mis), a, b))
     cands.sort()
-    out: List[Guess] = []
-    ks = ns // 3
-    for mis, a, b in cands:
-        T = ts[b] - ts[a]
-        s_t = ts[a] + T * np.arange(ns) / ns              # sample instants of the loop
-        seg_t = ts[a:b + 1]
-        seg = us[a:b + 1]
-        loop = np.empty((ns, nx))
-        for m in range(nx):                               # linear interpolation in time
-            loop[:, m] = np.interp(s_t, seg_t, seg[:, m])
-        spec = np.fft.fft(loop, axis=0)
-        kk = np.fft.fftfreq(ns, d=1.0 / ns)
-        spec[np.abs(kk) > ks, :] = 0.0
-        loop = np.real(np.fft.ifft(spec, axis=0))
-        # x band as well (the run is dealiased; this only removes the Nyquist mode)
-        sx = np.fft.rfft(loop, axis=1)
-        sx[:, nx // 3 + 1:] = 0.0
-        loop = np.fft.irfft(sx, n=nx, axis=1)
-        out.append(Guess(u=loop, T=float(T), t0=float(ts[a]), mismatch=float(mis)))
-        if max_loops and len(out) >= max_loops:
-            break
-    return out
+    return cands
+
+
+def recurrence_loops(run: Run, L: float, ns: int, T_range=(10.0, 100.0), tol: float = 0.01,
+                     t_min: float = 0.0, max_loops: Optional[int] = None) -> List[Guess]:
+    """Loops from the close recurrences of one saved run (``recurrence_pairs``): the segment
+    u(., [t_a, t_b)) at Ns equispaced instants s = n/Ns (linear interpolation in time, on the
+    GPU), projected onto the descent's 2/3 band |j| <= Nx/3, |k| <= Ns/3 (the temporal low-pass
+    of Sec. 4.3), returned on the grid.  Sorted by mismatch, best first."""
+    import torch
+    ts, us, nrm = run
+    cands = recurrence_pairs(ts, nrm, T_range, tol, t_min)
+    if max_loops:
+        cands = cands[:max_loops]
+    if not cands:
+        return []
+    nsave, nx = us.shape
+    dts = float(ts[1] - ts[0])
+    a_idx = np.array([a for _, a, _ in cands], dtype=np.int32)
+    Ts = np.array([ts[b] - ts[a] for _, a, b in cands], dtype=np.float64)
+    B = len(cands)
+    dev = us.device
+    raw = torch.empty(B * ns * nx, dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream()
+        K.ks_dns_segments(nx, nsave, dts, us.contiguous(), a_idx, Ts, [ns] * B, raw, stream=stream)
+        out = torch.empty_like(raw)
+        Tt = torch.tensor(Ts, dtype=torch.float64, device=dev)
+        with K.KSLoop(L, nx, [ns] * B, K.KS_FP64) as h:
+            K.ks_set_state(h.handle, raw, Tt, stream=stream)
+            K.ks_get_state(h.handle, out, stream=stream)
+        torch.cuda.synchronize(dev)
+    loops = out.cpu().numpy().reshape(B, ns, nx)
+    return [Guess(u=loops[i], T=float(Ts[i]), t0=float(ts[a]), mismatch=float(mis))
+            for i, (mis, a, _) in enumerate(cands)]
 
 
 def chaotic_run(L: float, nx: int, t_end: float, dt: float = 0.25, seed: int = 0,
-                save_dt: float = 0.5, amplitude: float = 0.1, symmetric: bool = False):
+                save_dt: float = 0.5, amplitude: float = 0.1, symmetric: bool = False,
+                device: str = "cuda") -> Run:
     """A chaotic KS trajectory from a small seeded perturbation (transient included); with
     symmetric, in the centre-symmetric subspace."""
     rng = np.random.default_rng(seed)
@@ -148,4 +136,5 @@ def chaotic_run(L: float, nx: int, t_end: float, dt: float = 0.25, seed: int = 0
                       + np.sin(4 * np.pi * x / L) * rng.standard_normal()
                       + 0.3 * rng.standard_normal(nx))
     save_every = max(1, int(round(save_dt / dt)))
-    return ks_dns(L, nx, dt, int(round(t_end / dt)), u0, save_every, symmetric=symmetric)
+    return ks_dns(L, nx, dt, int(round(t_end / dt)), u0, save_every, symmetric=symmetric,
+                  device=device)

@@ -26,7 +26,7 @@ _EXPORTS = ("ks_loop_create", "ks_destroy", "ks_residual", "ks_adjoint_grad", "k
             "ks_set_state", "ks_step", "ks_get_state", "ks_last_error", "ks_version",
             "ks_config_sizeof", "ks_profile", "ks_profile_read", "ks_set_option", "ks_get_option",
             "ks_residual_noalloc", "ks_get_history", "ks_autotune", "ks_band_size",
-            "ks_get_band", "ks_set_band", "ks_probe_peak")
+            "ks_get_band", "ks_set_band", "ks_probe_peak", "ks_dns", "ks_dns_segments")
 
 
 class KsError(RuntimeError):
@@ -84,10 +84,13 @@ def load_library(path: str = LIB_PATH):
     lib.ks_set_band.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ks_profile_read.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     lib.ks_probe_peak.argtypes = [i32, i32, vp, vp]
+    lib.ks_dns.argtypes = [dp, i32, i32, dp, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.ks_dns_segments.argtypes = [i32, i64, dp, vp, i32, vp, vp, vp, vp, vp]
     for f in ("ks_loop_create", "ks_destroy", "ks_residual", "ks_adjoint_grad", "ks_descend",
               "ks_set_state", "ks_step", "ks_get_state", "ks_profile", "ks_profile_read",
               "ks_set_option", "ks_get_option", "ks_residual_noalloc", "ks_get_history",
-              "ks_autotune", "ks_get_band", "ks_set_band", "ks_probe_peak"):
+              "ks_autotune", "ks_get_band", "ks_set_band", "ks_probe_peak", "ks_dns",
+              "ks_dns_segments"):
         getattr(lib, f).restype = i32
     lib.ks_last_error.restype = ctypes.c_char_p
     lib.ks_version.restype = ctypes.c_char_p
@@ -241,6 +244,21 @@ def ks_probe_peak(precision: int, iters: int = 0, stream=None) -> float:
     v = ctypes.c_double()
     _check(load_library().ks_probe_peak(int(precision), int(iters), ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+def ks_dns(L: float, nx: int, batch: int, dt: float, nsteps: int, save_every: int, symmetric: bool,
+           u0, u_saved=None, norms=None, u_end=None, stream=None) -> None:
+    _check(load_library().ks_dns(L, nx, batch, dt, nsteps, save_every, int(bool(symmetric)),
+                                 _ptr(u0), _ptr(u_saved), _ptr(norms), _ptr(u_end), _stream(stream)))
+
+
+def ks_dns_segments(nx: int, nsave: int, dts: float, us, a_idx, T, ns, out, stream=None) -> None:
+    """a_idx, T and ns are host arrays (int32, float64, int32), one entry per loop."""
+    a_idx = np.ascontiguousarray(a_idx, dtype=np.int32)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    _check(load_library().ks_dns_segments(nx, nsave, dts, _ptr(us), len(a_idx), _ptr(a_idx), _ptr(T),
+                                          _ptr(ns), _ptr(out), _stream(stream)))
 
 
 def ks_profile(h, enable: bool) -> None:

@@ -153,8 +153,8 @@ def search(L: float = 39.0, nx: int = 64, ns: int = 64, t_end: float = 3000.0,
     converge in the batched descent continue alone with the extrapolated mixed descent
     (``refine``)."""
     t0 = time.perf_counter()
-    ts, us = chaotic_run(L, nx, t_end, seed=seed, symmetric=symmetric)
-    gs = recurrence_loops(ts, us, L, ns, T_range=T_range, tol=rec_tol, t_min=t_min,
+    run = chaotic_run(L, nx, t_end, seed=seed, symmetric=symmetric)
+    gs = recurrence_loops(run, L, ns, T_range=T_range, tol=rec_tol, t_min=t_min,
                           max_loops=guesses)
     t1 = time.perf_counter()
     states: list = []

@@ -84,3 +84,44 @@ def test_probe_rejects_bad_arguments_and_needs_a_device(lib):
     if not torch.cuda.is_available():
         assert lib.ks_probe_peak(K.KS_FP64, 10, ctypes.byref(v), None) == K.KS_ERR_CUDA
         assert v.value == 0.0
+
+
+@pytest.mark.parametrize("kw", [
+    dict(L=0.0), dict(dt=-0.25), dict(nx=48), dict(nx=2048), dict(batch=0), dict(nsteps=-1),
+    dict(save_every=0), dict(u0=None),
+])
+def test_dns_rejects_bad_arguments(lib, kw):
+    import numpy as np
+    a = dict(L=22.0, nx=32, batch=1, dt=0.25, nsteps=4, save_every=1, symmetric=False,
+             u0=np.zeros(32))
+    a.update(kw)
+    with pytest.raises(K.KsError) as e:
+        K.ks_dns(**a)
+    assert e.value.code == K.KS_ERR_ARG
+
+
+def test_dns_segments_rejects_bad_arguments(lib):
+    import numpy as np
+    us = np.zeros((10, 8))
+    out = np.zeros(8 * 8)
+    good = dict(nx=8, nsave=10, dts=0.5, us=us, a_idx=[0], T=[3.0], ns=[8], out=out)
+    for kw in (dict(nsave=1), dict(dts=0.0), dict(T=[-1.0]), dict(ns=[0]), dict(a_idx=[-1]),
+               dict(T=[5.5]), dict(us=None)):
+        a = dict(good)
+        a.update(kw)
+        with pytest.raises(K.KsError) as e:
+            K.ks_dns_segments(**a)
+        assert e.value.code == K.KS_ERR_ARG, kw
+
+
+def test_dns_needs_a_device(lib):
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(K.KsError) as e:
+        K.ks_dns(22.0, 32, 1, 0.25, 4, 1, False, np.zeros(32))
+    assert e.value.code == K.KS_ERR_CUDA
+    with pytest.raises(K.KsError) as e:       # the last instant 5 * 7/8 needs samples 8 and 9
+        K.ks_dns_segments(8, 10, 0.5, np.zeros((10, 8)), [0], [5.0], [8], np.zeros(64))
+    assert e.value.code == K.KS_ERR_CUDA

@@ -13,8 +13,8 @@ pytestmark = pytest.mark.gpu
 
 def test_descent_from_recurrence_guess():
     L, nx, ns = 22.0, 32, 32
-    ts, us = chaotic_run(L, nx, 2000.0, seed=0)
-    g = recurrence_loops(ts, us, L, ns, T_range=(10.0, 80.0), tol=0.005, t_min=200.0,
+    run = chaotic_run(L, nx, 2000.0, seed=0)
+    g = recurrence_loops(run, L, ns, T_range=(10.0, 80.0), tol=0.005, t_min=200.0,
                          max_loops=1)[0]
     u = torch.tensor(g.u.ravel(), device="cuda")
     T = torch.tensor([g.T], dtype=torch.float64, device="cuda")
@@ -33,8 +33,8 @@ def test_descent_from_centre_symmetric_guess_at_L39():
     centre-symmetric chaotic run, descended with the "symmetry" knob: J falls monotonically
     and the band stays exactly invariant."""
     L, nx, ns = 39.0, 64, 64
-    ts, us = chaotic_run(L, nx, 1500.0, seed=2, symmetric=True)
-    g = recurrence_loops(ts, us, L, ns, T_range=(10.0, 120.0), tol=0.01, t_min=200.0,
+    run = chaotic_run(L, nx, 1500.0, seed=2, symmetric=True)
+    g = recurrence_loops(run, L, ns, T_range=(10.0, 120.0), tol=0.01, t_min=200.0,
                          max_loops=1)[0]
     u = torch.tensor(g.u.ravel(), device="cuda")
     T = torch.tensor([g.T], dtype=torch.float64, device="cuda")

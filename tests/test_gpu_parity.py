@@ -301,8 +301,8 @@ def test_mixed_descent_starts_below_float_floor_in_double():
     sqrt(J) to the float floor; it descends in double from the first chunk."""
     from paper_2007_06427_gb300.guesses import chaotic_run
     L, nx, ns = 22.0, 32, 32
-    _, us = chaotic_run(L, nx, 1500.0, seed=0, symmetric=True)
-    loop = np.repeat(us[-1][None, :], ns, axis=0)
+    us = chaotic_run(L, nx, 1500.0, seed=0, symmetric=True).us
+    loop = np.repeat(us[-1].cpu().numpy()[None, :], ns, axis=0)
     u = torch.tensor(loop.ravel(), device="cuda")
     T = torch.tensor([11.0], dtype=torch.float64, device="cuda")
     J0 = torch.empty(1, dtype=torch.float64, device="cuda")

@@ -8,8 +8,8 @@ guesses of Sec. 4.3, against what the mathematics fixes:
   powers, with the product negligible);
 * fourth-order convergence under step halving, and agreement with classical RK4 at a step far
   inside RK4's stability limit (an independent integrator of the same semi-discrete system);
-* the centre-symmetric subspace u(-x) = -u(x) kept exactly;
-and the host NumPy integrator of the package against it.
+* the centre-symmetric subspace u(-x) = -u(x) kept exactly.
+The GPU integrator of the package is checked against it in ``test_gpu_dns.py``.
 """
 import math
 
@@ -84,14 +84,3 @@ def test_centre_symmetric_subspace_is_kept_exactly():
     assert np.abs(us + mirror).max() < 1e-13 * np.abs(us).max()
     assert np.abs(us[-1]).max() > 0.1                    # a nontrivial state
 
-
-def test_host_integrator_of_the_package_matches_the_oracle():
-    """guesses.ks_dns (NumPy FFTs, contour-integral phi-functions) against the oracle over
-    t = 50 at L = 22, Nx = 64 (a chaotic run; the difference grows with time, so the horizon is
-    short)."""
-    from paper_2007_06427_gb300.guesses import ks_dns
-    L, nx = 22.0, 64
-    u0 = field(L, nx)
-    _, a = ks_dns(L, nx, 0.25, 200, u0, save_every=50)
-    _, b = ko.dns(L, nx, 0.25, 200, u0, save_every=50)
-    assert np.abs(a - b).max() < 1e-11 * np.abs(b).max()
