@@ -111,6 +111,12 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     const int cid = blockIdx.x / C;
     const int ncl = gridDim.x / C;
     const int tid = threadIdx.x, nt = blockDim.x;
+    // A block of 4k + 1 warps (the double kernel, see cluster_block) carries one extra warp for
+    // the scalars of phase B'; the element loops of a step run on the other 4k warps (ntw
+    // threads) and the extra warp starts them past their end (wtid).  The transforms of such a
+    // plan have at most ntw butterflies a pass, so the extra warp gets none there either.
+    const int ntw = nt - (nt % 64);
+    const int wtid = (tid < ntw) ? tid : (1 << 30);
     const int nx = d.nx, lgnx = d.lgnx, kx = d.kx, nkx = d.nkx, B = d.B;
     const int rmax = cp.rmax;
     constexpr bool xi = XI;
@@ -131,8 +137,11 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     cpx<RA>* Mloc_a = reinterpret_cast<cpx<RA>*>(Mloc);
     cpx<RA>* scr_a = reinterpret_cast<cpx<RA>*>(scr);
     cpx<RA>* tws_a = kSame ? reinterpret_cast<cpx<RA>*>(tws) : reinterpret_cast<cpx<RA>*>(smem + cp.off_tw_a);
-    const R h = (R)d.hx;
-    const RA h_a = (RA)d.hx;
+    // 1/(2 Nx) of the row split; per loop it is multiplied by 1/Ns, the normalisation of the
+    // forward s-transform that the column phases would otherwise apply (both powers of two, so
+    // the product is exact and scaling before the transform gives the same bits as after it)
+    const R h0 = (R)d.hx;
+    const RA h0_a = (RA)d.hx;
     // the per-x-mode tables, read in every phase, live in shared memory
     R* const s_qv = reinterpret_cast<R*>(smem + cp.off_tab);
     R* const s_lin = s_qv + nkx;
@@ -169,6 +178,8 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         const int ks = one ? cp.nsmax / 3 : p.ks[b];
         const int nk = 2 * ks + 1;
         const R ins = p.insv[b];
+        const R h = h0 * ins;
+        const RA h_a = h0_a * (RA)ins;
         const size_t bo = one ? 0 : (size_t)p.boff[b];
         const long long moff_b = one ? 0 : p.moff[b], goff_b = one ? 0 : p.goff[b];
         double T = p.T[(size_t)par0 * B + b];
@@ -218,7 +229,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)],
         // two rows per store (rows per rank and rmax are even, so a pair has one owner)
         auto push_columns = [&](const auto* X, auto* RinT) {
-            for (int i = tid; i < (ncol << lg) >> 1; i += nt) {
+            for (int i = wtid; i < (ncol << lg) >> 1; i += ntw) {
                 const int q = (2 * i) >> lg, n = (2 * i) & (ns - 1);
                 const int owner = n / rpr;
                 auto* dst = cl.map_shared_rank(RinT, owner);
@@ -230,7 +241,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         auto push_pairs = [&](const auto* Cp, auto* RinT, bool imag) {
             typedef typename std::remove_pointer<decltype(RinT)>::type CT;
             typedef decltype(CT{}.x) X;
-            for (int i = tid; i < (ncol << lg) >> 2; i += nt) {
+            for (int i = wtid; i < (ncol << lg) >> 2; i += ntw) {
                 const int pp = (2 * i) >> lg, n = (2 * i) & (ns - 1);
                 const int owner = n / rpr;
                 auto* dst = cl.map_shared_rank(RinT, owner) + (n - owner * rpr);
@@ -250,7 +261,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         if (!use_M) {
             // no valid mixed values: prime them from the band (s-inverse of the owned columns)
             if (xi) {
-                for (int i = tid; i < (ncol >> 1) << lg; i += nt) {
+                for (int i = wtid; i < (ncol >> 1) << lg; i += ntw) {
                     const int pp = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
                     Mloc[i] = (k >= -ks && k <= ks)
@@ -261,7 +272,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 col_fft_inplace(Mloc, scr, lg, ncol >> 1, +1, tws);
                 push_pairs(Mloc, Rin, true);
             } else {
-                for (int i = tid; i < ncol << lg; i += nt) {
+                for (int i = wtid; i < ncol << lg; i += ntw) {
                     const int q = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
                     Mloc[i] = (k >= -ks && k <= ks) ? uhl[q * nk + k + ks] : mk<R>(0, 0);
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const int n0 = row0 + t0;
                 cpx<R>* A = scr;
                 cpx<R>* Bf = scr + (size_t)nr * nx;
-                for (int i = tid; i < nr * nx; i += nt) {
+                for (int i = wtid; i < nr * nx; i += ntw) {
                     const int J = i >> lgnr, r = i & (nr - 1);
                     cpx<R> z = mk<R>(0, 0);
                     if (J <= kx) z = scale(Rin[(size_t)J * rmax + t0 + r], (R)1 - s_qv[J]);
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 cpx<R>* z = fft_warp<R, true>(A, Bf, lgnx, nr, +1, tws);
                 cpx<R>* Y = (z == A) ? Bf : A;
                 const int np = nr >> 1;
-                for (int i = tid; i < np * nx; i += nt) {
+                for (int i = wtid; i < np * nx; i += ntw) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
                     const cpx<R> za = z[(size_t)(2 * pr) * nx + m];
                     const cpx<R> zb = z[(size_t)(2 * pr + 1) * nx + m];
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 __syncthreads();
                 cpx<R>* F = fft_pair_warp<R, true>(Y, z, lgnx, np, -1, tws);
                 const int lgp = lgnr - 1;
-                for (int i = tid; i < (nkx << lgp); i += nt) {
+                for (int i = wtid; i < (nkx << lgp); i += ntw) {
                     const int j = i >> lgp, pr = i & (np - 1);
                     if (xi && j == 0) continue;  // the zero column of the subspace
                     const cpx<R> yj = F[(size_t)pr * nx + j];
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             if (ncol > 0 && xi) {
                 // centre-symmetric subspace: one s-transform per column pair (col_pair_item)
                 const int npair = ncol >> 1;
-                for (int i = tid; i < npair << lg; i += nt) {
+                for (int i = wtid; i < npair << lg; i += ntw) {
                     const int pp = i >> lg, n = i & (ns - 1);
                     // a ghost second column (past Kx) holds no data: it packs zeros
                     const bool hasb = colj(2 * pp + 1) <= kx;
@@ -350,14 +361,14 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                             if (k >= -ks && k <= ks) {
                                 const cpx<R> ck = Cp[n], cm = Cp[(ns - n) & (ns - 1)];
                                 const R bk = -(R)k * wTr;
-                                const cpx<R> pa = scale(xi_split_a(ck, cm), ins);
+                                const cpx<R> pa = xi_split_a(ck, cm);
                                 const cpx<R> ua = uhl[(2 * pp) * nk + k + ks];
                                 const cpx<R> ra = mk<R>(lin_a * ua.x - bk * ua.y - pa.x, lin_a * ua.y + bk * ua.x - pa.y);
                                 rhl[(2 * pp) * nk + k + ks] = ra;
                                 acc[0].add(ua, ra, k);
                                 cpx<R> xb = mk<R>(0, 0);
                                 if (hasb) {
-                                    const cpx<R> pb = scale(xi_split_b(ck, cm), ins);
+                                    const cpx<R> pb = xi_split_b(ck, cm);
                                     const cpx<R> ub = uhl[(2 * pp + 1) * nk + k + ks];
                                     const cpx<R> rb = mk<R>(lin_b * ub.x - bk * ub.y - pb.x, lin_b * ub.y + bk * ub.x - pb.y);
                                     rhl[(2 * pp + 1) * nk + k + ks] = rb;
@@ -403,7 +414,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                                 cpx<R> x = mk<R>(0, 0);
                                 if (k >= -ks && k <= ks) {
                                     const R a_lin = s_lin[j], rq = s_qv[j];
-                                    const cpx<R> ph = scale(Mloc[(q << lg) + n], ins);
+                                    const cpx<R> ph = Mloc[(q << lg) + n];
                                     const cpx<R> u = uhl[q * nk + k + ks];
                                     const R bk = -(R)k * wTr;
                                     const cpx<R> r = mk<R>(a_lin * u.x - bk * u.y - ph.x, a_lin * u.y + bk * u.x - ph.y);
@@ -446,7 +457,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const int n0 = row0 + t0;
                 cpx<RA>* A = scr_a;
                 cpx<RA>* Bf = scr_a + (size_t)nr * nx;
-                for (int i = tid; i < np * nx; i += nt) {
+                for (int i = wtid; i < np * nx; i += ntw) {
                     const int J = i >> lgp, pr = i & (np - 1);
                     cpx<RA> z = mk<RA>(0, 0);
                     if (J <= kx) {
@@ -461,7 +472,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 __syncthreads();
                 cpx<RA>* z = fft_pair_warp<RA, true>(A, Bf, lgnx, np, +1, tws_a);
                 cpx<RA>* Y = (z == A) ? Bf : A;
-                for (int i = tid; i < np * nx; i += nt) {
+                for (int i = wtid; i < np * nx; i += ntw) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
                     const cpx<RA> rx = z[i];
                     Y[i] = mk<RA>((RA)Ul[(size_t)(t0 + 2 * pr) * nx + m] * rx.x,
@@ -469,7 +480,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 }
                 __syncthreads();
                 cpx<RA>* F = fft_pair_warp<RA, true>(Y, z, lgnx, np, -1, tws_a);
-                for (int i = tid; i < (nkx << lgp); i += nt) {
+                for (int i = wtid; i < (nkx << lgp); i += ntw) {
                     const int j = i >> lgp, pr = i & (np - 1);
                     if (xi && j == 0) continue;
                     const cpx<RA> yj = F[(size_t)pr * nx + j];
@@ -525,7 +536,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             }
             if (kFloatAdj && ncol > 0) {
                 if (xi) {
-                    for (int i = tid; i < (ncol >> 1) << lg; i += nt) {
+                    for (int i = wtid; i < (ncol >> 1) << lg; i += ntw) {
                         const int pp = i >> lg, n = i & (ns - 1);
                         const bool hasb = colj(2 * pp + 1) <= kx;
                         scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
@@ -552,8 +563,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;
                 const RA wTa = (RA)wT;
-                const RA ins_a = (RA)ins;
-                for (int i = tid; i < npair << lg; i += nt) {
+                for (int i = wtid; i < npair << lg; i += ntw) {
                     const int pp = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
                     cpx<R> x = mk<R>(0, 0);
@@ -562,8 +572,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                         const cpx<RA> ck = scr_a[i], cm = scr_a[(pp << lg) + ((ns - n) & (ns - 1))];
                         const RA bk = (RA)k * wTa;
                         const R kk2 = (R)k * (R)k;
-                        auto update = [&](int q, int j, cpx<RA> whs) {
-                            const cpx<RA> wh = scale(whs, ins_a);
+                        auto update = [&](int q, int j, cpx<RA> wh) {
                             const RA a_lin = s_lina[j];
                             const cpx<R> rr = rhl[q * nk + k + ks];
                             const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
@@ -589,10 +598,9 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const R dt = (R)d.dtau;
                 const R wT2 = wTr * wTr;
                 const RA wTa = (RA)wT;
-                const RA ins_a = (RA)ins;
                 // G_hat = (a + i omega/T) r_hat + F[P(u r_x)], in the adjoint precision
                 auto g_hat = [&](int i, int q, int k) {
-                    const cpx<RA> wh = scale(Mloc_a[i], ins_a);
+                    const cpx<RA> wh = Mloc_a[i];
                     const RA a_lin = s_lina[rank + q * C];
                     const cpx<R> rr = rhl[q * nk + k + ks];
                     const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
@@ -600,7 +608,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     const cpx<RA> G = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
                     return mk<R>((R)G.x, (R)G.y);
                 };
-                for (int i = tid; i < ncol << lg; i += nt) {
+                for (int i = wtid; i < ncol << lg; i += ntw) {
                     const int q = i >> lg, n = i & (ns - 1);
                     const int k = (n < (ns >> 1)) ? n : n - ns;
                     cpx<R> x = mk<R>(0, 0);

@@ -599,32 +599,70 @@ KS_HD int warp0_start(int nw) {
     return o;
 }
 
+#ifndef KS_HOST_EMULATION
+// Xor-tree sums of NV values per lane (NV = 2 or 4) over the lanes below 2 o0, starting at xor
+// distance o0.  The first levels scatter: at each of the first log2(NV) levels a lane sends half
+// of the values it holds and keeps the other half, so a lane adds NV/2, NV/4, ..., 1 values per
+// level instead of NV (an FP64 add costs a whole warp-issue slot on this part whatever the lane
+// count).  Each value still meets the same xor tree as in a plain butterfly (own + partner at
+// every level), and IEEE addition commutes, so every sum has the bits the plain butterfly gives
+// at lane 0.  On return the sum of value t sits in lane xor_sum_lane(t, o0) (and its group).
+template <int NV>
+__device__ __forceinline__ double xor_sum_scatter(const double (&v)[NV], int o0) {
+    static_assert(NV == 2 || NV == 4, "two or four values");
+    const int l = threadIdx.x & 31;
+    double k0, k1;
+    int o = o0;
+    if constexpr (NV == 4) {
+        // level o0: keep (v0, v1) or (v2, v3)
+        const bool hi = (l & o) != 0;
+        k0 = hi ? v[2] : v[0];
+        k1 = hi ? v[3] : v[1];
+        const double s0 = __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[2], o);
+        const double s1 = __shfl_xor_sync(0xffffffffu, hi ? v[1] : v[3], o);
+        k0 += s0;
+        k1 += s1;
+        o >>= 1;
+    } else {
+        k0 = v[0];
+        k1 = v[1];
+    }
+    // next level: keep the first or the second of the pair
+    const bool hi = (l & o) != 0;
+    double k = hi ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, hi ? k0 : k1, o);
+    for (o >>= 1; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    return k;
+}
+
+// lane holding the sum of value t after xor_sum_scatter<NV>(., o0)
+template <int NV>
+__device__ __forceinline__ int xor_sum_lane(int t, int o0) {
+    return NV == 4 ? (t >> 1) * o0 + (t & 1) * (o0 >> 1) : t * o0;
+}
+#endif
+
 // Block-wide sum of two doubles per thread (warp shuffles, then one warp over the warp sums);
 // red has room for 2 * (warps + 1) doubles.  The result is valid in every thread after the call.
 KS_HD void block_sum2(double* red, double& s0, double& s1) {
 #ifdef KS_HOST_EMULATION
     (void)red;
 #else
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0) {
-        red[2 * w] = s0;
-        red[2 * w + 1] = s1;
+    {
+        const double v[2] = {s0, s1};
+        const double k = xor_sum_scatter<2>(v, 16);
+        if (l == xor_sum_lane<2>(0, 16)) red[2 * w] = k;
+        if (l == xor_sum_lane<2>(1, 16)) red[2 * w + 1] = k;
     }
     __syncthreads();
     if (w == 0) {
-        s0 = (l < nw) ? red[2 * l] : 0.0;
-        s1 = (l < nw) ? red[2 * l + 1] : 0.0;
-        for (int o = warp0_start(nw); o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        }
-        if (l == 0) {
-            red[2 * nw] = s0;
-            red[2 * nw + 1] = s1;
+        const double v[2] = {(l < nw) ? red[2 * l] : 0.0, (l < nw) ? red[2 * l + 1] : 0.0};
+        const int o0 = warp0_start(nw);
+        if (o0 >= 1) {
+            const double k = xor_sum_scatter<2>(v, o0);
+            if (l == xor_sum_lane<2>(0, o0)) red[2 * nw] = k;
+            if (l == xor_sum_lane<2>(1, o0)) red[2 * nw + 1] = k;
         }
     }
     __syncthreads();
@@ -737,24 +775,33 @@ KS_HD void block_reduce2(ColAcc<double>& a, ColAcc<double>& b, double* red) {
     block_reduce(a, red);
     block_reduce(b, red);
 #else
-    double v[4] = {a.J, a.L, b.J, b.L};
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0)
+    {
+        const double v[4] = {a.J, a.L, b.J, b.L};
+        const double k = xor_sum_scatter<4>(v, 16);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) red[4 * w + t] = v[t];
+        for (int t = 0; t < 4; ++t)
+            if (l == xor_sum_lane<4>(t, 16)) red[4 * w + t] = k;
+    }
     __syncthreads();
     if (w == 0) {
+        double v[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) v[t] = (l < nw) ? red[4 * l + t] : 0.0;
-        for (int o = warp0_start(nw); o > 0; o >>= 1)
+        const int o0 = warp0_start(nw);
+        if (o0 >= 2) {
+            const double k = xor_sum_scatter<4>(v, o0);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
-        if (l == 0)
+            for (int t = 0; t < 4; ++t)
+                if (l == xor_sum_lane<4>(t, o0)) red[4 * nw + t] = k;
+        } else {  // one or two warps: the plain butterfly
+            for (int o = o0; o > 0; o >>= 1)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) red[4 * nw + t] = v[t];
+                for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+            if (l == 0)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) red[4 * nw + t] = v[t];
+        }
     }
     __syncthreads();
     a.J = red[4 * nw];

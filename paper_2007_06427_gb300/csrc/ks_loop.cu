@@ -679,6 +679,23 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     return cp;
 }
 
+// Threads per CTA of the cluster kernel in plan slot `slot` (0 double, 1 float, 2 double state
+// with a float adjoint) for plan cp.  The double kernel at the default width of 128 threads
+// runs one more warp when no transform of the plan has more than 128 butterflies a pass: in
+// phase B' that warp forms J, the next T and 2 pi / T while the other four run the s-transform
+// of w_hat, which with four warps takes one round of its warps per pass instead of two (two
+// columns of 128 points: 128 radix-2 butterflies).  The element loops keep to the four work
+// warps (see k_cluster), so the extra warp only adds to phase B'.
+int cluster_block(const ks_loop* h, int slot, const ClusterPlan& cp) {
+    if (slot != 0 || h->cthreads != 128) return h->cthreads;
+    const int nx = h->d.nx;
+    const int lgnx = ilog2(nx);
+    const int zb = cp.rt * ((lgnx & 1) ? nx / 2 : nx / 4);  // transform of u + i u_x, one per row
+    const int pb = (cp.rt / 2) * (nx / 2);                   // row pairs
+    const int cb = cp.ncmax * (cp.nsmax / 2);                // columns (or column pairs)
+    return (zb <= 128 && pb <= 128 && cb <= 128) ? 160 : 128;
+}
+
 // pick the cluster size: enough CTAs to cover the GPU (about two per SM), at most 16, and a
 // plan that fits shared memory (grid rows of u in global memory if needed)
 // plan slots: 0 double, 1 float, 2 double state with a float adjoint (mixed finishing)
@@ -710,7 +727,7 @@ int setup_cluster(ks_loop* h) {
             KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);
-            cfg.blockDim = dim3(h->cthreads);
+            cfg.blockDim = dim3(cluster_block(h, pr, cp));
             cfg.dynamicSmemBytes = cp.bytes;
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeClusterDimension;
@@ -786,7 +803,7 @@ int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     const ClusterPlan& cp = h->cplan[slot];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(h->cgrid[slot]);
-    cfg.blockDim = dim3(h->cthreads);
+    cfg.blockDim = dim3(cluster_block(h, slot, cp));
     cfg.dynamicSmemBytes = cp.bytes;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
