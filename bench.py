@@ -83,6 +83,10 @@ def parse(argv=None):
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case: load the workload, run 3 x K tau-steps, no timing")
+    ap.add_argument("--ncu-dns", type=int, default=0, metavar="K",
+                    help="profiling case: K steps of the batched KSE run (1216 trajectories, "
+                         "L = 39, 64 modes), no timing")
+    ap.add_argument("--no-dns", action="store_true", help="skip the chaotic-run (DNS) line")
     ap.add_argument("--path", type=int, default=-1,
                     help="profiling case: launch path (0 cluster, 1 persistent, 2 per-phase)")
     return ap.parse_args(argv)
@@ -91,6 +95,16 @@ def parse(argv=None):
 # ---------------------------------------------------------------------------------------
 # algorithmic work per launch
 # ---------------------------------------------------------------------------------------
+def dns_step_flops(nx: int) -> float:
+    """Algorithmic flops of one ETDRK4 step of one trajectory of the KSE run: four nonlinear
+    evaluations, each an inverse and a forward complex transform of Nx points shared by two
+    trajectories (5 N log2 N flops each, so 20 Nx log2 Nx per trajectory), the square on the grid
+    (Nx), the split and the -(i q / 2) factor (6 per retained mode), and the scheme's stage
+    combinations (52 per retained mode)."""
+    nh = nx // 3 + 1
+    return 20.0 * nx * math.log2(nx) + 4.0 * (nx + 6.0 * nh) + 52.0 * nh
+
+
 def survey_step_flops(nx: int, nss) -> float:
     """Algorithmic flops of one tau-step of the batch by the hot path's work count: five 2-D real
     transforms of Nx Ns points, each 2.5 N log2 N flops (an unpruned real FFT), plus 40 flops per
@@ -585,6 +599,11 @@ def ours_arm(args):
     if not args.no_batched and ws == 1 and args.workload != "ragged256_64xNs":
         batched = batched_line(args, dev, flush, K)
 
+    dns = None
+    if not args.no_dns and ws == 1:
+        dns = dns_line(dev, flush, K)
+        add_probe((dns.get("batch1216") or {}).get("roofline"), probe)
+
     to_tol = None
     if not args.no_to_tol and ws == 1:
         to_tol = run_to_tol(args, w, dev, K)
@@ -615,6 +634,8 @@ def ours_arm(args):
             line["fp32"] = fp32
         if batched:
             line["batched"] = batched
+        if dns:
+            line["dns"] = dns
         if to_tol:
             attach_cpu_extrapolation(to_tol, cpu, w)
             line["time_to_tol"] = to_tol
@@ -821,6 +842,63 @@ def summarize(to_tol) -> dict:
     return out
 
 
+def dns_line(dev, flush, K):
+    """The chaotic run behind the initial loops (Sec. 4.3) on the GPU (ks_dns): the paper-length
+    run (L = 39, 64 modes, dt = 0.25, t = 6000, one trajectory, saved every 2 steps) and a batch
+    of 1216 trajectories (eight per block on every SM), each launch after an L2 flush and timed
+    with CUDA events; gridpoint-steps/s and the FP64 roofline of the batched run."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    L, nx, dt = 39.0, 64, 0.25
+    for name, B, nsteps in (("single_t6000", 1, 24000), ("batch1216", 1216, 4000)):
+        rng = np.random.default_rng(7)
+        u0 = torch.tensor(0.1 * rng.standard_normal((B, nx)), device=dev)
+        nsave = nsteps // 2 + 1
+        us = torch.empty(B, nsave, nx, dtype=torch.float64, device=dev)
+        nrm = torch.empty(B, nsave, dtype=torch.float64, device=dev)
+        K.ks_dns(L, nx, B, dt, 200, 2, True, u0, us, nrm, None, stream)   # warm-up
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        K.ks_dns(L, nx, B, dt, nsteps, 2, True, u0, us, nrm, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ent = {"trajectories": B, "steps": nsteps, "ms": ms, "us_per_step": 1e3 * ms / nsteps,
+               "value": B * nx * nsteps / (ms / 1e3), "unit": "gridpoint*steps/s"}
+        if B > 1:
+            ach = B * nsteps * dns_step_flops(nx) / (ms / 1e3) / 1e12
+            ent["roofline"] = {"bound": "alu", "achieved": ach, "peak": PEAK_TFLOPS["f64"],
+                               "unit": "TFLOP/s", "frac": ach / PEAK_TFLOPS["f64"],
+                               "traffic": None, "kernel": "k_dns",
+                               "flops_per_launch": B * nsteps * dns_step_flops(nx),
+                               "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)"}
+        out[name] = ent
+    out["note"] = ("ETDRK4 of the KSE, L = 39, 64 modes, dt = 0.25, centre-symmetric, state "
+                   "saved every 2 steps with its norm; one launch per run")
+    return out
+
+
+def ncu_dns(args):
+    """Small fixed case for ncu captures of the KSE run: 1216 trajectories, K steps."""
+    import numpy as np
+    import torch
+    from paper_2007_06427_gb300 import ks_loop as K
+    B, nx = 1216, 64
+    u0 = torch.tensor(0.1 * np.random.default_rng(7).standard_normal((B, nx)), device="cuda")
+    nsave = args.ncu_dns // 2 + 1
+    us = torch.empty(B, nsave, nx, dtype=torch.float64, device="cuda")
+    nrm = torch.empty(B, nsave, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        K.ks_dns(39.0, nx, B, 0.25, args.ncu_dns, 2, True, u0, us, nrm, None)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_dns": B, "steps": args.ncu_dns}))
+    return 0
+
+
 def ncu_case(args):
     """Small fixed case for ncu captures: set the state, 3 calls of K tau-steps, synchronise."""
     import torch
@@ -846,6 +924,8 @@ def main():
     args = parse()
     if args.ncu_case:
         return ncu_case(args)
+    if args.ncu_dns:
+        return ncu_dns(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)
