@@ -454,6 +454,8 @@ def throughput(args, w, mode, dev, flush, K, nsteps, autotune=False, latency_ste
     u = torch.from_numpy(w.packed()).to(dev, dt)
     T = torch.tensor(w.T0, dtype=torch.float64, device=dev)
     h = K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau, autotune=int(autotune))
+    if w.meta.get("symmetry"):
+        K.ks_set_option(h.handle, "symmetry", 1)
     K.ks_set_state(h.handle, u, T, stream)
     # warm-up: W tau-steps in the timed launch pattern (untimed)
     timed_launches(K, h, args.warmup, args.chunk, flush, stream, args.no_flush)
@@ -756,8 +758,9 @@ def run_to_tol(args, w, dev, K):
     single = {}
     single["fp64"] = descend_variant(K, w, dev, K.KS_FP64, tol, cap)
     single["mixed"] = descend_variant(K, w, dev, K.KS_MIXED, tol, cap, switch_tol=args.switch_tol)
-    single["mixed_f64_finish"] = descend_variant(K, w, dev, K.KS_MIXED, tol, cap,
-                                                 switch_tol=args.switch_tol, f32_adjoint=0)
+    # the finishing steps with the descent direction formed in float (knob finish_f32_adjoint)
+    single["mixed_f32_adjoint_finish"] = descend_variant(K, w, dev, K.KS_MIXED, tol, cap,
+                                                         switch_tol=args.switch_tol, f32_adjoint=1)
     single["fp64_extrapolated"] = descend_variant(K, w, dev, K.KS_FP64, tol, cap, extrapolate=True)
     # the extrapolated mixed run switches to double at sqrt(J) = 1e-5, about the float floor of
     # this loop: the jumps of the extrapolation restart the stall window the plain run waits on

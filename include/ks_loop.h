@@ -58,7 +58,8 @@ enum {
     KS_FP32 = 1,   /* every step in float; reductions finished in double; T in double */
     KS_MIXED = 2   /* ks_descend: float steps while sqrt(J), evaluated in double at every
                       read-back, exceeds switch_tol and keeps falling; then double steps to the
-                      end (the adjoint half of each in float unless "finish_f32_adjoint" is 0).
+                      end, all in double (the adjoint half of each in float when
+                      "finish_f32_adjoint" is 1).
                       "Keeps falling" is decided by a probe (knob "switch_probe") once the
                       float phase's rate bends, with the stall window as a fallback.
                       A loop whose float rounding alone more than doubles sqrt(J) (one that
@@ -270,11 +271,13 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *                    in float and may be probed again after stall_window steps.  0: switch only
  *                    on switch_tol or the stall window.
  *   "switch_probe_steps"  double steps of a probe, 1 .. 1e6 (default 1000)
- *   "finish_f32_adjoint"  KS_MIXED handles: 1 (default): the finishing steps keep the state,
- *                    the residual, J, dJ/dT and the update in double and form only the descent
- *                    direction G (the adjoint half of a step) in float, in the cluster-resident
- *                    form (the other forms finish all in double); 0: all-double finish.  With 0
- *                    every launch form gives bit-identical mixed descents. */
+ *   "finish_f32_adjoint"  KS_MIXED handles: 0 (default): the finishing steps run all in
+ *                    double, as the final convergence steps of the method require; every launch
+ *                    form then gives bit-identical mixed descents.  1: the finishing steps keep
+ *                    the state, the residual, J, dJ/dT and the update in double and form only
+ *                    the descent direction G (the adjoint half of a step) in float, in the
+ *                    cluster-resident form (the other forms finish all in double): faster, and
+ *                    its direction carries float rounding. */
 KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
 
 /* Read a knob or a derived launch parameter: "path" (the bulk precision's: float for KS_FP32

@@ -298,24 +298,54 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const int n0 = row0 + t0;
                 cpx<R>* A = scr;
                 cpx<R>* Bf = scr + (size_t)nr * nx;
-                for (int i = wtid; i < nr * nx; i += ntw) {
-                    const int J = i >> lgnr, r = i & (nr - 1);
-                    cpx<R> z = mk<R>(0, 0);
-                    if (J <= kx) z = scale(Rin[(size_t)J * rmax + t0 + r], (R)1 - s_qv[J]);
-                    else if (J >= nx - kx) z = scale(conj(Rin[(size_t)(nx - J) * rmax + t0 + r]), (R)1 + s_qv[nx - J]);
-                    A[(size_t)r * nx + J] = z;
-                }
-                __syncthreads();
-                cpx<R>* z = fft_warp<R, true>(A, Bf, lgnx, nr, +1, tws);
-                cpx<R>* Y = (z == A) ? Bf : A;
                 const int np = nr >> 1;
-                for (int i = wtid; i < np * nx; i += ntw) {
-                    const int pr = i >> lgnx, m = i & (nx - 1);
-                    const cpx<R> za = z[(size_t)(2 * pr) * nx + m];
-                    const cpx<R> zb = z[(size_t)(2 * pr + 1) * nx + m];
-                    Ul[(size_t)(t0 + 2 * pr) * nx + m] = za.x;
-                    Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] = zb.x;
-                    Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
+                cpx<R>* z;
+                cpx<R>* Y;
+                if constexpr (xi) {
+                    // u and u_x of a row pair in one transform (xi_zpair, as the row items)
+                    const int lgq = lgnr - 1;
+                    for (int i = wtid; i < np * nx; i += ntw) {
+                        const int J = i >> lgq, pr = i & (np - 1);
+                        cpx<R> y = mk<R>(0, 0);
+                        if (J <= kx) {
+                            const cpx<R>* src = Rin + (size_t)J * rmax + t0 + 2 * pr;
+                            y = xi_zpair(src[0], src[1], s_qv[J]);
+                        } else if (J >= nx - kx) {
+                            const cpx<R>* src = Rin + (size_t)(nx - J) * rmax + t0 + 2 * pr;
+                            y = xi_zpair(conj(src[0]), conj(src[1]), -s_qv[nx - J]);
+                        }
+                        A[(size_t)pr * nx + J] = y;
+                    }
+                    __syncthreads();
+                    z = fft_pair_warp<R, true>(A, Bf, lgnx, np, +1, tws);
+                    Y = (z == A) ? Bf : A;
+                    for (int i = wtid; i < np * nx; i += ntw) {
+                        const int pr = i >> lgnx, m = i & (nx - 1);
+                        R ua, ub, uxa, uxb;
+                        xi_zsplit(z[i], z[(size_t)pr * nx + ((nx - m) & (nx - 1))], ua, ub, uxa, uxb);
+                        Ul[(size_t)(t0 + 2 * pr) * nx + m] = ua;
+                        Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] = ub;
+                        Y[i] = mk<R>(ua * uxa, ub * uxb);
+                    }
+                } else {
+                    for (int i = wtid; i < nr * nx; i += ntw) {
+                        const int J = i >> lgnr, r = i & (nr - 1);
+                        cpx<R> zz = mk<R>(0, 0);
+                        if (J <= kx) zz = scale(Rin[(size_t)J * rmax + t0 + r], (R)1 - s_qv[J]);
+                        else if (J >= nx - kx) zz = scale(conj(Rin[(size_t)(nx - J) * rmax + t0 + r]), (R)1 + s_qv[nx - J]);
+                        A[(size_t)r * nx + J] = zz;
+                    }
+                    __syncthreads();
+                    z = fft_warp<R, true>(A, Bf, lgnx, nr, +1, tws);
+                    Y = (z == A) ? Bf : A;
+                    for (int i = wtid; i < np * nx; i += ntw) {
+                        const int pr = i >> lgnx, m = i & (nx - 1);
+                        const cpx<R> za = z[(size_t)(2 * pr) * nx + m];
+                        const cpx<R> zb = z[(size_t)(2 * pr + 1) * nx + m];
+                        Ul[(size_t)(t0 + 2 * pr) * nx + m] = za.x;
+                        Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] = zb.x;
+                        Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
+                    }
                 }
                 __syncthreads();
                 cpx<R>* F = fft_pair_warp<R, true>(Y, z, lgnx, np, -1, tws);

@@ -911,6 +911,28 @@ KS_HD bool loop_live(const Bufs<R>& p, int b) {
     return p.prec[b] == p.myprec && p.status[b] == ST_RUNNING;
 }
 
+// ---- centre-symmetric (Xi) subspace: the rows of u and u_x in pairs -------------------------
+// In the subspace every grid row of u is odd in x and its x-derivative u_x is even, so two rows
+// a, b share one complex x-transform: y = (u_a + i u_b) + (u_x,a + i u_x,b), whose odd part in x
+// is u_a + i u_b and whose even part is u_x,a + i u_x,b.  Its spectrum at x-mode J (signed
+// wavenumber q_J) is Y(J) = (1 + i q_J) (U_a(J) + i U_b(J)), U(J) the rows' spectra (the mixed
+// value v_j for J = j <= Kx, its conjugate for J = Nx - j).  One transform per row pair replaces
+// the transform of u + i u_x per row.
+template <typename R>
+KS_HD cpx<R> xi_zpair(cpx<R> ua, cpx<R> ub, R qJ) {
+    const cpx<R> c = mk<R>(ua.x - ub.y, ua.y + ub.x);  // U_a + i U_b
+    return mk<R>(c.x - qJ * c.y, c.y + qJ * c.x);      // (1 + i q_J) c
+}
+
+// The rows from y[m] and y[-m]: u = odd part, u_x = even part.
+template <typename R>
+KS_HD void xi_zsplit(cpx<R> ym, cpx<R> yn, R& ua, R& ub, R& uxa, R& uxb) {
+    ua = (R)0.5 * (ym.x - yn.x);
+    ub = (R)0.5 * (ym.y - yn.y);
+    uxa = (R)0.5 * (ym.x + yn.x);
+    uxb = (R)0.5 * (ym.y + yn.y);
+}
+
 // ------------------------------------------------------------------------------------
 // Row items (x-direction work on a tile of rows of one loop)
 // ------------------------------------------------------------------------------------
@@ -1016,6 +1038,41 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         }
         KS_SYNC();
     } else if constexpr (MODE == ROW_NONLIN) {
+        if (p.xi) {
+            // centre-symmetric subspace: u and u_x of a row pair in one transform (xi_zpair)
+            const int total = npairs * nx;
+            for (int i = KS_TID; i < total; i += KS_NT) {
+                const int J = i >> lgp;
+                const int pr = i & (npairs - 1);
+                cpx<R> y = mk<R>(0, 0);
+                if (J <= kx) {
+                    const cpx<R>* col = Mb + (size_t)J * ns + n0 + 2 * pr;
+                    y = xi_zpair(col[0], col[1], p.qv[J]);
+                } else if (J >= nx - kx) {
+                    const cpx<R>* col = Mb + (size_t)(nx - J) * ns + n0 + 2 * pr;
+                    y = xi_zpair(conj(col[0]), conj(col[1]), -p.qv[nx - J]);
+                }
+                A[(size_t)pr * nx + J] = y;
+            }
+            KS_SYNC();
+            cpx<R>* yv = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
+            cpx<R>* Y = (yv == A) ? Bf : A;
+            for (int i = KS_TID; i < total; i += KS_NT) {
+                const int pr = i >> lgnx;
+                const int m = i & (nx - 1);
+                R ua, ub, uxa, uxb;
+                xi_zsplit(yv[i], yv[(size_t)pr * nx + ((nx - m) & (nx - 1))], ua, ub, uxa, uxb);
+                R* urow = Ub + (size_t)(n0 + 2 * pr) * nx;
+                urow[m] = ua;
+                urow[nx + m] = ub;
+                Y[i] = mk<R>(ua * uxa, ub * uxb);
+            }
+            KS_SYNC();
+            cpx<R>* F = fft_pair<R, SWZ>(Y, yv, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
+            store_pair_spectra(d, F, Mb, ns, n0, lgp);
+            KS_SYNC();
+            return;
+        }
         // z = u + i u_x per row: Z_j = (1 - q_j) v_j, Z_{-j} = (1 + q_j) conj(v_j)   (a1, a2)
         const int total = nr * nx;
         for (int i = KS_TID; i < total; i += KS_NT) {

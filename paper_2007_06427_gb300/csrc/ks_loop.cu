@@ -306,7 +306,7 @@ struct ks_loop {
     ClusterPlan cplan[3] = {};      // double, float, double + float adjoint; bytes = 0: unavailable
     int cthreads = 128;
     int cgrid[3] = {0, 0, 0};
-    int finish_f32_adjoint = 1;     // mixed descents: finishing steps form the adjoint in float
+    int finish_f32_adjoint = 0;     // mixed descents: 1 = finishing steps form the adjoint in float
     // mixed descents: probe of the float floor (knobs "switch_probe", "switch_probe_steps")
     int switch_probe = 1;
     long long probe_steps = 1000;
