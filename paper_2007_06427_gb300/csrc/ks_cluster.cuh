@@ -111,12 +111,25 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     const int cid = blockIdx.x / C;
     const int ncl = gridDim.x / C;
     const int tid = threadIdx.x, nt = blockDim.x;
-    // A block of 4k + 1 warps (the double kernel, see cluster_block) carries one extra warp for
-    // the scalars of phase B'; the element loops of a step run on the other 4k warps (ntw
-    // threads) and the extra warp starts them past their end (wtid).  The transforms of such a
-    // plan have at most ntw butterflies a pass, so the extra warp gets none there either.
+    // A block of 4k + 1 warps (see cluster_block) carries one extra warp, which forms the
+    // scalars of a step (step_scalars) beside the work of the other 4k warps (ntw threads).  The
+    // element loops of a step run on the work warps only and the extra warp starts them past
+    // their end (wtid); a double transform of such a plan has at most ntw butterflies a pass, so
+    // the extra warp gets none there either.
     const int ntw = nt - (nt % 64);
     const int wtid = (tid < ntw) ? tid : (1 << 30);
+    const bool xw = ntw != nt;     // the block has the extra warp
+    // Where the extra warp forms the scalars: in phase A' for a float state (there its double
+    // arithmetic finds the FP64 pipe idle; in phase B' it held up the whole phase, 3.7 k of the
+    // 22.7 k clocks of the 64x128 float step), in phase B' for a double state (beside the
+    // s-transform of w_hat, which hides it; in phase A' it takes the FP64 pipe from the work
+    // warps, measured 1 % slower).
+    const bool sa = xw && sizeof(R) == 4;
+    const int wn = sa ? ntw : 0;   // thread count of the phase-A' transforms (0: the block)
+    auto wsync = [&]() {           // barrier of the threads that run phase A'
+        if (sa) part_sync(ntw);
+        else __syncthreads();
+    };
     const int nx = d.nx, lgnx = d.lgnx, kx = d.kx, nkx = d.nkx, B = d.B;
     const int rmax = cp.rmax;
     constexpr bool xi = XI;
@@ -287,6 +300,27 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         int done = 0;
         int st = ST_RUNNING;
         double Jlast = 0.0;
+        // The scalars of a step: the sums of the column partials in a fixed order (every rank the
+        // same bits), J, L^dag_2, the next T and 2 pi / T, and the freeze decision, taken once so
+        // that the other threads compare ints; written to red[0..3] by one lane.  Called by one
+        // whole warp.
+        auto step_scalars = [&]() {
+            double sJ, sL;
+            sum_partials(part, part + nkx, nkx, sJ, sL);
+            if ((tid & 31) == 0) {
+                const double J = sJ * d.L;
+                const double L2 = sL * d.L * (wT * wT) * kInv2Pi;  // (L / T^2) 2 pi sum
+                const double Tn = T - d.dtau * L2;    // explicit Euler for T (Sec. 4.2)
+                int sv = ST_RUNNING;
+                if (!(J == J) || J > 1e300 || !(T > 0.0)) sv = ST_DIVERGED;
+                else if (J < p.tol * p.tol) sv = ST_CONVERGED;
+                else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) sv = ST_SWITCH;
+                red[0] = J;
+                red[1] = Tn;
+                red[2] = 2.0 * 3.14159265358979323846 / Tn;
+                reinterpret_cast<int*>(red + 3)[0] = sv;
+            }
+        };
         for (int s = 0; s < nsteps; ++s) {
             // ======== phase A: rows, z = u + i u_x, U, p = u u_x, forward (a1-a4) ========
             for (int t0 = 0; t0 < nrow;) {
@@ -477,6 +511,12 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             cl.sync();
 
             // ======== phase A': rows, r_x, w = u r_x, forward (a7, a8) ========
+            // A float state with an extra warp (sa): the work warps run the phase alone,
+            // synchronised by a named barrier, while the extra warp forms this step's scalars;
+            // the partials of J and L^dag_2 are complete since the barrier that closed phase B.
+            if (sa && tid >= ntw) {
+                step_scalars();
+            } else
             for (int t0 = 0; t0 < nrow;) {
                 int nr = 2, lgp = 0;
                 while (nr * 2 <= cp.rt && nr * 2 <= nrow - t0) {
@@ -499,8 +539,8 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     }
                     A[(size_t)pr * nx + J] = z;
                 }
-                __syncthreads();
-                cpx<RA>* z = fft_pair_warp<RA, true>(A, Bf, lgnx, np, +1, tws_a);
+                wsync();
+                cpx<RA>* z = fft_pair_warp<RA, true>(A, Bf, lgnx, np, +1, tws_a, wn);
                 cpx<RA>* Y = (z == A) ? Bf : A;
                 for (int i = wtid; i < np * nx; i += ntw) {
                     const int pr = i >> lgnx, m = i & (nx - 1);
@@ -508,8 +548,8 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     Y[i] = mk<RA>((RA)Ul[(size_t)(t0 + 2 * pr) * nx + m] * rx.x,
                                   (RA)Ul[(size_t)(t0 + 2 * pr + 1) * nx + m] * rx.y);
                 }
-                __syncthreads();
-                cpx<RA>* F = fft_pair_warp<RA, true>(Y, z, lgnx, np, -1, tws_a);
+                wsync();
+                cpx<RA>* F = fft_pair_warp<RA, true>(Y, z, lgnx, np, -1, tws_a, wn);
                 for (int i = wtid; i < (nkx << lgp); i += ntw) {
                     const int j = i >> lgp, pr = i & (np - 1);
                     if (xi && j == 0) continue;
@@ -519,49 +559,38 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     cpx<RA>* dst = cl.map_shared_rank(Mloc_a, own_rank(j)) + (size_t)own_slot(j) * ns + n0 + 2 * pr;
                     store_pair(dst, scale(sm, h_a), mk<RA>(df.y * h_a, -df.x * h_a));
                 }
-                __syncthreads();
+                wsync();
                 t0 += nr;
             }
             cl.sync();
 
             // ======== phase B': J, L2, freeze test, G_hat, update, v = s-inverse (a9, a10) ===
-            // The last warp sums the partials and its first lane forms J, L^dag_2 and the next
-            // T, 2 pi / T, while the other warps run the s-transform of w_hat (its result is not
-            // used when the loop stops at this step).  A float transform is warp-owned: the last
+            // The last warp sums the partials and its first lane forms J, L^dag_2 and the next T,
+            // 2 pi / T (step_scalars), while the other warps run the s-transform of w_hat (its
+            // result is not used when the loop stops at this step); a float state with an extra
+            // warp has them ready from phase A' (sa).  A float transform is warp-owned: the last
             // warp owns none for up to (warps - 1) columns and only joins its closing barrier.  A
-            // double transform runs on the other warps alone, synchronised by a named barrier
-            // (the block has 128 or 256 threads, so there are other warps).
+            // double transform runs on the other warps alone (nfft threads), synchronised by a
+            // named barrier.
             constexpr bool kFloatAdj = sizeof(RA) == 4;
-            if (tid >= nt - 32) {
-                double sJ, sL;
-                sum_partials(part, part + nkx, nkx, sJ, sL);
-                if (tid == nt - 32) {
-                    const double J = sJ * d.L;
-                    const double L2 = sL * d.L * (wT * wT) * kInv2Pi;  // (L / T^2) 2 pi sum
-                    const double Tn = T - d.dtau * L2;    // explicit Euler for T (Sec. 4.2)
-                    // the freeze decision is taken here once, so the other threads compare ints
-                    int sv = ST_RUNNING;
-                    if (!(J == J) || J > 1e300 || !(T > 0.0)) sv = ST_DIVERGED;
-                    else if (J < p.tol * p.tol) sv = ST_CONVERGED;
-                    else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) sv = ST_SWITCH;
-                    red[0] = J;
-                    red[1] = Tn;
-                    red[2] = 2.0 * 3.14159265358979323846 / Tn;
-                    reinterpret_cast<int*>(red + 3)[0] = sv;
-                }
+            const int nfft = nt - 32;  // threads of a double transform of w_hat
+            if (!sa && tid >= nt - 32) {
+                step_scalars();
             } else if constexpr (!kFloatAdj) {
-                if (ncol > 0 && xi) {
-                    // pairs: the imaginary columns of W packed two to a transform
-                    for (int i = tid; i < (ncol >> 1) << lg; i += nt - 32) {
-                        const int pp = i >> lg, n = i & (ns - 1);
-                        const bool hasb = colj(2 * pp + 1) <= kx;
-                        scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
-                                          hasb ? Mloc_a[((2 * pp + 1) << lg) + n].y : (RA)0);
+                if (tid < nfft) {
+                    if (ncol > 0 && xi) {
+                        // pairs: the imaginary columns of W packed two to a transform
+                        for (int i = tid; i < (ncol >> 1) << lg; i += nfft) {
+                            const int pp = i >> lg, n = i & (ns - 1);
+                            const bool hasb = colj(2 * pp + 1) <= kx;
+                            scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
+                                              hasb ? Mloc_a[((2 * pp + 1) << lg) + n].y : (RA)0);
+                        }
+                        part_sync(nfft);
+                        col_fft_inplace(scr_a, Mloc_a, lg, ncol >> 1, -1, tws_a, nfft);
+                    } else if (ncol > 0) {
+                        col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a, nfft);
                     }
-                    part_sync(nt - 32);
-                    col_fft_inplace(scr_a, Mloc_a, lg, ncol >> 1, -1, tws_a, nt - 32);
-                } else if (ncol > 0) {
-                    col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a, nt - 32);
                 }
             }
             if (kFloatAdj && ncol > 0) {

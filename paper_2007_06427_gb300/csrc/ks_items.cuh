@@ -465,11 +465,14 @@ KS_HD cpx<R>* fft_pair(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx
 // lengths saved little inside the step and cost instruction-cache misses after a launch.)
 // ------------------------------------------------------------------------------------
 #ifndef KS_HOST_EMULATION
+// nthr > 0: only the first nthr threads (a multiple of 32) own transforms and call this; the
+// closing barrier is then part_sync(nthr).
 template <typename R, bool SWZ = false>
 __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
-                                                const cpx<R>* tw) {
+                                                const cpx<R>* tw, int nthr = 0) {
     const int n = 1 << lg;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (nthr > 0 ? nthr : (int)blockDim.x) >> 5;
     int span = 1;
     int p = lg;
     // this warp's transforms f = w, w + nw, ...; lanes walk (transform, butterfly) jointly
@@ -522,7 +525,8 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
         span <<= 2;
         p -= 2;
     }
-    __syncthreads();
+    if (nthr > 0) part_sync(nthr);
+    else __syncthreads();
     return a;
 }
 
@@ -565,27 +569,27 @@ __device__ __forceinline__ void load_twiddles_compact(cpx<X>* dst, const cpx<X>*
 
 template <typename R, bool SWZ = false>
 __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
-                                            const cpx<R>* tw) {
-    if constexpr (sizeof(R) == 8) return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw);
-    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw);
+                                            const cpx<R>* tw, int nthr = 0) {
+    if constexpr (sizeof(R) == 8) return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
+    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
 }
 
 // row-pair x-transforms of the cluster kernel: the double ones as fft_pair (block-wide), the float
 // ones warp-owned (the same arithmetic as fft_pair's radix-4 passes)
 template <typename R, bool SWZ = false>
 __device__ __forceinline__ cpx<R>* fft_pair_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
-                                                 const cpx<R>* tw) {
-    if constexpr (sizeof(R) == 8) return fft_pair<R, SWZ>(a, b, lg, cnt, dir, tw);
-    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw);
+                                                 const cpx<R>* tw, int nthr = 0) {
+    if constexpr (sizeof(R) == 8) return fft_pair<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
+    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
 }
 
 // s-transforms of the cluster kernel: the double ones as fft_col (block-wide), the float ones
 // warp-owned (the same arithmetic as fft_col's radix-4 passes)
 template <typename R, bool SWZ = false>
 __device__ __forceinline__ cpx<R>* fft_col_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
-                                                const cpx<R>* tw) {
-    if constexpr (sizeof(R) == 8) return fft_col<R, SWZ>(a, b, lg, cnt, dir, tw);
-    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw);
+                                                const cpx<R>* tw, int nthr = 0) {
+    if constexpr (sizeof(R) == 8) return fft_col<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
+    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
 }
 #endif
 

@@ -680,14 +680,18 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
 }
 
 // Threads per CTA of the cluster kernel in plan slot `slot` (0 double, 1 float, 2 double state
-// with a float adjoint) for plan cp.  The double kernel at the default width of 128 threads
-// runs one more warp when no transform of the plan has more than 128 butterflies a pass: in
-// phase B' that warp forms J, the next T and 2 pi / T while the other four run the s-transform
-// of w_hat, which with four warps takes one round of its warps per pass instead of two (two
-// columns of 128 points: 128 radix-2 butterflies).  The element loops keep to the four work
-// warps (see k_cluster), so the extra warp only adds to phase B'.
+// with a float adjoint) for plan cp.  At the default width of 128 threads the kernel runs one more
+// warp, which forms the scalars of each step (J, the next T and 2 pi / T, the freeze decision)
+// beside the four work warps: in phase B' for a double state (before, the s-transform of w_hat
+// ran on three warps, two rounds of its 128 butterflies a pass), in phase A' for a float state
+// (before, the scalars held up phase B': 3.7 k of 22.7 k clocks of the 64x128 float step).  The
+// element loops keep to the four work warps (see k_cluster).  A double transform spread over
+// five warps could put two warps on one SM sub-partition, so the double plans take the extra
+// warp only when none of their transforms has more than 128 butterflies a pass; the float
+// transforms are warp-owned, where a fifth warp never adds a round.
 int cluster_block(const ks_loop* h, int slot, const ClusterPlan& cp) {
-    if (slot != 0 || h->cthreads != 128) return h->cthreads;
+    if (h->cthreads != 128) return h->cthreads;
+    if (slot == 1) return 160;  // float: warp-owned transforms, never more rounds with 5 warps
     const int nx = h->d.nx;
     const int lgnx = ilog2(nx);
     const int zb = cp.rt * ((lgnx & 1) ? nx / 2 : nx / 4);  // transform of u + i u_x, one per row
