@@ -284,7 +284,10 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
  * and KS_MIXED handles), "path_f64", "path_f32", "finish_f32_adjoint", "switch_probe",
  * "switch_probe_steps", "cluster_f64",
  * "cluster_f32", "cluster_mixed_finish" (cluster
- * size in use, 0 if the cluster path cannot hold the batch), "cluster_smem_f64",
+ * size in use, 0 if the cluster path cannot hold the batch), "cluster_block_f64",
+ * "cluster_block_f32", "cluster_block_mixed_finish" (threads per CTA of that cluster kernel:
+ * "cluster_threads" work threads, plus one warp for the step scalars at the default width of
+ * 128 where the plan allows it; 0 if no plan), "cluster_smem_f64",
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "stall_drop_ppm",
  * "chunk", "symmetry", "graph", "graph_replays" (graphs replayed since create),
  * "row_threads", "col_threads",

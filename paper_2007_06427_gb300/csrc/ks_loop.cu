@@ -2253,6 +2253,9 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "switch_probe") *value = h->switch_probe;
     else if (k == "switch_probe_steps") *value = h->probe_steps;
     else if (k == "cluster_threads") *value = h->cthreads;
+    else if (k == "cluster_block_f64") *value = h->cplan[0].bytes ? cluster_block(h, 0, h->cplan[0]) : 0;
+    else if (k == "cluster_block_f32") *value = h->cplan[1].bytes ? cluster_block(h, 1, h->cplan[1]) : 0;
+    else if (k == "cluster_block_mixed_finish") *value = h->cplan[2].bytes ? cluster_block(h, 2, h->cplan[2]) : 0;
     else if (k == "cluster_mixed_finish") *value = h->cplan[2].bytes ? h->cplan[2].C : 0;
     else if (k == "stall_window") *value = h->stall_window;
     else if (k == "stall_drop_ppm") *value = std::llround(h->stall_drop * 1e6);

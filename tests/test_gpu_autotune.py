@@ -100,3 +100,18 @@ def test_default_launch_path_rule():
         assert (K.ks_get_option(h.handle, "path_f64"), K.ks_get_option(h.handle, "path_f32")) == (1, 1)
         K.ks_set_option(h.handle, "path_f64", 0)
         assert (K.ks_get_option(h.handle, "path_f64"), K.ks_get_option(h.handle, "path_f32")) == (0, 1)
+
+
+def test_cluster_block_width_rule():
+    """Threads per CTA of the cluster kernel: the 128 work threads plus one warp for the step
+    scalars for a float state always, for a double state when no transform of its plan has more
+    than 128 butterflies a pass (the single 64 x 128 loop on 16 CTAs: 8 rows and 2 columns of 128
+    per CTA); the 256-thread width has no extra warp.  Every width gives the same bits (the
+    launch-form and autotune tests compare them)."""
+    with K.KSLoop(22.0, 64, [128], K.KS_MIXED) as h:
+        assert K.ks_get_option(h.handle, "cluster_threads") == 128
+        assert K.ks_get_option(h.handle, "cluster_block_f64") == 160
+        assert K.ks_get_option(h.handle, "cluster_block_f32") == 160
+    with K.KSLoop(100.0, 256, [1024], K.KS_FP64) as h:       # 256-point rows, 1024-point columns
+        if K.ks_get_option(h.handle, "cluster_f64"):
+            assert K.ks_get_option(h.handle, "cluster_block_f64") == 128
