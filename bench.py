@@ -89,6 +89,8 @@ def parse(argv=None):
     ap.add_argument("--no-dns", action="store_true", help="skip the chaotic-run (DNS) line")
     ap.add_argument("--path", type=int, default=-1,
                     help="profiling case: launch path (0 cluster, 1 persistent, 2 per-phase)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="profiling case: launch the per-phase kernels directly, not as CUDA graphs")
     return ap.parse_args(argv)
 
 
@@ -915,6 +917,8 @@ def ncu_case(args):
     with K.KSLoop(w.L, w.nx, w.ns, mode, w.scheme, w.dtau) as h:
         if args.path >= 0:
             K.ks_set_option(h.handle, "path", args.path)
+        if args.no_graph:
+            K.ks_set_option(h.handle, "graph", 0)
         K.ks_set_state(h.handle, u, T)
         for _ in range(3):
             K.ks_step(h.handle, args.ncu_case, 0.0)

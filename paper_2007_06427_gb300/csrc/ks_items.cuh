@@ -908,6 +908,18 @@ KS_HD void sum_partials(const ff* a, const ff* c, int n, double& sa, double& sc)
 #endif
 }
 
+// The freeze decision of a loop after the reductions of a step (J and the current T): diverged
+// (J not finite or huge, T not positive), converged (sqrt(J) < tol), the float phase's switch
+// threshold reached, or running.  Taken by one thread of a column item, which passes the int on
+// through shared memory: in double, a compare occupies the FP64 pipe for a whole warp-issue slot.
+template <typename R>
+KS_HD int freeze_status(const Bufs<R>& p, double J, double T) {
+    if (!(J == J) || J > 1e300 || !(T > 0.0)) return ST_DIVERGED;
+    if (J < p.tol * p.tol) return ST_CONVERGED;
+    if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) return ST_SWITCH;
+    return ST_RUNNING;
+}
+
 // is the loop processed by this kernel set?
 template <typename R>
 KS_HD bool loop_live(const Bufs<R>& p, int b) {
@@ -1368,16 +1380,15 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
                 double sJ, sL;
                 sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
                 if (KS_TID == 0) {
-                    red[0] = sJ * d.L;
+                    const double Js = sJ * d.L;
+                    red[0] = Js;
                     red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
+                    reinterpret_cast<int*>(red + 2)[0] = freeze_status(p, Js, T);
                 }
             }
             KS_SYNC();
             const double J = red[0], L2 = red[1];
-            int st = ST_RUNNING;
-            if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
-            else if (J < p.tol * p.tol) st = ST_CONVERGED;
-            else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
+            const int st = reinterpret_cast<const int*>(red + 2)[0];
             if (pp == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
             if (st != ST_RUNNING) {
                 if (pp == 0 && KS_TID == 0) {
@@ -1567,17 +1578,16 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 double sJ, sL;
                 sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
                 if (KS_TID == 0) {
-                    red[0] = sJ * d.L;
+                    const double Js = sJ * d.L;
+                    red[0] = Js;
                     // (L / T^2) * 2 pi * sum, with 2 pi / T^2 = (2 pi / T)^2 / (2 pi): no division
                     red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
+                    reinterpret_cast<int*>(red + 2)[0] = freeze_status(p, Js, T);
                 }
             }
             KS_SYNC();
             const double J = red[0], L2 = red[1];
-            int st = ST_RUNNING;
-            if (!(J == J) || J > 1e300 || !(T > 0.0)) st = ST_DIVERGED;
-            else if (J < p.tol * p.tol) st = ST_CONVERGED;
-            else if (p.myprec == 1 && p.switch_tol > 0.0 && J <= p.switch_tol * p.switch_tol) st = ST_SWITCH;
+            const int st = reinterpret_cast<const int*>(red + 2)[0];
             if (j == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
             if (st != ST_RUNNING) {
                 if (j == 0 && KS_TID == 0) {
