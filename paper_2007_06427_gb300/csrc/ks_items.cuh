@@ -251,6 +251,8 @@ struct Bufs {
     int own_frozen_only;    // cluster kernel: 1 = carry T forward only for frozen loops of this
                             // precision (the other precision's launch runs concurrently and
                             // carries its own)
+    int step_scalars;       // 1 (tau-steps): ROW_ADJ forms each running loop's step scalars
+                            // (loop_scalars) for the COL_UPDATE items that follow
 };
 
 // Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 4.1, the
@@ -920,6 +922,42 @@ KS_HD int freeze_status(const Bufs<R>& p, double J, double T) {
     return ST_RUNNING;
 }
 
+// 1 / (2 pi), for L^dag_2 = (L / T^2) 2 pi S = L (2 pi / T)^2 S / (2 pi) from the stored 2 pi / T
+constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
+
+// The scalars of loop b's tau-step once its column partials are complete: J and L^dag_2 (the
+// partials summed in a fixed order, as every launch form sums them), the freeze decision, sqrt(J)
+// and, at step parity par ^ 1, the next T by explicit Euler (Sec. 4.2) and 2 pi / T, or the
+// current ones carried forward with the status when the loop freezes.  Per loop, not per column:
+// one warp of the ROW_ADJ item that holds the loop's first rows calls it, so the COL_UPDATE items
+// of the loop find the decision in p.status instead of each forming it again.
+template <typename R>
+KS_HD void loop_scalars(const Dims& d, const Bufs<R>& p, int b, int par) {
+    const int B = d.B, nkx = d.nkx;
+    double sJ, sL;
+    sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
+    if ((KS_TID & 31) == 0) {
+        const double T = p.T[(size_t)par * B + b], wT = p.wT[(size_t)par * B + b];
+        const double J = sJ * d.L;
+        // (L / T^2) 2 pi sum, with 2 pi / T^2 = (2 pi / T)^2 / (2 pi): no division
+        const double L2 = sL * d.L * (wT * wT) * kInv2Pi;
+        const int st = freeze_status(p, J, T);
+        double* Tn = p.T + (size_t)(par ^ 1) * B;
+        double* wTn = p.wT + (size_t)(par ^ 1) * B;
+        p.sqrtJ[b] = sqrt(J);
+        if (st != ST_RUNNING) {
+            p.status[b] = st;
+            Tn[b] = T;
+            wTn[b] = wT;
+        } else {
+            const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
+            Tn[b] = Tnew;
+            wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
+            p.steps[b] += 1;
+        }
+    }
+}
+
 // is the loop processed by this kernel set?
 template <typename R>
 KS_HD bool loop_live(const Bufs<R>& p, int b) {
@@ -1010,8 +1048,10 @@ KS_HD void store_pair_spectra(const Dims& d, const cpx<R>* Y, cpx<R>* Mb, int ns
 }
 
 // SWZ: p.tw is the bank-swizzled shared-memory copy of the twiddle table (load_twiddles).
+// par: step parity of the T arrays (the persistent kernel passes its step's; the per-phase
+// launches take p.par).
 template <typename R, int MODE, bool SWZ = false>
-KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem) {
+KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* smem, int par = -1) {
     const RowItem it = p.rows[item];
     const int b = it.b;
     if constexpr (MODE == ROW_NONLIN || MODE == ROW_ADJ) {
@@ -1140,6 +1180,9 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         cpx<R>* F = fft_pair<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
+        // the loop's step scalars, once per loop (the column partials are complete since
+        // COL_RESID); after the item's last barrier, so the rest of the block moves on
+        if (p.step_scalars && n0 == 0 && KS_TID < 32) loop_scalars(d, p, b, par < 0 ? p.par : par);
     }
 }
 
@@ -1159,8 +1202,6 @@ enum ColMode {
 // Shared-memory bytes a column item needs beyond its two transform buffers.
 constexpr int COL_RED_DOUBLES = 4 * (256 / 32 + 1) + 4;  // blocks of up to 256 threads
 
-// 1 / (2 pi), for L^dag_2 = (L / T^2) 2 pi S = L (2 pi / T)^2 S / (2 pi) from the stored 2 pi / T
-constexpr double kInv2Pi = 0.5 / 3.14159265358979323846;
 
 // Threads that accumulate one column's J and L^dag_2 partial: element n of a column goes to
 // accumulator n mod COL_ACC_LANES in every launch form, whatever the block size, so the partial
@@ -1375,30 +1416,9 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
         }
 
         if constexpr (MODE == COL_UPDATE) {
-            const double T = Tc[b];
-            if (KS_TID < 32) {
-                double sJ, sL;
-                sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
-                if (KS_TID == 0) {
-                    const double Js = sJ * d.L;
-                    red[0] = Js;
-                    red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
-                    reinterpret_cast<int*>(red + 2)[0] = freeze_status(p, Js, T);
-                }
-            }
-            KS_SYNC();
-            const double J = red[0], L2 = red[1];
-            const int st = reinterpret_cast<const int*>(red + 2)[0];
-            if (pp == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
-            if (st != ST_RUNNING) {
-                if (pp == 0 && KS_TID == 0) {
-                    p.status[b] = st;
-                    Tn[b] = T;
-                    wTn[b] = wTc[b];
-                }
-                KS_SYNC();
-                return;
-            }
+            // J, the freeze decision and the next T of this step were formed once for the loop
+            // by ROW_ADJ (loop_scalars): a loop that froze now is in p.status
+            if (p.status[b] != ST_RUNNING) return;
             const R dt = (R)d.dtau;
             const R wT2 = w_over_T * w_over_T;
             const R cq_a = p.cq[ja], cq_b = hasb ? p.cq[jb] : (R)0;
@@ -1432,12 +1452,6 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
                 cola[i] = mk<R>(0, v[i].x);
                 if (hasb) colb[i] = mk<R>(0, v[i].y);
                 if (pp == 0) M0[i] = zero;
-            }
-            if (pp == 0 && KS_TID == 0) {
-                const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
-                Tn[b] = Tnew;
-                wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
-                p.steps[b] += 1;
             }
             KS_SYNC();
         }
@@ -1571,33 +1585,9 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 KS_SYNC();
             }
         } else if constexpr (MODE == COL_UPDATE) {
-            // J and L^dag_2 of this loop from the column partials: warp 0 sums them in a fixed
-            // order (identical in every CTA of the loop, so all CTAs take the same decision)
-            const double T = Tc[b];
-            if (KS_TID < 32) {
-                double sJ, sL;
-                sum_partials(p.Jpart + (size_t)b * nkx, p.L2part + (size_t)b * nkx, nkx, sJ, sL);
-                if (KS_TID == 0) {
-                    const double Js = sJ * d.L;
-                    red[0] = Js;
-                    // (L / T^2) * 2 pi * sum, with 2 pi / T^2 = (2 pi / T)^2 / (2 pi): no division
-                    red[1] = sL * d.L * (wTc[b] * wTc[b]) * kInv2Pi;
-                    reinterpret_cast<int*>(red + 2)[0] = freeze_status(p, Js, T);
-                }
-            }
-            KS_SYNC();
-            const double J = red[0], L2 = red[1];
-            const int st = reinterpret_cast<const int*>(red + 2)[0];
-            if (j == 0 && KS_TID == 0) p.sqrtJ[b] = sqrt(J);
-            if (st != ST_RUNNING) {
-                if (j == 0 && KS_TID == 0) {
-                    p.status[b] = st;
-                    Tn[b] = T;
-                    wTn[b] = wTc[b];
-                }
-                KS_SYNC();
-                return;
-            }
+            // J, the freeze decision and the next T of this step were formed once for the loop
+            // by ROW_ADJ (loop_scalars): a loop that froze now is in p.status
+            if (p.status[b] != ST_RUNNING) return;
             const R dt = (R)d.dtau;
             const R cqj = p.cq[j];
             const R wT2 = w_over_T * w_over_T;
@@ -1647,12 +1637,6 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             KS_SYNC();
             cpx<R>* v = fft_col<R, SWZ>(Y, p.xi ? X : F, lg, 1, +1, p.tw, 0, p.twsh);
             for (int i = KS_TID; i < ns; i += KS_NT) col[i] = v[i];
-            if (j == 0 && KS_TID == 0) {
-                const double Tnew = T - d.dtau * L2;  // explicit Euler for T (Sec. 4.2)
-                Tn[b] = Tnew;
-                wTn[b] = 2.0 * 3.14159265358979323846 / Tnew;
-                p.steps[b] += 1;
-            }
             KS_SYNC();
         }
     }

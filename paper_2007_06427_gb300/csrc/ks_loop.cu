@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128, 6) k_persist(Dims d, Bufs<R> p, int nstep
         if (!grid_sync(bar)) return;
         for (int it = blockIdx.x; it < ncol_r; it += gridDim.x) col_item<R, COL_RESID, true>(d, q, it, smem, par);
         if (!grid_sync(bar)) return;
-        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ, true>(d, q, it, smem);
+        for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ, true>(d, q, it, smem, par);
         if (!grid_sync(bar)) return;
         for (int it = blockIdx.x; it < ncol_u; it += gridDim.x) col_item<R, COL_UPDATE, true>(d, q, it, smem, par);
         if (s + 1 < nsteps && !grid_sync(bar)) return;
@@ -511,6 +511,7 @@ Bufs<R> make_bufs(ks_loop* h, const Work& w, int pr, int check_active, double to
     p.tol = tol;
     p.switch_tol = switch_tol;
     p.check_active = check_active;
+    p.step_scalars = check_active;  // the tau-step contexts; the gradient pass forms none
     p.xi = h->xi;
     return p;
 }

@@ -173,6 +173,7 @@ int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T
     cols_pass<R, COL_SYNTH_U>(d, h, 0);
     if (mode == 0) {
         p.check_active = 1;
+        p.step_scalars = 1;  // ROW_ADJ forms each loop's step scalars, as in the launches
         for (int s = 0; s < steps; ++s) {
             p.par = s & 1;
             rows_pass<R>(d, h, ROW_NONLIN);
@@ -182,6 +183,7 @@ int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T
             if (s == 0) a = h.sqrtJ;
         }
         p.check_active = 0;
+        p.step_scalars = 0;
         for (int b = 0; b < B; ++b) c[b] = h.T[(size_t)(steps & 1) * B + b];
         cols_pass<R, COL_SYNTH_U>(d, h, 0);
     } else {
