@@ -781,6 +781,9 @@ def run_to_tol(args, w, dev, K):
                                 ("mixed_extrapolated", K.KS_MIXED, True)):
             orb[name] = descend_variant(K, g, dev, mode, tol, oc, extrapolate=ext, symmetry=True,
                                         switch_tol=1e-5 if (ext and mode == K.KS_MIXED) else 0.0)
+        # the finishing steps with the descent direction formed in float
+        orb["mixed_f32_adjoint_finish"] = descend_variant(K, g, dev, K.KS_MIXED, tol, oc,
+                                                          symmetry=True, f32_adjoint=1)
         out[g.name] = orb
     if args.batched_max_steps > 0:
         rg = workload("ragged256_64xNs")

@@ -375,6 +375,7 @@ KS_API int ks_dns(double L, int nx, int batch, double dt, long long nsteps, int 
  *   nx, nsave: the trajectory's [nsave][nx] layout in `us` (device or host doubles)
  *   dts      : time between saved samples, > 0
  *   a_idx, T, ns: HOST arrays [nloops]: first sample, period (> 0) and Ns (>= 1) of each loop
+ *             (device pointers there are rejected with KS_ERR_ARG)
  *   out      : out, ragged-packed loops [sum_l Ns_l * nx] doubles, layout [n][m] (device or host)
  * KS_ERR_ARG for a null pointer, nsave < 2, dts not finite and > 0, nloops < 0, or a segment
  * whose last instant needs a sample past the last saved one (the interpolation reads the samples

@@ -491,6 +491,9 @@ extern "C" int ks_dns_segments(int nx, long long nsave, double dts, const double
     if (nloops < 0) return dns_fail(KS_ERR_ARG, "nloops must be >= 0");
     if (nloops == 0) return KS_OK;
     if (!us || !a_idx || !T || !ns || !out) return dns_fail(KS_ERR_ARG, "null pointer");
+    // the per-loop tables are read here on the host
+    if (dns_is_device(a_idx) || dns_is_device(T) || dns_is_device(ns))
+        return dns_fail(KS_ERR_ARG, "a_idx, T and ns must be host arrays");
     std::vector<long long> off(nloops);
     long long tot = 0;
     for (int l = 0; l < nloops; ++l) {

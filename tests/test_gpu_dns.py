@@ -208,3 +208,19 @@ def test_recurrence_loops_lie_near_solutions():
         J = ko.residual(lp.u, lp.T, L)["J"]
         J_rnd = ko.residual(rnd * math.sqrt(np.mean(lp.u ** 2)), lp.T, L)["J"]
         assert J / e < 0.2 and J < 0.1 * J_rnd
+
+
+def test_segments_reject_device_tables():
+    """The per-loop tables are read on the host: device pointers there are rejected with
+    KS_ERR_ARG (called through ctypes, since the binding always passes host arrays)."""
+    import ctypes
+    lib = K.load_library()
+    us = torch.zeros(10, 8, dtype=torch.float64, device="cuda")
+    out = torch.zeros(64, dtype=torch.float64, device="cuda")
+    a_dev = torch.zeros(1, dtype=torch.int32, device="cuda")
+    T = np.array([3.0])
+    ns = np.array([8], dtype=np.int32)
+    rc = lib.ks_dns_segments(8, 10, 0.5, ctypes.c_void_p(us.data_ptr()), 1, ctypes.c_void_p(a_dev.data_ptr()),
+                             T.ctypes.data_as(ctypes.c_void_p), ns.ctypes.data_as(ctypes.c_void_p),
+                             ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == K.KS_ERR_ARG
