@@ -297,6 +297,25 @@ KS_HD cpx<R> twid(const cpx<R>* tw, int t, int dir, int sh = 0) {
     return w;
 }
 
+// Row skew of a transform buffer.  The element loops around the x-transforms address their
+// buffers row by row with the rows fastest (the gathers of the mixed values, the splits of the
+// spectra), so consecutive lanes touch one element of each row at a stride of Nx elements: all on
+// one bank.  Element x of transform (row) f therefore sits at f n + (x ^ row_skew(f, n)), the
+// column index XORed with the row's low bits (below the 128 bytes of E elements, and below n), so
+// the lanes of such a loop spread over E banks.  Only the buffers that those loops fill (the
+// input of an inverse x-transform) or read (the output of a forward one) are skewed: the
+// transform reads its input (SKI) or writes its output (SKO) through the same map, one XOR in its
+// first or last pass.  Addresses only: the arithmetic, hence every result, is unchanged.
+// Float buffers only: on GB300 the per-phase float steps ran about 3% faster with it, while the
+// double ones (8 elements per 128 bytes, pipe-bound FP64 transforms) did not gain, so for double
+// the skew is 0 and the XORs fold away.
+template <typename R>
+KS_HD int row_skew(int f, int n) {
+    if constexpr (sizeof(R) != 4) return 0;
+    constexpr int E = 128 / (int)sizeof(cpx<R>);
+    return f & ((n < E ? n : E) - 1);
+}
+
 // Barrier of the first nthr threads of the block (a multiple of 32): a plain block barrier when
 // that is the whole block, else named barrier 1, which the other warps never use.
 KS_HD void part_sync(int nthr) {
@@ -312,7 +331,8 @@ KS_HD void part_sync(int nthr) {
 // nthr > 0: only the first nthr threads (a multiple of 32) run the transform and meet at
 // part_sync(nthr); every one of them must call it.  The arithmetic is the same either way.
 // twsh: the swizzled table is compact (entry t at tw_swz(t >> twsh)).
-template <typename R, bool SWZ = false>
+// SKI / SKO: the input / output is row-skewed (row_skew).
+template <typename R, bool SWZ = false, bool SKI = false, bool SKO = false>
 KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
                         int nthr = 0, int twsh = 0) {
 #ifdef KS_HOST_EMULATION
@@ -323,16 +343,18 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
     const int n = 1 << lg;
     int span = 1;  // size of the sub-transforms completed so far
     int p = lg;
+    bool first = true;
     if (p & 1) {
-        // radix-2 pass with span 1: no twiddles
+        // radix-2 pass with span 1: no twiddles (never the last pass: n >= 8)
         const int nb = n >> 1;
         const int total = cnt * nb;
         for (int i = KS_TID; i < total; i += NT) {
             const int f = i >> (lg - 1);
             const int j = i & (nb - 1);
+            const int si = SKI ? row_skew<R>(f, n) : 0;
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            const cpx<R> v0 = s[j], v1 = s[j + nb];
+            const cpx<R> v0 = s[j ^ si], v1 = s[(j + nb) ^ si];
             d[2 * j] = v0 + v1;
             d[2 * j + 1] = v0 - v1;
         }
@@ -343,31 +365,36 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
         b = t;
         span = 2;
         p -= 1;
+        first = false;
     }
     while (p > 0) {
         const int nb = n >> 2;
         const int total = cnt * nb;
         const int tu = NMAX / (span * 4);
+        const bool ski = SKI && first, sko = SKO && p == 2;
         for (int i = KS_TID; i < total; i += NT) {
             const int f = i >> (lg - 2);
             const int j = i & (nb - 1);
+            const int si = ski ? row_skew<R>(f, n) : 0;
+            const int so = sko ? row_skew<R>(f, n) : 0;
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            const cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+            const cpx<R> v0 = s[j ^ si], v1 = s[(j + nb) ^ si], v2 = s[(j + 2 * nb) ^ si], v3 = s[(j + 3 * nb) ^ si];
             const int jm = j & (span - 1);
             const int od = ((j - jm) << 2) + jm;
             if (span > 1) {
                 const int t = jm * tu;
                 bfly4_tw(v0, v1, v2, v3, twid<R, SWZ>(tw, t, dir, twsh),
                          twid<R, SWZ>(tw, 2 * t, dir, twsh), twid<R, SWZ>(tw, 3 * t, dir, twsh),
-                         dir, d[od], d[od + span], d[od + 2 * span], d[od + 3 * span]);
+                         dir, d[od ^ so], d[(od + span) ^ so], d[(od + 2 * span) ^ so],
+                         d[(od + 3 * span) ^ so]);
             } else {
                 const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
                 const cpx<R> t3 = mul_i(v1 - v3, dir);
-                d[od] = t0 + t2;
-                d[od + 1] = t1 + t3;
-                d[od + 2] = t0 - t2;
-                d[od + 3] = t1 - t3;
+                d[od ^ so] = t0 + t2;
+                d[(od + 1) ^ so] = t1 + t3;
+                d[(od + 2) ^ so] = t0 - t2;
+                d[(od + 3) ^ so] = t1 - t3;
             }
         }
         if (nthr > 0) part_sync(nthr);
@@ -377,6 +404,7 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
         b = t;
         span <<= 2;
         p -= 2;
+        first = false;
     }
     return a;
 }
@@ -386,7 +414,7 @@ KS_HD cpx<R>* fft_batch(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cp
 // a single column keeps twice as many warps busy; with the twiddle product fused into the
 // additions (v0 + w v1 as four fused multiply-adds, v0 - w v1 as 2 v0 minus that) it costs 3
 // floating-point operations per point per radix-2 stage, as the fused radix-4 butterfly does.
-template <typename R, bool SWZ = false>
+template <typename R, bool SWZ = false, bool SKI = false, bool SKO = false>
 KS_HD cpx<R>* fft_batch_r2(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
                            int nthr = 0, int twsh = 0) {
 #ifdef KS_HOST_EMULATION
@@ -399,21 +427,24 @@ KS_HD cpx<R>* fft_batch_r2(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const
     const int total = cnt * nb;
     for (int span = 1; span < n; span <<= 1) {
         const int tu = NMAX / (span * 2);
+        const bool ski = SKI && span == 1, sko = SKO && 2 * span == n;
         for (int i = KS_TID; i < total; i += NT) {
             const int f = i >> (lg - 1);
             const int j = i & (nb - 1);
+            const int si = ski ? row_skew<R>(f, n) : 0;
+            const int so = sko ? row_skew<R>(f, n) : 0;
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            const cpx<R> v0 = s[j], v1 = s[j + nb];
+            const cpx<R> v0 = s[j ^ si], v1 = s[(j + nb) ^ si];
             const int jm = j & (span - 1);
             const int od = ((j - jm) << 1) + jm;
             if (span > 1) {
                 const cpx<R> t = cfma(v0, twid<R, SWZ>(tw, jm * tu, dir, twsh), v1);
-                d[od] = t;
-                d[od + span] = twice_minus(v0, t);
+                d[od ^ so] = t;
+                d[(od + span) ^ so] = twice_minus(v0, t);
             } else {
-                d[od] = v0 + v1;
-                d[od + 1] = v0 - v1;
+                d[od ^ so] = v0 + v1;
+                d[(od + 1) ^ so] = v0 - v1;
             }
         }
         if (nthr > 0) part_sync(nthr);
@@ -447,11 +478,12 @@ KS_HD cpx<R>* fft_col(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<
 #ifndef KS_PAIR_RADIX2
 #define KS_PAIR_RADIX2 1
 #endif
-template <typename R, bool SWZ = false>
+template <typename R, bool SWZ = false, bool SKI = false, bool SKO = false>
 KS_HD cpx<R>* fft_pair(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx<R>* tw,
                        int nthr = 0, int twsh = 0) {
-    if constexpr (sizeof(R) == 8 && KS_PAIR_RADIX2) return fft_batch_r2<R, SWZ>(a, b, lg, cnt, dir, tw, nthr, twsh);
-    else return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw, nthr, twsh);
+    if constexpr (sizeof(R) == 8 && KS_PAIR_RADIX2)
+        return fft_batch_r2<R, SWZ, SKI, SKO>(a, b, lg, cnt, dir, tw, nthr, twsh);
+    else return fft_batch<R, SWZ, SKI, SKO>(a, b, lg, cnt, dir, tw, nthr, twsh);
 }
 
 // ------------------------------------------------------------------------------------
@@ -469,7 +501,7 @@ KS_HD cpx<R>* fft_pair(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir, const cpx
 #ifndef KS_HOST_EMULATION
 // nthr > 0: only the first nthr threads (a multiple of 32) own transforms and call this; the
 // closing barrier is then part_sync(nthr).
-template <typename R, bool SWZ = false>
+template <typename R, bool SWZ = false, bool SKI = false, bool SKO = false>
 __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                                 const cpx<R>* tw, int nthr = 0) {
     const int n = 1 << lg;
@@ -479,13 +511,15 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
     int p = lg;
     // this warp's transforms f = w, w + nw, ...; lanes walk (transform, butterfly) jointly
     const int nf = (cnt > w) ? (cnt - w + nw - 1) / nw : 0;
+    bool first = true;
     if (p & 1) {
         const int nb = n >> 1;
         for (int i = lane; i < nf * nb; i += 32) {
             const int f = w + (i >> (lg - 1)) * nw, j = i & (nb - 1);
+            const int si = SKI ? row_skew<R>(f, n) : 0;
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            const cpx<R> v0 = s[j], v1 = s[j + nb];
+            const cpx<R> v0 = s[j ^ si], v1 = s[(j + nb) ^ si];
             d[2 * j] = v0 + v1;
             d[2 * j + 1] = v0 - v1;
         }
@@ -495,29 +529,33 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
         b = t;
         span = 2;
         p -= 1;
+        first = false;
     }
     while (p > 0) {
         const int nb = n >> 2;
         const int tu = NMAX / (span * 4);
+        const bool ski = SKI && first, sko = SKO && p == 2;
         for (int i = lane; i < nf * nb; i += 32) {
             const int f = w + (i >> (lg - 2)) * nw, j = i & (nb - 1);
+            const int si = ski ? row_skew<R>(f, n) : 0;
+            const int so = sko ? row_skew<R>(f, n) : 0;
             const cpx<R>* s = a + (size_t)f * n;
             cpx<R>* d = b + (size_t)f * n;
-            const cpx<R> v0 = s[j], v1 = s[j + nb], v2 = s[j + 2 * nb], v3 = s[j + 3 * nb];
+            const cpx<R> v0 = s[j ^ si], v1 = s[(j + nb) ^ si], v2 = s[(j + 2 * nb) ^ si], v3 = s[(j + 3 * nb) ^ si];
             const int jm = j & (span - 1);
             const int od = ((j - jm) << 2) + jm;
             if (span > 1) {
                 const int t = jm * tu;
                 bfly4_tw(v0, v1, v2, v3, twid<R, SWZ>(tw, t, dir), twid<R, SWZ>(tw, 2 * t, dir),
-                         twid<R, SWZ>(tw, 3 * t, dir), dir, d[od], d[od + span],
-                         d[od + 2 * span], d[od + 3 * span]);
+                         twid<R, SWZ>(tw, 3 * t, dir), dir, d[od ^ so], d[(od + span) ^ so],
+                         d[(od + 2 * span) ^ so], d[(od + 3 * span) ^ so]);
             } else {
                 const cpx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
                 const cpx<R> t3 = mul_i(v1 - v3, dir);
-                d[od] = t0 + t2;
-                d[od + 1] = t1 + t3;
-                d[od + 2] = t0 - t2;
-                d[od + 3] = t1 - t3;
+                d[od ^ so] = t0 + t2;
+                d[(od + 1) ^ so] = t1 + t3;
+                d[(od + 2) ^ so] = t0 - t2;
+                d[(od + 3) ^ so] = t1 - t3;
             }
         }
         __syncwarp();
@@ -526,6 +564,7 @@ __device__ __forceinline__ cpx<R>* fft_warp_any(cpx<R>* a, cpx<R>* b, int lg, in
         b = t;
         span <<= 2;
         p -= 2;
+        first = false;
     }
     if (nthr > 0) part_sync(nthr);
     else __syncthreads();
@@ -569,20 +608,20 @@ __device__ __forceinline__ void load_twiddles_compact(cpx<X>* dst, const cpx<X>*
         cp_async<sizeof(cpx<X>)>(dst + tw_swz<X>(i), src + (size_t)i * st);
 }
 
-template <typename R, bool SWZ = false>
+template <typename R, bool SWZ = false, bool SKI = false, bool SKO = false>
 __device__ __forceinline__ cpx<R>* fft_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                             const cpx<R>* tw, int nthr = 0) {
-    if constexpr (sizeof(R) == 8) return fft_batch<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
-    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
+    if constexpr (sizeof(R) == 8) return fft_batch<R, SWZ, SKI, SKO>(a, b, lg, cnt, dir, tw, nthr);
+    else return fft_warp_any<R, SWZ, SKI, SKO>(a, b, lg, cnt, dir, tw, nthr);
 }
 
 // row-pair x-transforms of the cluster kernel: the double ones as fft_pair (block-wide), the float
 // ones warp-owned (the same arithmetic as fft_pair's radix-4 passes)
-template <typename R, bool SWZ = false>
+template <typename R, bool SWZ = false, bool SKI = false, bool SKO = false>
 __device__ __forceinline__ cpx<R>* fft_pair_warp(cpx<R>* a, cpx<R>* b, int lg, int cnt, int dir,
                                                  const cpx<R>* tw, int nthr = 0) {
-    if constexpr (sizeof(R) == 8) return fft_pair<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
-    else return fft_warp_any<R, SWZ>(a, b, lg, cnt, dir, tw, nthr);
+    if constexpr (sizeof(R) == 8) return fft_pair<R, SWZ, SKI, SKO>(a, b, lg, cnt, dir, tw, nthr);
+    else return fft_warp_any<R, SWZ, SKI, SKO>(a, b, lg, cnt, dir, tw, nthr);
 }
 
 // s-transforms of the cluster kernel: the double ones as fft_col (block-wide), the float ones
@@ -992,8 +1031,8 @@ KS_HD void xi_zsplit(cpx<R> ym, cpx<R> yn, R& ua, R& ub, R& uxa, R& uxb) {
 // ------------------------------------------------------------------------------------
 enum RowMode { ROW_ANALYZE = 0, ROW_NONLIN = 1, ROW_ADJ = 2, ROW_SYNTH = 3 };
 
-// Fill A[pair][J] (J in [0, Nx)) with the Hermitian-extended spectra of two rows (a = 2*pair,
-// b = 2*pair + 1) read from M: Z_J = X^a_J + i X^b_J with X_{-j} = conj(X_j).
+// Fill A[pair][J] (J in [0, Nx), row-skewed) with the Hermitian-extended spectra of two rows
+// (a = 2*pair, b = 2*pair + 1) read from M: Z_J = X^a_J + i X^b_J with X_{-j} = conj(X_j).
 template <typename R>
 KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, int lgp,
                              cpx<R>* A) {
@@ -1021,11 +1060,12 @@ KS_HD void load_pair_spectra(const Dims& d, const cpx<R>* Mb, int ns, int n0, in
             }
             z = xa + mul_i(xb, 1);
         }
-        A[(size_t)pr * nx + J] = z;
+        A[(size_t)pr * nx + (J ^ row_skew<R>(pr, nx))] = z;  // row-skewed (the transform's SKI)
     }
 }
 
-// From Y = FFT(y_a + i y_b) (forward, unscaled) extract the half spectra of the two real rows,
+// From Y = FFT(y_a + i y_b) (forward, unscaled, row-skewed) extract the half spectra of the two
+// real rows,
 // scaled by 1/Nx, for j = 0..Kx, and store them to M[j][n0 + 2 pr + {0,1}].
 template <typename R>
 KS_HD void store_pair_spectra(const Dims& d, const cpx<R>* Y, cpx<R>* Mb, int ns, int n0,
@@ -1037,8 +1077,9 @@ KS_HD void store_pair_spectra(const Dims& d, const cpx<R>* Y, cpx<R>* Mb, int ns
     for (int i = KS_TID; i < total; i += KS_NT) {
         const int j = i >> lgp;
         const int pr = i & (npairs - 1);
-        const cpx<R> yj = Y[(size_t)pr * nx + j];
-        const cpx<R> ym = conj(Y[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
+        const int sk = row_skew<R>(pr, nx);  // Y is row-skewed (the transform's SKO)
+        const cpx<R> yj = Y[(size_t)pr * nx + (j ^ sk)];
+        const cpx<R> ym = conj(Y[(size_t)pr * nx + (((nx - j) & (nx - 1)) ^ sk)]);
         const cpx<R> sm = yj + ym;  // 2 X^a
         const cpx<R> df = yj - ym;  // 2 i X^b
         cpx<R>* col = Mb + (size_t)j * ns + n0 + 2 * pr;
@@ -1077,13 +1118,13 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             A[i] = mk<R>(ra[m], ra[nx + m]);
         }
         KS_SYNC();
-        cpx<R>* Y = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, -1, p.tw, 0, p.twsh);
+        cpx<R>* Y = fft_pair<R, SWZ, false, true>(A, Bf, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, Y, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_SYNTH) {
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
+        cpx<R>* z = fft_pair<R, SWZ, true, false>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
         const int total = npairs * nx;
         for (int i = KS_TID; i < total; i += KS_NT) {
             const int pr = i >> lgnx;
@@ -1108,10 +1149,10 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                     const cpx<R>* col = Mb + (size_t)(nx - J) * ns + n0 + 2 * pr;
                     y = xi_zpair(conj(col[0]), conj(col[1]), -p.qv[nx - J]);
                 }
-                A[(size_t)pr * nx + J] = y;
+                A[(size_t)pr * nx + (J ^ row_skew<R>(pr, nx))] = y;
             }
             KS_SYNC();
-            cpx<R>* yv = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
+            cpx<R>* yv = fft_pair<R, SWZ, true, false>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
             cpx<R>* Y = (yv == A) ? Bf : A;
             for (int i = KS_TID; i < total; i += KS_NT) {
                 const int pr = i >> lgnx;
@@ -1124,7 +1165,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 Y[i] = mk<R>(ua * uxa, ub * uxb);
             }
             KS_SYNC();
-            cpx<R>* F = fft_pair<R, SWZ>(Y, yv, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
+            cpx<R>* F = fft_pair<R, SWZ, false, true>(Y, yv, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
             store_pair_spectra(d, F, Mb, ns, n0, lgp);
             KS_SYNC();
             return;
@@ -1141,10 +1182,10 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
                 const int j = nx - J;
                 z = scale(conj(Mb[(size_t)j * ns + n0 + r]), (R)1 + p.qv[j]);
             }
-            A[(size_t)r * nx + J] = z;
+            A[(size_t)r * nx + (J ^ row_skew<R>(r, nx))] = z;
         }
         KS_SYNC();
-        cpx<R>* z = fft_batch<R, SWZ>(A, Bf, lgnx, nr, +1, p.tw, 0, p.twsh);
+        cpx<R>* z = fft_batch<R, SWZ, true, false>(A, Bf, lgnx, nr, +1, p.tw, 0, p.twsh);
         cpx<R>* Y = (z == A) ? Bf : A;
         // keep u, form p = u u_x for the row pairs (a3)
         const int tp = npairs * nx;
@@ -1159,14 +1200,14 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(za.x * za.y, zb.x * zb.y);
         }
         KS_SYNC();
-        cpx<R>* F = fft_pair<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
+        cpx<R>* F = fft_pair<R, SWZ, false, true>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);  // a4 (x-pass)
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
     } else if constexpr (MODE == ROW_ADJ) {
         // r_x rows from the column pass output rho = s-inverse of i q_j r_hat   (a7)
         load_pair_spectra(d, Mb, ns, n0, lgp, A);
         KS_SYNC();
-        cpx<R>* z = fft_pair<R, SWZ>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
+        cpx<R>* z = fft_pair<R, SWZ, true, false>(A, Bf, lgnx, npairs, +1, p.tw, 0, p.twsh);
         cpx<R>* Y = (z == A) ? Bf : A;
         const int tp = npairs * nx;
         for (int i = KS_TID; i < tp; i += KS_NT) {
@@ -1177,7 +1218,7 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             Y[i] = mk<R>(ua[m] * rx.x, ua[nx + m] * rx.y);  // w = u r_x  (a8)
         }
         KS_SYNC();
-        cpx<R>* F = fft_pair<R, SWZ>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
+        cpx<R>* F = fft_pair<R, SWZ, false, true>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
         // the loop's step scalars, once per loop (the column partials are complete since
