@@ -217,6 +217,13 @@ KS_API int ks_profile_read(ks_loop_t h, int n, char* names, double* ms, long lon
  *                    else 128.
  *   "cluster"        0 (default): cluster size chosen per precision; 1..16: force this size
  *                    (KS_ERR_ARG when no plan of that size fits the batch)
+ *   "cluster_exchange" 1 (default): the cluster kernel's DSMEM exchanges are asynchronous
+ *                    stores counted on an mbarrier of the receiving CTA, which starts its next
+ *                    phase once its bytes have landed (in plans with room for a second column
+ *                    buffer that keep the CTAs per SM the batch uses); 0: the phases are
+ *                    separated by cluster barriers.  Results are bit-identical either way.
+ *   "cluster_min_blocks" 0 (default): the cluster kernel variant is chosen by occupancy (see
+ *                    "cluster_min_blocks_f64"); 1 or 2: force it.  Results are bit-identical.
  *   "symmetry"       1: restrict the descent to loops invariant under Xi: (x, s) -> (-x, s),
  *                    u -> -u (the centre-symmetric subspace, Sec. 4.1).  Every later analysis of a
  *                    grid field (ks_residual, ks_adjoint_grad, ks_set_state, ks_descend) projects
@@ -284,8 +291,14 @@ KS_API int ks_set_option(ks_loop_t h, const char* key, long long value);
  * and KS_MIXED handles), "path_f64", "path_f32", "finish_f32_adjoint", "switch_probe",
  * "switch_probe_steps", "cluster_f64",
  * "cluster_f32", "cluster_mixed_finish" (cluster
- * size in use, 0 if the cluster path cannot hold the batch), "cluster_block_f64",
- * "cluster_block_f32", "cluster_block_mixed_finish" (threads per CTA of that cluster kernel:
+ * size in use, 0 if the cluster path cannot hold the batch),
+ * "cluster_exchange", "cluster_exchange_f64", "cluster_exchange_f32" (whether that plan
+ * exchanges through mbarriers), "cluster_grid_f64", "cluster_grid_f32" (CTAs of that cluster
+ * launch: cluster size x resident clusters, at most the batch), "cluster_min_blocks_f64",
+ * "cluster_min_blocks_f32" (the kernel variant's resident blocks per SM bound: 1, no register
+ * cap; 2, at most 128 registers, chosen where it keeps more clusters resident),
+ * "cluster_block_f64", "cluster_block_f32", "cluster_block_mixed_finish" (threads per CTA of
+ * that cluster kernel:
  * "cluster_threads" work threads, plus one warp for the step scalars at the default width of
  * 128 where the plan allows it; 0 if no plan), "cluster_smem_f64",
  * "cluster_smem_f32" (bytes per CTA), "rows_per_tile", "stall_window", "stall_drop_ppm",

@@ -12,8 +12,11 @@
 //     U array when the plan cannot hold them).
 // The four phases of a tau-step (see ks_items.cuh) exchange data through DSMEM: a row phase
 // gathers the columns' values for its rows from the owners and scatters its results back.
-// Phases are separated by hardware cluster barriers; there is no grid-wide synchronisation
-// and no global-memory round trip inside a step.  Column owners broadcast their partials of
+// Each exchange is a set of asynchronous remote stores (st.async) that count their bytes on an
+// mbarrier of the receiving CTA; a CTA starts its next phase once the bytes it expects have
+// landed (plans without room for the second column buffer this needs, and the knob
+// "cluster_exchange" = 0, separate the phases by hardware cluster barriers instead).  There is
+// no grid-wide synchronisation and no global-memory round trip inside a step.  Column owners broadcast their partials of
 // J and L^dag_2 to every rank; every rank sums them in the same fixed order, so all ranks
 // take the same freeze decision and advance T identically.  The per-element arithmetic and
 // the reduction orders are those of the per-phase items, so results agree bit for bit.
@@ -40,7 +43,100 @@ struct ClusterPlan {
     int off_tab;  // per-x-mode tables q_j, q_j^2 - q_j^4, q_j^4 (q_j^2 - 1)^2 (and the second in RA)
     int bytes;
     int u_global;  // 1: the rank's grid rows of u live in global memory (U array), not SMEM
+    // mbarrier exchanges (ax = 1): a second column buffer (off_M2) receives the phase-A' results,
+    // so that no exchange writes a buffer its receiver may still be reading (see k_cluster), and
+    // four mbarriers (off_bar), one per exchange of a step.  ax = 0: off_M2 = off_M, cluster
+    // barriers.
+    int ax, off_M2, off_bar;
+    int* err;      // set to 1 when an exchange wait gives up (bounded, see xbar_wait)
+    int mb;        // the kernel's minimum resident blocks per SM (launch bounds): 1 or 2
 };
+
+// ---- mbarrier exchanges ---------------------------------------------------------------------
+// A producer writes its values into the receiver's shared memory with st.async, each store
+// counting its bytes (complete_tx) on the receiver's mbarrier of that exchange; the receiver
+// arms the barrier with the byte count it expects (one arrival, arrive.expect_tx) and waits for
+// the phase to complete.  Stores may land before the arming: the transaction count then runs
+// negative until it.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// shared::cluster address of the same offset in the shared memory of cluster rank `rank`
+__device__ __forceinline__ unsigned cluster_u32(unsigned a, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void xbar_init(unsigned bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void xbar_arm(unsigned bar, unsigned bytes) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state) : "r"(bar), "r"(bytes) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ bool xbar_test(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long xbar_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of parity `parity`; true once it completed.  Bounded: after about a second
+// of the global timer (or 2^26 polls) the wait gives up, sets *err and returns false, and it
+// returns false at once when another wait has set *err.  The caller then stops arming and
+// pushing (k_cluster: xdead), so the launch runs out its steps without waiting and the host
+// reports the error; every thread takes the same path through the kernel's block barriers.
+__device__ __forceinline__ bool xbar_wait(unsigned bar, unsigned parity, int* err) {
+    if (xbar_test(bar, parity)) return true;
+    const unsigned long long t0 = xbar_clock_ns();
+    for (unsigned it = 1;; ++it) {
+        if (xbar_test(bar, parity)) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int*)err) return false;
+            if (it > (1u << 26) || xbar_clock_ns() - t0 > 1000000000ull) {
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+// Two adjacent complex values to shared::cluster address dst (16-byte aligned), counted on bar.
+__device__ __forceinline__ void st_async_pair(unsigned dst, cpx<float> a, cpx<float> b, unsigned bar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+        ::"r"(dst), "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async_pair(unsigned dst, cpx<double> a, cpx<double> b, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+                 ::"r"(dst), "d"(a.x), "d"(a.y), "r"(bar) : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+                 ::"r"(dst + 16u), "d"(b.x), "d"(b.y), "r"(bar) : "memory");
+}
+// One partial (8 bytes, 8-byte aligned).
+__device__ __forceinline__ void st_async_part(unsigned dst, double v, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];"
+                 ::"r"(dst), "d"(v), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async_part(unsigned dst, ff v, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+                 ::"r"(dst), "f"(v.hi), "f"(v.lo), "r"(bar) : "memory");
+}
 
 // rows per rank: an even number covering Ns with C ranks
 __host__ __device__ inline int cluster_rows_per_rank(int ns, int C) {
@@ -92,15 +188,18 @@ struct AdjTables {
 // the forward transform and G_hat assembly of phase B').  RA = R is the plain float or double
 // descent; R = double, RA = float is the finishing stage of a mixed descent, where r, J,
 // dJ/dT and the update stay in double and only the descent direction is formed in float.
-// Launch bounds: up to 256 threads, at least one resident block per SM.  With the first bound
-// alone ptxas held the double kernel to 64 registers and spilled 120 bytes per thread, whose
-// stores and reloads reached L2 and DRAM after a flush; with both it uses ~150 registers and
-// spills nothing.  The single loop runs one block per SM anyway, and the batched workloads
-// (64x64 batch, ragged, 256x1024) measured no slower with the fewer resident blocks.
+// Launch bounds: up to 256 threads and MB resident blocks per SM.  MB = 1 leaves ptxas its
+// choice (128-157 registers, no spills; with the thread bound alone it held the double kernel
+// to 64 registers and spilled), the faster form for one loop; MB = 2 caps it at 128 (it then
+// takes 96-113, no spills), which lets three blocks of 160 threads share an SM (a sub-partition
+// holds four warps of at most 128 registers), so a batch of 16 loops in clusters of 16 runs in
+// one wave instead of two (batch16_64x64: 17.3 -> 10.7 us float, 48.9 -> 29.4 us double, while
+// one 64x128 loop takes 9.14 -> 9.46 and 28.5 -> 28.8 us).  The plan picks MB by occupancy
+// (setup_cluster).
 // XI: the centre-symmetric subspace (p.xi set), a separate instantiation so that each kernel
 // carries only the code of its own column scheme.
-template <typename R, typename RA, bool XI>
-__global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables<RA> ta,
+template <typename R, typename RA, bool XI, int MB>
+__global__ void __launch_bounds__(256, MB) k_cluster(Dims d, Bufs<R> p, AdjTables<RA> ta,
                                                  ClusterPlan cp, int nsteps, int par0, int use_M) {
     typedef typename PartT<R>::type Part;
     constexpr bool kSame = sizeof(R) == sizeof(RA);
@@ -148,6 +247,14 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     // adjoint-precision views of the same buffers (phases are separated by barriers)
     cpx<RA>* Rin_a = reinterpret_cast<cpx<RA>*>(Rin);
     cpx<RA>* Mloc_a = reinterpret_cast<cpx<RA>*>(Mloc);
+    // mbarrier exchanges (ax): the phase-A' results land in a second column buffer, which phase
+    // B' also works in, so Mloc is only ever written by phase A's exchange and read in phase B
+    cpx<R>* const Mloc2 = reinterpret_cast<cpx<R>*>(smem + cp.off_M2);
+    cpx<RA>* const Mloc2_a = reinterpret_cast<cpx<RA>*>(Mloc2);
+    const bool ax = cp.ax != 0;
+    const unsigned xbar0 = smem_u32(smem + cp.off_bar);  // exchange x: xbar0 + 8 x
+    unsigned xpar = 0;  // bit x: parity of the next phase of exchange x's mbarrier
+    bool xdead = false;  // a wait of this thread gave up: no more arming, pushing or waiting
     cpx<RA>* scr_a = reinterpret_cast<cpx<RA>*>(scr);
     cpx<RA>* tws_a = kSame ? reinterpret_cast<cpx<RA>*>(tws) : reinterpret_cast<cpx<RA>*>(smem + cp.off_tw_a);
     // 1/(2 Nx) of the row split; per loop it is multiplied by 1/Ns, the normalisation of the
@@ -180,6 +287,11 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
     const int nm = max(nx, cp.nsmax);  // longest transform of the launch
     load_twiddles(tws, p.tw, nm);
     if (!kSame) load_twiddles(tws_a, ta.tw, nm);
+    if (ax && tid == 0) {
+        // first used after the cluster barrier that precedes a loop's steps
+        for (int x = 0; x < 4; ++x) xbar_init(xbar0 + 8u * x);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
 
     for (int bi = cid; bi < B; bi += ncl) {
         const int b = one ? 0 : ((bi == cid) ? b_first : p.colorder[bi]);
@@ -207,6 +319,19 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         const int row0 = rank * rpr;
         const int nrow = (row0 < ns) ? min(rpr, ns - row0) : 0;
         cpx<R>* Mg = p.M + moff_b;
+        // bytes each exchange of a step delivers to this rank: phase A (A'), the values of its
+        // real columns at every row; phase B, the values of its rows in every exchanged column
+        // and two partials per column; phase B', the values of its rows in every column
+        int mycols = ncol;
+        if (xi) {
+            mycols = 0;
+            for (int q = 0; q < ncol; ++q) mycols += (colj(q) <= kx) ? 1 : 0;
+        }
+        const int ncx = xi ? kx : nkx;
+        const unsigned bx_A = (unsigned)(mycols * ns) * (unsigned)sizeof(cpx<R>);
+        const unsigned bx_B = (unsigned)(ncx * nrow) * (unsigned)sizeof(cpx<RA>) + 2u * ncx * (unsigned)sizeof(Part);
+        const unsigned bx_Aa = (unsigned)(mycols * ns) * (unsigned)sizeof(cpx<RA>);
+        const unsigned bx_Ba = (unsigned)(ncx * nrow) * (unsigned)sizeof(cpx<R>);
         R* Ul = cp.u_global ? p.U + goff_b + (size_t)row0 * nx : Us;
 
         // ---- the band of the owned columns, and the rows' mixed values (when valid) ----
@@ -239,32 +364,48 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
         }
         if (!one) load_state();
 
+        // two adjacent values to the same offset (local pointer `local`) in the shared memory of
+        // rank rk: counted on rk's mbarrier of exchange x (x >= 0 and ax), or plain DSMEM stores
+        auto xput = [&](auto* local, int rk, int x, auto a, auto b) {
+            if (ax && x >= 0) {
+                if (!xdead) st_async_pair(cluster_u32(smem_u32(local), rk), a, b, cluster_u32(xbar0 + 8u * x, rk));
+            } else {
+                store_pair(cl.map_shared_rank(local, rk), a, b);
+            }
+        };
+        // partial slot j of rank rk (exchange 1, phase B)
+        auto xpart = [&](int j, int rk, Part v) {
+            if (ax) {
+                if (!xdead) st_async_part(cluster_u32(smem_u32(part + j), rk), v, cluster_u32(xbar0 + 8u, rk));
+            } else {
+                cl.map_shared_rank(part, rk)[j] = v;
+            }
+        };
         // push a column result X[q][n] (n = 0..Ns-1) to the row owners' Rin[j][n - row0(owner)],
         // two rows per store (rows per rank and rmax are even, so a pair has one owner)
-        auto push_columns = [&](const auto* X, auto* RinT) {
+        auto push_columns = [&](const auto* X, auto* RinT, int x) {
             for (int i = wtid; i < (ncol << lg) >> 1; i += ntw) {
                 const int q = (2 * i) >> lg, n = (2 * i) & (ns - 1);
                 const int owner = n / rpr;
-                auto* dst = cl.map_shared_rank(RinT, owner);
-                store_pair(dst + (size_t)colj(q) * rmax + (n - owner * rpr), X[2 * i], X[2 * i + 1]);
+                xput(RinT + (size_t)colj(q) * rmax + (n - owner * rpr), owner, x, X[2 * i], X[2 * i + 1]);
             }
         };
         // push the s-inverse c of each column pair: column 2p+1 gets Re c, column 2p+2 Im c, as
         // the imaginary parts (imag = true: u, v) or the real parts (rho)
-        auto push_pairs = [&](const auto* Cp, auto* RinT, bool imag) {
+        auto push_pairs = [&](const auto* Cp, auto* RinT, bool imag, int x) {
             typedef typename std::remove_pointer<decltype(RinT)>::type CT;
             typedef decltype(CT{}.x) X;
             for (int i = wtid; i < (ncol << lg) >> 2; i += ntw) {
                 const int pp = (2 * i) >> lg, n = (2 * i) & (ns - 1);
                 const int owner = n / rpr;
-                auto* dst = cl.map_shared_rank(RinT, owner) + (n - owner * rpr);
+                auto* dst = RinT + (n - owner * rpr);
                 const auto c0 = Cp[2 * i], c1 = Cp[2 * i + 1];
                 const int ja = colj(2 * pp), jb = ja + 1;
-                if (imag) store_pair(dst + (size_t)ja * rmax, mk<X>(0, c0.x), mk<X>(0, c1.x));
-                else store_pair(dst + (size_t)ja * rmax, mk<X>(c0.x, 0), mk<X>(c1.x, 0));
+                if (imag) xput(dst + (size_t)ja * rmax, owner, x, mk<X>(0, c0.x), mk<X>(0, c1.x));
+                else xput(dst + (size_t)ja * rmax, owner, x, mk<X>(c0.x, 0), mk<X>(c1.x, 0));
                 if (jb <= kx) {
-                    if (imag) store_pair(dst + (size_t)jb * rmax, mk<X>(0, c0.y), mk<X>(0, c1.y));
-                    else store_pair(dst + (size_t)jb * rmax, mk<X>(c0.y, 0), mk<X>(c1.y, 0));
+                    if (imag) xput(dst + (size_t)jb * rmax, owner, x, mk<X>(0, c0.y), mk<X>(0, c1.y));
+                    else xput(dst + (size_t)jb * rmax, owner, x, mk<X>(c0.y, 0), mk<X>(c1.y, 0));
                 }
             }
         };
@@ -283,7 +424,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 }
                 __syncthreads();
                 col_fft_inplace(Mloc, scr, lg, ncol >> 1, +1, tws);
-                push_pairs(Mloc, Rin, true);
+                push_pairs(Mloc, Rin, true, -1);
             } else {
                 for (int i = wtid; i < ncol << lg; i += ntw) {
                     const int q = i >> lg, n = i & (ns - 1);
@@ -292,7 +433,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 }
                 __syncthreads();
                 col_fft_inplace(Mloc, scr, lg, ncol, +1, tws);
-                push_columns(Mloc, Rin);
+                push_columns(Mloc, Rin, -1);
             }
         }
         cl.sync();
@@ -320,6 +461,22 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 red[2] = 2.0 * 3.14159265358979323846 / Tn;
                 reinterpret_cast<int*>(red + 3)[0] = sv;
             }
+        };
+        // End of a phase: wait until exchange x has delivered its `bytes` to this rank (ax), or a
+        // cluster barrier.  The block barrier first: the pushes read local buffers (the
+        // transforms' scratch) that the next phase overwrites.
+        auto xsync = [&](int x, unsigned bytes) {
+            if (!ax) {
+                cl.sync();
+                return;
+            }
+            __syncthreads();
+            const unsigned bar = xbar0 + 8u * x;
+            if (!xdead) {
+                if (tid == 0) xbar_arm(bar, bytes);
+                xdead = !xbar_wait(bar, (xpar >> x) & 1u, cp.err);
+            }
+            xpar ^= 1u << x;
         };
         for (int s = 0; s < nsteps; ++s) {
             // ======== phase A: rows, z = u + i u_x, U, p = u u_x, forward (a1-a4) ========
@@ -390,13 +547,13 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     const cpx<R> yj = F[(size_t)pr * nx + j];
                     const cpx<R> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<R> sm = yj + ym, df = yj - ym;
-                    cpx<R>* dst = cl.map_shared_rank(Mloc, own_rank(j)) + (size_t)own_slot(j) * ns + n0 + 2 * pr;
-                    store_pair(dst, scale(sm, h), mk<R>(df.y * h, -df.x * h));
+                    xput(Mloc + (size_t)own_slot(j) * ns + n0 + 2 * pr, own_rank(j), 0, scale(sm, h),
+                         mk<R>(df.y * h, -df.x * h));
                 }
                 __syncthreads();
                 t0 += nr;
             }
-            cl.sync();
+            xsync(0, bx_A);
 
             // ======== phase B: columns, r_hat, partials, rho = s-inverse of i q r_hat ========
             if (ncol > 0 && xi) {
@@ -446,18 +603,17 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     }
                     block_reduce2(acc[0], acc[1], red);
                     if (tid < C) {
-                        Part* dstp = cl.map_shared_rank(part, tid);
-                        dstp[ja] = acc[0].part_J(2.0);
-                        dstp[nkx + ja] = acc[0].part_L(2.0);
+                        xpart(ja, tid, acc[0].part_J(2.0));
+                        xpart(nkx + ja, tid, acc[0].part_L(2.0));
                         if (hasb) {
-                            dstp[jb] = acc[1].part_J(2.0);
-                            dstp[nkx + jb] = acc[1].part_L(2.0);
+                            xpart(jb, tid, acc[1].part_J(2.0));
+                            xpart(nkx + jb, tid, acc[1].part_L(2.0));
                         }
                     }
                 }
                 __syncthreads();
                 // inverse of the pairs of i q r_hat (Mloc holds the spectra, scr is scratch)
-                push_pairs(fft_col_warp<RA, true>(Mloc_a, scr_a, lg, npair, +1, tws_a), Rin_a, false);
+                push_pairs(fft_col_warp<RA, true>(Mloc_a, scr_a, lg, npair, +1, tws_a), Rin_a, false, 1);
             } else if (ncol > 0) {
                 col_fft_inplace(Mloc, scr, lg, ncol, -1, tws);
                 const R wTr = (R)wT;
@@ -493,22 +649,21 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     if (two) block_reduce2(acc[0], acc[1], red);
                     else block_reduce(acc[0], red);
                     if (tid < C) {
-                        Part* dstp = cl.map_shared_rank(part, tid);
 #pragma unroll
                         for (int t = 0; t < 2; ++t) {
                             if (t == 1 && !two) break;
                             const int j = rank + (q0 + t) * C;
                             const double wj = (j == 0) ? 1.0 : 2.0;
-                            dstp[j] = acc[t].part_J(wj);
-                            dstp[nkx + j] = acc[t].part_L(wj);
+                            xpart(j, tid, acc[t].part_J(wj));
+                            xpart(nkx + j, tid, acc[t].part_L(wj));
                         }
                     }
                 }
                 __syncthreads();
                 // inverse of i q r_hat (scr holds the spectra, Mloc is scratch), then push rho
-                push_columns(fft_col_warp<RA, true>(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a);
+                push_columns(fft_col_warp<RA, true>(scr_a, Mloc_a, lg, ncol, +1, tws_a), Rin_a, 1);
             }
-            cl.sync();
+            xsync(1, bx_B);
 
             // ======== phase A': rows, r_x, w = u r_x, forward (a7, a8) ========
             // A float state with an extra warp (sa): the work warps run the phase alone,
@@ -556,13 +711,13 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     const cpx<RA> yj = F[(size_t)pr * nx + j];
                     const cpx<RA> ym = conj(F[(size_t)pr * nx + ((nx - j) & (nx - 1))]);
                     const cpx<RA> sm = yj + ym, df = yj - ym;
-                    cpx<RA>* dst = cl.map_shared_rank(Mloc_a, own_rank(j)) + (size_t)own_slot(j) * ns + n0 + 2 * pr;
-                    store_pair(dst, scale(sm, h_a), mk<RA>(df.y * h_a, -df.x * h_a));
+                    xput(Mloc2_a + (size_t)own_slot(j) * ns + n0 + 2 * pr, own_rank(j), 2, scale(sm, h_a),
+                         mk<RA>(df.y * h_a, -df.x * h_a));
                 }
                 wsync();
                 t0 += nr;
             }
-            cl.sync();
+            xsync(2, bx_Aa);
 
             // ======== phase B': J, L2, freeze test, G_hat, update, v = s-inverse (a9, a10) ===
             // The last warp sums the partials and its first lane forms J, L^dag_2 and the next T,
@@ -583,13 +738,13 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                         for (int i = tid; i < (ncol >> 1) << lg; i += nfft) {
                             const int pp = i >> lg, n = i & (ns - 1);
                             const bool hasb = colj(2 * pp + 1) <= kx;
-                            scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
-                                              hasb ? Mloc_a[((2 * pp + 1) << lg) + n].y : (RA)0);
+                            scr_a[i] = mk<RA>(Mloc2_a[((2 * pp) << lg) + n].y,
+                                              hasb ? Mloc2_a[((2 * pp + 1) << lg) + n].y : (RA)0);
                         }
                         part_sync(nfft);
-                        col_fft_inplace(scr_a, Mloc_a, lg, ncol >> 1, -1, tws_a, nfft);
+                        col_fft_inplace(scr_a, Mloc2_a, lg, ncol >> 1, -1, tws_a, nfft);
                     } else if (ncol > 0) {
-                        col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a, nfft);
+                        col_fft_inplace(Mloc2_a, scr_a, lg, ncol, -1, tws_a, nfft);
                     }
                 }
             }
@@ -598,13 +753,13 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     for (int i = wtid; i < (ncol >> 1) << lg; i += ntw) {
                         const int pp = i >> lg, n = i & (ns - 1);
                         const bool hasb = colj(2 * pp + 1) <= kx;
-                        scr_a[i] = mk<RA>(Mloc_a[((2 * pp) << lg) + n].y,
-                                          hasb ? Mloc_a[((2 * pp + 1) << lg) + n].y : (RA)0);
+                        scr_a[i] = mk<RA>(Mloc2_a[((2 * pp) << lg) + n].y,
+                                          hasb ? Mloc2_a[((2 * pp + 1) << lg) + n].y : (RA)0);
                     }
                     __syncthreads();
-                    col_fft_inplace(scr_a, Mloc_a, lg, ncol >> 1, -1, tws_a);
+                    col_fft_inplace(scr_a, Mloc2_a, lg, ncol >> 1, -1, tws_a);
                 } else {
-                    col_fft_inplace(Mloc_a, scr_a, lg, ncol, -1, tws_a);
+                    col_fft_inplace(Mloc2_a, scr_a, lg, ncol, -1, tws_a);
                 }
             }
             __syncthreads();
@@ -616,7 +771,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
             if (ncol > 0 && xi) {
                 // pairs (col_pair_item): G_hat of both columns from the packed transform in scr,
                 // no projection needed (the split keeps the symmetry exactly); the new u_hat of
-                // both packed into Mloc for one inverse transform
+                // both packed into Mloc2 for one inverse transform
                 const int npair = ncol >> 1;
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
@@ -648,10 +803,10 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                         const cpx<R> ub = (jb <= kx) ? update(2 * pp + 1, jb, xi_split_b(ck, cm)) : mk<R>(0, 0);
                         x = xi_join_imag(ua, ub);
                     }
-                    Mloc[i] = x;
+                    Mloc2[i] = x;
                 }
                 __syncthreads();
-                push_pairs(fft_col_warp<R, true>(Mloc, scr, lg, npair, +1, tws), Rin, true);
+                push_pairs(fft_col_warp<R, true>(Mloc2, scr, lg, npair, +1, tws), Rin, true, 3);
             } else if (ncol > 0) {
                 const R wTr = (R)wT;
                 const R dt = (R)d.dtau;
@@ -659,7 +814,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                 const RA wTa = (RA)wT;
                 // G_hat = (a + i omega/T) r_hat + F[P(u r_x)], in the adjoint precision
                 auto g_hat = [&](int i, int q, int k) {
-                    const cpx<RA> wh = Mloc_a[i];
+                    const cpx<RA> wh = Mloc2_a[i];
                     const RA a_lin = s_lina[rank + q * C];
                     const cpx<R> rr = rhl[q * nk + k + ks];
                     const cpx<RA> r = mk<RA>((RA)rr.x, (RA)rr.y);
@@ -687,12 +842,12 @@ __global__ void __launch_bounds__(256, 1) k_cluster(Dims d, Bufs<R> p, AdjTables
                     scr[i] = x;
                 }
                 __syncthreads();
-                push_columns(fft_col_warp<R, true>(scr, Mloc, lg, ncol, +1, tws), Rin);
+                push_columns(fft_col_warp<R, true>(scr, Mloc2, lg, ncol, +1, tws), Rin, 3);
             }
             T = Tnext;
             wT = wTnext;
             ++done;
-            cl.sync();
+            xsync(3, bx_Ba);
         }
 
         // ---- write the loop back: band of the owned columns, mixed values of the own rows

@@ -303,6 +303,8 @@ struct ks_loop {
     // fits, else 1; 1 = grid-persistent cooperative kernel; 2 = four launches per tau-step
     int path[2] = {0, 0};
     int force_cluster = 0;          // 0: choose the cluster size; else use this one
+    int cexchange = 1;              // cluster kernel: mbarrier exchanges where the plan has room
+    int force_mb = 0;               // cluster kernel variant: 0 by occupancy, 1 or 2 forced
     ClusterPlan cplan[3] = {};      // double, float, double + float adjoint; bytes = 0: unavailable
     int cthreads = 128;
     int cgrid[3] = {0, 0, 0};
@@ -633,7 +635,8 @@ int setup_persistent(ks_loop* h) {
 
 // Shared-memory plan of the cluster kernel for cluster size C (bytes = 0 if it cannot fit).
 template <typename R, typename RA>
-ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_limit) {
+ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_limit, int smem_sm,
+                              int sms) {
     ClusterPlan cp{};
     const size_t cs = sizeof(cpx<R>), rs = sizeof(R);
     const int nx = h->d.nx, nkx = h->d.nkx;
@@ -676,6 +679,24 @@ ClusterPlan make_cluster_plan(const ks_loop* h, int C, int u_global, int smem_li
     if (sizeof(RA) != sizeof(R)) off += al((size_t)NMAX * sizeof(cpx<RA>));
     cp.off_tab = (int)off;
     off += al((size_t)nkx * (3 * rs + sizeof(RA)));
+    // mbarrier exchanges: a second column buffer and four mbarriers, where they fit and keep the
+    // CTAs per SM that the batch's clusters can use (1 KB of each CTA's shared memory is the
+    // system's).  Not for clusters of one CTA, whose cluster barrier is a block barrier (a
+    // batch of 256 64x64 loops measured 2 % slower with the exchanges).
+    cp.ax = 0;
+    cp.off_M2 = cp.off_M;
+    cp.off_bar = 0;
+    if (h->cexchange && C > 1) {
+        const size_t m2 = al((size_t)cp.ncmax * cp.nsmax * cs), with = off + m2 + 32;
+        const size_t need = ((size_t)h->d.B * C + sms - 1) / sms;  // CTAs per SM for one wave
+        const size_t per0 = (size_t)smem_sm / (off + 1024), per1 = (size_t)smem_sm / (with + 1024);
+        if (with <= (size_t)smem_limit && per1 >= std::min(per0, need)) {
+            cp.off_M2 = (int)off;
+            cp.off_bar = (int)(off + m2);
+            cp.ax = 1;
+            off = with;
+        }
+    }
     cp.bytes = (off <= (size_t)smem_limit) ? (int)off : 0;
     return cp;
 }
@@ -701,20 +722,33 @@ int cluster_block(const ks_loop* h, int slot, const ClusterPlan& cp) {
     return (zb <= 128 && pb <= 128 && cb <= 128) ? 160 : 128;
 }
 
+// the cluster kernel of a column scheme and launch-bound variant (see k_cluster)
+template <typename R, typename RA>
+using ClusterFn = void (*)(Dims, Bufs<R>, AdjTables<RA>, ClusterPlan, int, int, int);
+template <typename R, typename RA>
+ClusterFn<R, RA> cluster_fn(bool xi, int mb) {
+    if (mb == 2) return xi ? k_cluster<R, RA, true, 2> : k_cluster<R, RA, false, 2>;
+    return xi ? k_cluster<R, RA, true, 1> : k_cluster<R, RA, false, 1>;
+}
+
 // pick the cluster size: enough CTAs to cover the GPU (about two per SM), at most 16, and a
-// plan that fits shared memory (grid rows of u in global memory if needed)
+// plan that fits shared memory (grid rows of u in global memory if needed).  Of the kernel's
+// two launch-bound variants the plan takes the one without a register cap unless the capped one
+// keeps more of the batch's clusters resident at once.
 // plan slots: 0 double, 1 float, 2 double state with a float adjoint (mixed finishing)
 template <typename R, typename RA>
 int setup_cluster(ks_loop* h) {
     const int pr = std::is_same<R, double>::value ? (std::is_same<RA, double>::value ? 0 : 2) : 1;
     h->cplan[pr] = ClusterPlan{};
-    int limit = 0, sms = 0;
+    int limit = 0, sms = 0, smem_sm = 0;
     KS_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
     KS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    KS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->dev));
     int target = 16;
     while (target > 1 && (long long)target * h->d.B > 2LL * sms) target >>= 1;
-    KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int v = 0; v < 4; ++v)
+        KS_CUDA(cudaFuncSetAttribute(cluster_fn<R, RA>(v & 1, 1 + (v >> 1)),
+                                     cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     // candidate sizes: powers of two from the target down.  (A size that only balances the
     // columns, e.g. 11 ranks of 2 columns for 22, gives each rank 12 rows in two x-batches and
     // measured slower than 16 ranks with one row batch each.)
@@ -726,10 +760,11 @@ int setup_cluster(ks_loop* h) {
     }
     for (int C : cands) {
         for (int ug = 0; ug < 2; ++ug) {
-            ClusterPlan cp = make_cluster_plan<R, RA>(h, C, ug, limit);
+            ClusterPlan cp = make_cluster_plan<R, RA>(h, C, ug, limit, smem_sm, sms);
             if (!cp.bytes) continue;
-            KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
-            KS_CUDA(cudaFuncSetAttribute(k_cluster<R, RA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
+            for (int v = 0; v < 4; ++v)
+                KS_CUDA(cudaFuncSetAttribute(cluster_fn<R, RA>(v & 1, 1 + (v >> 1)),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, cp.bytes));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);
             cfg.blockDim = dim3(cluster_block(h, pr, cp));
@@ -741,11 +776,21 @@ int setup_cluster(ks_loop* h) {
             at[0].val.clusterDim.z = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            int ncl = 0;
-            if (cudaOccupancyMaxActiveClusters(&ncl, k_cluster<R, RA, false>, &cfg) != cudaSuccess) {
-                cudaGetLastError();
-                ncl = 0;
+            // resident clusters of each launch-bound variant (the fewer of its two column schemes)
+            int nv[2] = {0, 0};
+            for (int m = 0; m < 2; ++m) {
+                nv[m] = 1 << 30;
+                for (int x = 0; x < 2; ++x) {
+                    int n = 0;
+                    if (cudaOccupancyMaxActiveClusters(&n, cluster_fn<R, RA>(x, 1 + m), &cfg) != cudaSuccess) {
+                        cudaGetLastError();
+                        n = 0;
+                    }
+                    nv[m] = std::min(nv[m], n);
+                }
             }
+            cp.mb = h->force_mb ? h->force_mb : ((nv[0] >= std::min(h->d.B, nv[1])) ? 1 : 2);
+            const int ncl = nv[cp.mb - 1];
             if (ncl <= 0) continue;
             h->cplan[pr] = cp;
             h->cgrid[pr] = C * std::min(h->d.B, ncl);
@@ -805,7 +850,8 @@ int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     const int slot = std::is_same<R, RA>::value ? pr : 2;
     const int pa = std::is_same<RA, double>::value ? P64 : P32;
     AdjTables<RA> ta{(const cpx<RA>*)h->d_tw[pa], (const RA*)h->d_qv[pa], (const RA*)h->d_lin[pa]};
-    const ClusterPlan& cp = h->cplan[slot];
+    ClusterPlan cp = h->cplan[slot];
+    cp.err = h->d_err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(h->cgrid[slot]);
     cfg.blockDim = dim3(cluster_block(h, slot, cp));
@@ -819,7 +865,7 @@ int run_cluster(ks_loop* h, Work& w, int pr, long long nsteps, double tol, doubl
     cfg.attrs = at;
     cfg.numAttrs = 1;
     LaunchScope ls(h, s, std::string("cluster") + prec_suffix(pr) + (slot == 2 ? "_adj_f32" : ""));
-    KS_CUDA(cudaLaunchKernelEx(&cfg, h->xi ? k_cluster<R, RA, true> : k_cluster<R, RA, false>, h->d, p,
+    KS_CUDA(cudaLaunchKernelEx(&cfg, cluster_fn<R, RA>(h->xi != 0, cp.mb), h->d, p,
                                ta, cp, (int)nsteps, w.par,
                                w.mix_valid[pr] ? 1 : 0));
     ls.done();
@@ -1581,11 +1627,12 @@ int readback(ks_loop* h, cudaStream_t s) {
     KS_CUDA(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
     if (err) {
-        // a bounded barrier wait gave up: clear the barrier for the next launch and report it
+        // a bounded wait gave up (a grid barrier of the persistent kernel, or an exchange of the
+        // cluster kernel): clear the barrier for the next launch and report it
         KS_CUDA(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), s));
         KS_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
         KS_CUDA(cudaStreamSynchronize(s));
-        return fail(KS_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
+        return fail(KS_ERR_TIMEOUT, "a bounded wait timed out (grid barrier or cluster exchange)");
     }
     return KS_OK;
 }
@@ -2196,6 +2243,17 @@ extern "C" int ks_set_option(ks_loop_t h, const char* key, long long value) {
         if (h->mode == KS_MIXED) KS_TRY((setup_cluster<double, float>(h)));
         if (value && (h->cplan[0].C != value && h->cplan[1].C != value))
             return fail(KS_ERR_ARG, "requested cluster size does not fit this batch");
+    } else if (k == "cluster_min_blocks") {
+        if (value < 0 || value > 2) return fail(KS_ERR_ARG, "cluster_min_blocks must be 0 (auto), 1 or 2");
+        h->force_mb = (int)value;
+        KS_TRY((setup_cluster<double, double>(h)));
+        KS_TRY((setup_cluster<float, float>(h)));
+        if (h->mode == KS_MIXED) KS_TRY((setup_cluster<double, float>(h)));
+    } else if (k == "cluster_exchange") {
+        h->cexchange = value ? 1 : 0;
+        KS_TRY((setup_cluster<double, double>(h)));
+        KS_TRY((setup_cluster<float, float>(h)));
+        if (h->mode == KS_MIXED) KS_TRY((setup_cluster<double, float>(h)));
     } else if (k == "test_barrier_timeout") {
         h->test_barrier_extra = value ? 1 : 0;
     } else if (k == "finish_f32_adjoint") {
@@ -2248,6 +2306,13 @@ extern "C" int ks_get_option(ks_loop_t h, const char* key, long long* value) {
     else if (k == "cluster_f64") *value = h->cplan[0].bytes ? h->cplan[0].C : 0;
     else if (k == "cluster_f32") *value = h->cplan[1].bytes ? h->cplan[1].C : 0;
     else if (k == "cluster_smem_f64") *value = h->cplan[0].bytes;
+    else if (k == "cluster_exchange") *value = h->cexchange;
+    else if (k == "cluster_grid_f64") *value = h->cplan[0].bytes ? h->cgrid[0] : 0;
+    else if (k == "cluster_min_blocks_f64") *value = h->cplan[0].bytes ? h->cplan[0].mb : 0;
+    else if (k == "cluster_min_blocks_f32") *value = h->cplan[1].bytes ? h->cplan[1].mb : 0;
+    else if (k == "cluster_grid_f32") *value = h->cplan[1].bytes ? h->cgrid[1] : 0;
+    else if (k == "cluster_exchange_f64") *value = h->cplan[0].bytes ? h->cplan[0].ax : 0;
+    else if (k == "cluster_exchange_f32") *value = h->cplan[1].bytes ? h->cplan[1].ax : 0;
     else if (k == "cluster_smem_f32") *value = h->cplan[1].bytes;
     else if (k == "rows_per_tile") *value = h->rows_per_tile;
     else if (k == "finish_f32_adjoint") *value = h->finish_f32_adjoint;
