@@ -100,3 +100,34 @@ def test_launch_bound_variant_by_occupancy():
             assert K.ks_get_option(h.handle, "cluster_" + sfx) == 16
             assert K.ks_get_option(h.handle, "cluster_min_blocks_" + sfx) == 2
             assert K.ks_get_option(h.handle, "cluster_grid_" + sfx) == 256
+
+
+@pytest.mark.parametrize("mode", [K.KS_FP64, K.KS_FP32])
+def test_several_loops_per_cluster(mode):
+    """More clusters than fit the GPU at once (40 ragged loops in clusters of 16): each cluster
+    descends several loops in turn, its mbarriers carrying their phases from one loop to the next
+    and the byte counts following each loop's Ns.  Both exchange forms and the per-phase
+    launches give the same bits."""
+    L, nx = 22.0, 64
+    nss = [(32, 64, 128)[i % 3] for i in range(40)]
+    u0, T0 = _loops(L, nx, nss, False)
+    dt = torch.float32 if mode == K.KS_FP32 else torch.float64
+    outs = []
+    for path, xch in ((0, 1), (0, 0), (2, 1)):
+        u = torch.tensor(u0, device="cuda").to(dt)
+        T = torch.tensor(T0, dtype=torch.float64, device="cuda")
+        with K.KSLoop(L, nx, nss, mode, K.KS_IMEX, 0.15, chunk=6) as h:
+            K.ks_set_option(h.handle, "cluster", 16)
+            K.ks_set_option(h.handle, "cluster_exchange", xch)
+            K.ks_set_option(h.handle, "path", path)
+            if path == 0:
+                sfx = "f32" if mode == K.KS_FP32 else "f64"
+                assert K.ks_get_option(h.handle, "cluster_" + sfx) == 16
+                assert K.ks_get_option(h.handle, "cluster_grid_" + sfx) < 16 * len(nss)
+                assert K.ks_get_option(h.handle, "cluster_exchange_" + sfx) == xch
+            K.ks_descend(h.handle, u, T, 12, 0.0)
+            torch.cuda.synchronize()
+        outs.append((u.cpu(), T.cpu()))
+    assert torch.isfinite(outs[0][0]).all()
+    for o in outs[1:]:
+        assert torch.equal(outs[0][0], o[0]) and torch.equal(outs[0][1], o[1])
