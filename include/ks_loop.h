@@ -79,7 +79,8 @@ enum {
     KS_ERR_ARG = -1,     /* bad argument: null pointer, size out of range, L <= 0, dtau <= 0 */
     KS_ERR_CUDA = -2,    /* a CUDA runtime call failed, or no device */
     KS_ERR_OOM = -3,     /* device allocation failed */
-    KS_ERR_TIMEOUT = -4, /* a bounded in-kernel wait gave up (persistent kernel) */
+    KS_ERR_TIMEOUT = -4, /* a bounded in-kernel wait gave up (a grid barrier of the persistent
+                            kernel or an exchange of the cluster kernel, about a second each) */
     KS_ERR_STATE = -5    /* call needs a resident state that was never set */
 };
 
