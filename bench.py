@@ -439,9 +439,17 @@ def add_probe(roof, probe):
 
 
 def launch_shape(K, h, mode, autotuned):
-    return {"path": K.ks_get_option(h.handle, "path"),
-            "cluster": K.ks_get_option(h.handle, "cluster_f32" if mode == K.KS_FP32 else "cluster_f64"),
+    sfx = "f32" if mode == K.KS_FP32 else "f64"
+    path = K.ks_get_option(h.handle, "path")
+    cl = path == 0 and K.ks_get_option(h.handle, "cluster_" + sfx) > 0  # the cluster kernel runs
+    return {"path": path,
+            "cluster": K.ks_get_option(h.handle, "cluster_" + sfx),
             "threads": K.ks_get_option(h.handle, "cluster_threads"),
+            # the cluster kernel's block, exchange form and launch-bound variant
+            "cluster_block": K.ks_get_option(h.handle, "cluster_block_" + sfx) if cl else None,
+            "exchange": (("mbarrier" if K.ks_get_option(h.handle, "cluster_exchange_" + sfx)
+                          else "cluster barrier") if cl else None),
+            "min_blocks": K.ks_get_option(h.handle, "cluster_min_blocks_" + sfx) if cl else None,
             "graph": K.ks_get_option(h.handle, "graph"),
             "graph_replays": K.ks_get_option(h.handle, "graph_replays"),
             "autotuned": bool(autotuned)}
