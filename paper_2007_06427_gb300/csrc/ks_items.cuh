@@ -251,8 +251,9 @@ struct Bufs {
     int own_frozen_only;    // cluster kernel: 1 = carry T forward only for frozen loops of this
                             // precision (the other precision's launch runs concurrently and
                             // carries its own)
-    int step_scalars;       // 1 (tau-steps): ROW_ADJ forms each running loop's step scalars
-                            // (loop_scalars) for the COL_UPDATE items that follow
+    int step_scalars;       // 1 (tau-steps): the ROW_ADJ launch forms each running loop's step
+                            // scalars (loop_scalars, loops_scalars) for the COL_UPDATE items
+                            // that follow
 };
 
 // Projection onto the loops invariant under Xi: (x, s) -> (-x, s), u -> -u (Sec. 4.1, the
@@ -1221,10 +1222,29 @@ KS_HD void row_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
         cpx<R>* F = fft_pair<R, SWZ, false, true>(Y, z, lgnx, npairs, -1, p.tw, 0, p.twsh);
         store_pair_spectra(d, F, Mb, ns, n0, lgp);
         KS_SYNC();
-        // the loop's step scalars, once per loop (the column partials are complete since
-        // COL_RESID); after the item's last barrier, so the rest of the block moves on
-        if (p.step_scalars && n0 == 0 && KS_TID < 32) loop_scalars(d, p, b, par < 0 ? p.par : par);
+        // double: the loop's step scalars, once per loop (the column partials are complete since
+        // COL_RESID), after the item's last barrier so the rest of the block moves on; float:
+        // after the launch's items (loops_scalars)
+        if constexpr (sizeof(R) == 8) {
+            if (p.step_scalars && n0 == 0 && KS_TID < 32) loop_scalars(d, p, b, par < 0 ? p.par : par);
+        }
     }
+}
+
+// Float: the step scalars of every live loop (loop_scalars), loop b on block b mod nblk, its
+// first warp.  The launches that run the ROW_ADJ items call it after them: the column partials
+// are complete since COL_RESID, and the ROW_ADJ items do not read T.  Called inside an item it
+// raised the float kernel's registers from 32 to 48 (10 instead of 16 resident blocks of 128
+// threads); outside the item loop it takes 36, and the per-phase float step got 2-4 % faster
+// (ragged256 82.7 -> 79.7 us, large8_256x1024 75.9 -> 74.2 us).  The double kernel keeps the call
+// in the item: outside it ptxas held the kernel to 32 registers with a spill, and the 256x1024
+// double step got 2 % slower.  Same arithmetic either way.
+template <typename R>
+KS_HD void loops_scalars(const Dims& d, const Bufs<R>& p, int par, int blk, int nblk) {
+    if constexpr (sizeof(R) == 8) return;
+    if (!p.step_scalars || KS_TID >= 32) return;
+    for (int b = blk; b < d.B; b += nblk)
+        if (loop_live(p, b)) loop_scalars(d, p, b, par);
 }
 
 // ------------------------------------------------------------------------------------

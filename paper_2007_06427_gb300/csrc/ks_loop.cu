@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) k_rows(Dims d, Bufs<R> p, int nitems, int
     extern __shared__ __align__(16) unsigned char smem[];
     const Bufs<R> q = stage_twiddles(p, smem, tw_off, nm);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) row_item<R, MODE, true>(d, q, it, smem);
+    if constexpr (MODE == ROW_ADJ) loops_scalars(d, q, q.par, blockIdx.x, gridDim.x);
 }
 
 template <typename R, int MODE>
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(128, 6) k_persist(Dims d, Bufs<R> p, int nstep
         for (int it = blockIdx.x; it < ncol_r; it += gridDim.x) col_item<R, COL_RESID, true>(d, q, it, smem, par);
         if (!grid_sync(bar)) return;
         for (int it = blockIdx.x; it < nrow; it += gridDim.x) row_item<R, ROW_ADJ, true>(d, q, it, smem, par);
+        loops_scalars(d, q, par, blockIdx.x, gridDim.x);
         if (!grid_sync(bar)) return;
         for (int it = blockIdx.x; it < ncol_u; it += gridDim.x) col_item<R, COL_UPDATE, true>(d, q, it, smem, par);
         if (s + 1 < nsteps && !grid_sync(bar)) return;

@@ -173,12 +173,13 @@ int run(const Dims& d, const std::vector<int>& nsv, const std::vector<double>& T
     cols_pass<R, COL_SYNTH_U>(d, h, 0);
     if (mode == 0) {
         p.check_active = 1;
-        p.step_scalars = 1;  // ROW_ADJ forms each loop's step scalars, as in the launches
+        p.step_scalars = 1;  // each loop's step scalars after the ROW_ADJ items, as in the launches
         for (int s = 0; s < steps; ++s) {
             p.par = s & 1;
             rows_pass<R>(d, h, ROW_NONLIN);
             cols_pass<R, COL_RESID>(d, h, p.par);
             rows_pass<R>(d, h, ROW_ADJ);
+            loops_scalars(d, p, p.par, 0, 1);  // after the ROW_ADJ items, as the launches do
             cols_pass<R, COL_UPDATE>(d, h, p.par);
             if (s == 0) a = h.sqrtJ;
         }
