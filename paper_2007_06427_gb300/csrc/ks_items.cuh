@@ -1478,7 +1478,7 @@ KS_HD void col_pair_item(const Dims& d, const Bufs<R>& p, int item, unsigned cha
 
         if constexpr (MODE == COL_UPDATE) {
             // J, the freeze decision and the next T of this step were formed once for the loop
-            // by ROW_ADJ (loop_scalars): a loop that froze now is in p.status
+            // by the ROW_ADJ launch (loop_scalars): a loop that froze now is in p.status
             if (p.status[b] != ST_RUNNING) return;
             const R dt = (R)d.dtau;
             const R wT2 = w_over_T * w_over_T;
@@ -1647,7 +1647,7 @@ KS_HD void col_item(const Dims& d, const Bufs<R>& p, int item, unsigned char* sm
             }
         } else if constexpr (MODE == COL_UPDATE) {
             // J, the freeze decision and the next T of this step were formed once for the loop
-            // by ROW_ADJ (loop_scalars): a loop that froze now is in p.status
+            // by the ROW_ADJ launch (loop_scalars): a loop that froze now is in p.status
             if (p.status[b] != ST_RUNNING) return;
             const R dt = (R)d.dtau;
             const R cqj = p.cq[j];
