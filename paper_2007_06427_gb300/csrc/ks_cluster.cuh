@@ -822,24 +822,58 @@ __global__ void __launch_bounds__(256, MB) k_cluster(Dims d, Bufs<R> p, AdjTable
                     const cpx<RA> G = mk<RA>(a_lin * r.x - bk * r.y + wh.x, a_lin * r.y + bk * r.x + wh.y);
                     return mk<R>((R)G.x, (R)G.y);
                 };
-                for (int i = wtid; i < ncol << lg; i += ntw) {
-                    const int q = i >> lg, n = i & (ns - 1);
-                    const int k = (n < (ns >> 1)) ? n : n - ns;
-                    cpx<R> x = mk<R>(0, 0);
-                    if (k >= -ks && k <= ks) {
-                        const int j = rank + q * C;
-                        const cpx<R> G = g_hat(i, q, k);
+                // double state with more than one element per thread: the band by (k, -k) pairs,
+                // which share the IMEX factor ((-k)^2 = k^2 exactly), so a thread divides once for
+                // both; the out-of-band elements are zeroed apart (64x128 double 28.48 -> 27.78 us
+                // per step, the same bits; the float kernels, where a division is cheap, measured
+                // slower with the branch compiled in, so they keep one loop)
+                bool paired = false;
+                if constexpr (sizeof(R) == 8) paired = (ncol << lg) > ntw;
+                if (paired) {
+                    const int nh = ks + 1;
+                    for (int i = wtid; i < ncol * nh; i += ntw) {
+                        const int q = i / nh, k = i - q * nh;
                         R f = dt;
                         if (d.scheme == 1) {
                             const R kk2 = (R)k * (R)k;
-                            f = dt / ((R)1 + dt * (kk2 * wT2 + s_cq[j]));
+                            f = dt / ((R)1 + dt * (kk2 * wT2 + s_cq[rank + q * C]));
                         }
-                        cpx<R> u = uhl[q * nk + k + ks];
-                        u = u - scale(G, f);
-                        uhl[q * nk + k + ks] = u;
-                        x = u;
+                        auto upd = [&](int kk, int n) {
+                            const int e = (q << lg) + n;
+                            const cpx<R> G = g_hat(e, q, kk);
+                            cpx<R> u = uhl[q * nk + kk + ks];
+                            u = u - scale(G, f);
+                            uhl[q * nk + kk + ks] = u;
+                            scr[e] = u;
+                        };
+                        upd(k, k);
+                        if (k > 0) upd(-k, ns - k);
                     }
-                    scr[i] = x;
+                    for (int i = wtid; i < ncol << lg; i += ntw) {
+                        const int n = i & (ns - 1);
+                        const int k = (n < (ns >> 1)) ? n : n - ns;
+                        if (k < -ks || k > ks) scr[i] = mk<R>(0, 0);
+                    }
+                } else {
+                    for (int i = wtid; i < ncol << lg; i += ntw) {
+                        const int q = i >> lg, n = i & (ns - 1);
+                        const int k = (n < (ns >> 1)) ? n : n - ns;
+                        cpx<R> x = mk<R>(0, 0);
+                        if (k >= -ks && k <= ks) {
+                            const int j = rank + q * C;
+                            const cpx<R> G = g_hat(i, q, k);
+                            R f = dt;
+                            if (d.scheme == 1) {
+                                const R kk2 = (R)k * (R)k;
+                                f = dt / ((R)1 + dt * (kk2 * wT2 + s_cq[j]));
+                            }
+                            cpx<R> u = uhl[q * nk + k + ks];
+                            u = u - scale(G, f);
+                            uhl[q * nk + k + ks] = u;
+                            x = u;
+                        }
+                        scr[i] = x;
+                    }
                 }
                 __syncthreads();
                 push_columns(fft_col_warp<R, true>(scr, Mloc2, lg, ncol, +1, tws), Rin, 3);
