@@ -30,6 +30,15 @@ def test_header_declares_the_boundary():
         assert f in names
 
 
+def test_every_option_key_is_documented():
+    """Every key ks_set_option / ks_get_option accept is described in the header."""
+    src = open(os.path.join(ROOT, "paper_2007_06427_gb300", "csrc", "ks_loop.cu")).read()
+    hdr = open(os.path.join(ROOT, "include", "ks_loop.h")).read()
+    keys = sorted(set(re.findall(r'k == "([a-z0-9_]+)"', src)))
+    assert len(keys) > 20
+    assert [k for k in keys if f'"{k}"' not in hdr] == []
+
+
 def test_every_declared_symbol_is_exported(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
